@@ -1,0 +1,631 @@
+/*
+ * pflb_oracle.c -- plain, slow FP64 CPU oracle for one time step of the
+ * low-Mach phase-field / lattice-Boltzmann / finite-difference (PF-LB-FD)
+ * scheme of Namdar, Norouzi & Varnik (arXiv 2310.17214).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library: the lattice tables, the unit conversions
+ * and every formula below are written out here independently.
+ *
+ * What it computes (paper references are to sections / equations):
+ *   - EOS rho = Mw P0 / (R T)                     (Sec. 3.1, eq. rho-in-terms-of-P0-and-T)
+ *   - P0 = m R / int(Mw/T dV) over the fluid      (Sec. 3.1, text after the EOS)
+ *   - drag F = -A_u mu phi_f phi_s^2/eta^2 u      (Sec. 3.2.1, eq. Fdrag-empirical-law; u_s = 0)
+ *   - species transport + omega_k = M_k sum s Q   (Sec. 3.2.2, eqs. volume-averaged-species-equation-5, 8)
+ *   - temperature equation with S_I and omega_T   (Sec. 3.3, eqs. diffusion-heat-flux-3,
+ *                                                   energy-transport-DI-version, 9)
+ *   - pressure-based LB with source Xi, f_eq, g_eq (Sec. 3.3, eqs. pop-g, body-force,
+ *                                                   eq-pop-f, eq-pop-g; mu = rho cs^2 (tau-1/2))
+ *   - upwind convection, central diffusion, forward Euler (Sec. 3.3, last paragraph)
+ *   - Sutherland viscosity and lambda = mu cp / Pr (Sec. 4, eqs. muT, lambdaT)
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   BGK with second-order (half-step) source; P_h = sum g + rho cs^2 D / 2 and
+ *   rho u = sum c g / cs^2 + F / 2 with the drag implicit in u; D = div u from
+ *   the low-Mach constraint using this step's increments; conservative
+ *   phi_f-weighted FD with arithmetic-mean face coefficients; S_I relaxes the
+ *   fluid toward the solid temperature; lagged dP0/dt; half-way bounce-back
+ *   walls, moving-wall bounce-back inlet, anti-bounce-back P_h = 0 outlet.
+ *
+ * Layout: cell = x + nx*(y + ny*z); populations g[i*N + cell]; species
+ * Y[k*N + cell]; velocity u[a*N + cell].
+ *
+ * Parity pins: tests/test_oracle_pins.py (closed forms, invariants, brute force).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_KMAX 8
+#define ORC_JMAX 4
+#define ORC_QMAX 19
+#define ORC_R 8.314 /* J/(mol K), value printed in Sec. 3.1 */
+
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_INLET = 2, ORC_BC_OUTLET = 3 };
+enum { ORC_P0_FIXED = 0, ORC_P0_CLOSED = 1 };
+enum { ORC_CHEM_NONE = 0, ORC_CHEM_EXPLICIT = 1, ORC_CHEM_IMPLICIT = 2 };
+
+typedef struct {
+  int dim, nx, ny, nz;
+  int bc[6];               /* x-lo, x-hi, y-lo, y-hi, z-lo, z-hi */
+  double wall_u[6][3];     /* tangential velocity of each wall face (lattice) */
+  double wall_T[6];        /* wall temperature (K) of each wall face, 0 = adiabatic */
+  double dx, dt, rho_ref;  /* physical scales (1,1,1 = pure lattice units) */
+  /* fluid properties */
+  int K;                   /* number of species, 0 = non-reactive single gas */
+  double M0, cp0;          /* molar mass / heat capacity when K == 0 */
+  double M[ORC_KMAX], cp[ORC_KMAX], hf[ORC_KMAX], Dref[ORC_KMAX];
+  double D_Tref, D_exp;    /* D_k = Dref_k (T / D_Tref)^D_exp */
+  double mu_ref;           /* dynamic viscosity (physical units) */
+  int sutherland;          /* 1: mu(T) Sutherland law */
+  double suth_T, suth_S, Pr;
+  double A_u, A_T, eta;    /* coupling parameters, interface width (cells) */
+  double Fb[3];            /* body force density (lattice) */
+  /* inlet */
+  int inlet_parabolic;
+  double u_in, T_in, Y_in[ORC_KMAX];
+  /* thermodynamic pressure */
+  int p0_mode;
+  /* solid */
+  int Ts_field;            /* 0: uniform fixed Ts_uniform, 1: transported field */
+  double Ts_uniform, rhocp_s, lambda_s;
+  double phi_min;
+  /* chemistry */
+  int chem_mode, J;
+  double A[ORC_JMAX], b[ORC_JMAX], EaR[ORC_JMAX];
+  double order[ORC_JMAX][ORC_KMAX], stoich[ORC_JMAX][ORC_KMAX];
+} orc_params;
+
+/* ---------------------------------------------------------------- lattices */
+static const int C2[9][3] = {{0,0,0},{1,0,0},{0,1,0},{-1,0,0},{0,-1,0},
+                             {1,1,0},{-1,1,0},{-1,-1,0},{1,-1,0}};
+static const double W2[9] = {4.0/9, 1.0/9, 1.0/9, 1.0/9, 1.0/9,
+                             1.0/36, 1.0/36, 1.0/36, 1.0/36};
+static const int C3[19][3] = {{0,0,0},
+  {1,0,0},{-1,0,0},{0,1,0},{0,-1,0},{0,0,1},{0,0,-1},
+  {1,1,0},{-1,-1,0},{1,-1,0},{-1,1,0},
+  {1,0,1},{-1,0,-1},{1,0,-1},{-1,0,1},
+  {0,1,1},{0,-1,-1},{0,1,-1},{0,-1,1}};
+static const double W3[19] = {1.0/3,
+  1.0/18,1.0/18,1.0/18,1.0/18,1.0/18,1.0/18,
+  1.0/36,1.0/36,1.0/36,1.0/36,1.0/36,1.0/36,
+  1.0/36,1.0/36,1.0/36,1.0/36,1.0/36,1.0/36};
+static const double CS2 = 1.0 / 3.0;
+
+typedef struct { int Q; const int (*c)[3]; const double* w; } lat_t;
+static lat_t lattice_of(int dim) {
+  lat_t L;
+  if (dim == 2) { L.Q = 9; L.c = C2; L.w = W2; }
+  else { L.Q = 19; L.c = C3; L.w = W3; }
+  return L;
+}
+static int opposite(lat_t L, int i) {
+  for (int j = 0; j < L.Q; ++j)
+    if (L.c[j][0] == -L.c[i][0] && L.c[j][1] == -L.c[i][1] && L.c[j][2] == -L.c[i][2]) return j;
+  return -1;
+}
+
+/* Exported so that tests can check both sides use the same direction order. */
+int orc_lattice(int dim, int* c_out, double* w_out) {
+  lat_t L = lattice_of(dim);
+  for (int i = 0; i < L.Q; ++i) {
+    for (int a = 0; a < 3; ++a) c_out[3 * i + a] = L.c[i][a];
+    w_out[i] = L.w[i];
+  }
+  return L.Q;
+}
+
+/* ------------------------------------------------ equilibrium and source */
+/* f_eq (Sec. 3.3, eq. eq-pop-f) and g_eq = cs^2 f_eq + w (P_h - rho cs^2)
+ * (eq. eq-pop-g), written literally. */
+void orc_equilibrium(int dim, double Ph, double rho, const double* u, double* geq) {
+  lat_t L = lattice_of(dim);
+  double uu = 0;
+  for (int a = 0; a < dim; ++a) uu += u[a] * u[a];
+  for (int i = 0; i < L.Q; ++i) {
+    double cu = 0;
+    for (int a = 0; a < dim; ++a) cu += L.c[i][a] * u[a];
+    double feq = rho * L.w[i] * (1.0 + cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+    geq[i] = CS2 * feq + L.w[i] * (Ph - rho * CS2);
+  }
+}
+
+/* Source Xi (Sec. 3.3, eq. body-force): G = grad(rho cs^2), F = total force
+ * density (body force plus drag), D = div u. */
+void orc_source(int dim, double rho, const double* G, const double* u, const double* F,
+                double D, double* xi) {
+  lat_t L = lattice_of(dim);
+  double uu = 0;
+  for (int a = 0; a < dim; ++a) uu += u[a] * u[a];
+  for (int i = 0; i < L.Q; ++i) {
+    double cu = 0;
+    for (int a = 0; a < dim; ++a) cu += L.c[i][a] * u[a];
+    double feq = rho * L.w[i] * (1.0 + cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+    double s = 0;
+    for (int a = 0; a < dim; ++a)
+      s += (L.c[i][a] - u[a]) * (G[a] * (feq / rho - L.w[i]) + F[a] * feq / rho);
+    xi[i] = s + rho * CS2 * L.w[i] * D;
+  }
+}
+
+/* ---------------------------------------------------------- thermo, props */
+typedef struct { double T, Y[ORC_KMAX], phi, Ts; } cellv;
+typedef struct { double Mw, rho, cp, mu, lam, D[ORC_KMAX]; } derv;
+
+static double mixture_Mw(const orc_params* p, const double* Y) {
+  if (p->K == 0) return p->M0;
+  double s = 0;
+  for (int k = 0; k < p->K; ++k) s += Y[k] / p->M[k];
+  return 1.0 / s;
+}
+static double mixture_cp(const orc_params* p, const double* Y) {
+  if (p->K == 0) return p->cp0;
+  double s = 0;
+  for (int k = 0; k < p->K; ++k) s += Y[k] * p->cp[k];
+  return s;
+}
+/* lattice density rho / rho_ref from the EOS */
+static double eos_rho(const orc_params* p, double P0, double Mw, double T) {
+  return P0 * Mw / (ORC_R * T * p->rho_ref);
+}
+/* lattice dynamic viscosity: Sutherland (Sec. 4, eq. muT) or constant */
+static double visc(const orc_params* p, double T) {
+  double mu = p->mu_ref;
+  if (p->sutherland)
+    mu = p->mu_ref * pow(T / p->suth_T, 1.5) * (p->suth_T + p->suth_S) / (T + p->suth_S);
+  return mu * p->dt / (p->rho_ref * p->dx * p->dx);
+}
+
+static void derive(const orc_params* p, const cellv* v, double P0, derv* d) {
+  d->Mw = mixture_Mw(p, v->Y);
+  d->rho = eos_rho(p, P0, d->Mw, v->T);
+  d->cp = mixture_cp(p, v->Y);
+  d->mu = visc(p, v->T);
+  d->lam = d->mu * d->cp / p->Pr; /* Sec. 4, eq. lambdaT (lattice units) */
+  for (int k = 0; k < p->K; ++k) {
+    double D = p->Dref[k];
+    if (p->D_exp != 0.0) D = p->Dref[k] * pow(v->T / p->D_Tref, p->D_exp);
+    d->D[k] = D * p->dt / (p->dx * p->dx);
+  }
+}
+
+/* Explicit rates: Q_j = A T^b exp(-Ea/RT) prod C_k^order, C_k = rho Y_k / M_k
+ * (mol/m^3); omega_k = M_k sum_j s_kj Q_j (Sec. 3.2.2, eq. 8), omega_T =
+ * -sum hf_k omega_k (Sec. 3.3, eq. 9).  Outputs are per lattice step per
+ * rho_ref:  omega_k dt / rho_ref (1/step) and omega_T dt / rho_ref (J/kg). */
+static double powi_or_pow(double x, double e) {
+  if (e == 1.0) return x;
+  if (e == 2.0) return x * x;
+  if (e == 0.0) return 1.0;
+  return pow(x, e);
+}
+void orc_chem_rates(const orc_params* p, double T, const double* Y, double rho_lat,
+                    double* omega, double* omegaT) {
+  double rho = rho_lat * p->rho_ref;
+  double C[ORC_KMAX];
+  for (int k = 0; k < p->K; ++k) C[k] = rho * (Y[k] > 0 ? Y[k] : 0.0) / p->M[k];
+  for (int k = 0; k < p->K; ++k) omega[k] = 0;
+  for (int j = 0; j < p->J; ++j) {
+    double q = p->A[j] * exp(-p->EaR[j] / T);
+    if (p->b[j] != 0.0) q *= pow(T, p->b[j]);
+    for (int k = 0; k < p->K; ++k)
+      if (p->order[j][k] != 0.0) q *= powi_or_pow(C[k], p->order[j][k]);
+    for (int k = 0; k < p->K; ++k) omega[k] += p->M[k] * p->stoich[j][k] * q;
+  }
+  double wt = 0;
+  for (int k = 0; k < p->K; ++k) {
+    omega[k] = omega[k] * p->dt / p->rho_ref;
+    wt -= p->hf[k] * omega[k];
+  }
+  *omegaT = wt;
+}
+
+/* ----------------------------------------------------------- grid helpers */
+static int ncell(const orc_params* p) { return p->nx * p->ny * (p->dim == 3 ? p->nz : 1); }
+static int extent(const orc_params* p, int a) { return a == 0 ? p->nx : a == 1 ? p->ny : p->nz; }
+
+/* Neighbour value along axis a, side s (-1/+1): periodic wraps; an inlet face
+ * gives the inlet state (T_in, Y_in); a wall with a set temperature gives that
+ * temperature; other walls and the outlet give the cell's own value (zero
+ * normal gradient).  phi, Y at walls and Ts of ghosts are the cell's own. */
+static void neighbour(const orc_params* p, const double* phi, const double* T, const double* Y,
+                      const double* Ts, int N, const int xyz[3], int a, int s, cellv* out) {
+  int q[3] = {xyz[0], xyz[1], xyz[2]};
+  q[a] += s;
+  int n = extent(p, a);
+  int face = 2 * a + (s > 0 ? 1 : 0);
+  int c0 = xyz[0] + p->nx * (xyz[1] + p->ny * xyz[2]);
+  int ghost = 0;
+  if (q[a] < 0 || q[a] >= n) {
+    if (p->bc[face] == ORC_BC_PERIODIC) q[a] = (q[a] + n) % n;
+    else ghost = 1;
+  }
+  if (!ghost) {
+    int c = q[0] + p->nx * (q[1] + p->ny * q[2]);
+    out->T = T[c];
+    for (int k = 0; k < p->K; ++k) out->Y[k] = Y[(size_t)k * N + c];
+    out->phi = phi[c];
+    out->Ts = Ts ? Ts[c] : p->Ts_uniform;
+    return;
+  }
+  out->phi = phi[c0];
+  out->Ts = Ts ? Ts[c0] : p->Ts_uniform;
+  if (p->bc[face] == ORC_BC_INLET) {
+    out->T = p->T_in;
+    for (int k = 0; k < p->K; ++k) out->Y[k] = p->Y_in[k];
+  } else if (p->bc[face] == ORC_BC_WALL && p->wall_T[face] > 0.0) {
+    out->T = p->wall_T[face];
+    for (int k = 0; k < p->K; ++k) out->Y[k] = Y[(size_t)k * N + c0];
+  } else {
+    out->T = T[c0];
+    for (int k = 0; k < p->K; ++k) out->Y[k] = Y[(size_t)k * N + c0];
+  }
+}
+
+static void own(const orc_params* p, const double* phi, const double* T, const double* Y,
+                const double* Ts, int N, int c, cellv* out) {
+  out->T = T[c];
+  for (int k = 0; k < p->K; ++k) out->Y[k] = Y[(size_t)k * N + c];
+  out->phi = phi[c];
+  out->Ts = Ts ? Ts[c] : p->Ts_uniform;
+}
+
+static void coords(const orc_params* p, int c, int xyz[3]) {
+  xyz[0] = c % p->nx;
+  xyz[1] = (c / p->nx) % p->ny;
+  xyz[2] = c / (p->nx * p->ny);
+}
+
+/* Inlet velocity at a cell of the x = 0 column: uniform, or a parabola over
+ * each wall-bounded transverse axis (walls half-way outside the domain). */
+static double inlet_u(const orc_params* p, const int xyz[3]) {
+  double u = p->u_in;
+  if (!p->inlet_parabolic) return u;
+  for (int a = 1; a < p->dim; ++a) {
+    if (p->bc[2 * a] != ORC_BC_WALL) continue;
+    double n = extent(p, a), s = xyz[a] + 0.5;
+    u *= 4.0 * s * (n - s) / (n * n);
+  }
+  return u;
+}
+
+/* --------------------------------------------------- FD transport (T, Y, Ts)
+ * Conservative phi_f-weighted form of eqs. volume-averaged-species-equation-5
+ * and energy-transport-DI-version, forward Euler, upwind convection with the
+ * cell velocity, central diffusion with arithmetic-mean face coefficients, the
+ * species-enthalpy term -(sum cp_k j_k).grad T with central gradients, the
+ * lagged dP0/dt, omega_T and S_I = A_T lambda phi_f phi_s^2 / eta^2 (Ts - T).
+ * u is the lattice velocity field u[a*N + c]; Tn/Yn/Tsn receive step n+1. */
+int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const double* Y,
+                 const double* Ts, const double* u, double P0, double P0prev,
+                 double* Tn, double* Yn, double* Tsn) {
+  int N = ncell(p), K = p->K, dim = p->dim;
+  double eta2 = p->eta * p->eta;
+  double Cs = p->rhocp_s / p->rho_ref;
+  double Lams = p->lambda_s * p->dt / (p->rho_ref * p->dx * p->dx);
+  for (int c = 0; c < N; ++c) {
+    int xyz[3];
+    coords(p, c, xyz);
+    cellv v0, vm[3], vp[3];
+    derv d0, dm[3], dp[3];
+    own(p, phi, T, Y, Ts, N, c, &v0);
+    derive(p, &v0, P0, &d0);
+    for (int a = 0; a < dim; ++a) {
+      neighbour(p, phi, T, Y, Ts, N, xyz, a, -1, &vm[a]);
+      neighbour(p, phi, T, Y, Ts, N, xyz, a, +1, &vp[a]);
+      derive(p, &vm[a], P0, &dm[a]);
+      derive(p, &vp[a], P0, &dp[a]);
+    }
+    double phif = 1.0 - v0.phi, phis = v0.phi;
+    int fluid_on = phif >= p->phi_min;
+    int solid_on = p->Ts_field ? (phis >= p->phi_min) : 1;
+    double SI = 0;
+    if (fluid_on && solid_on)
+      SI = p->A_T * d0.lam * phif * phis * phis / eta2 * (v0.Ts - v0.T);
+
+    /* species */
+    double omega[ORC_KMAX] = {0}, omegaT = 0;
+    if (p->chem_mode == ORC_CHEM_EXPLICIT && K > 0)
+      orc_chem_rates(p, v0.T, v0.Y, d0.rho, omega, &omegaT);
+    for (int k = 0; k < K; ++k) {
+      if (!fluid_on) { Yn[(size_t)k * N + c] = v0.Y[k]; continue; }
+      double adv = 0, dif = 0;
+      double kc = phif * d0.rho * d0.D[k];
+      for (int a = 0; a < dim; ++a) {
+        double ua = u[(size_t)a * N + c];
+        if (ua > 0) adv += ua * (v0.Y[k] - vm[a].Y[k]);
+        else adv += ua * (vp[a].Y[k] - v0.Y[k]);
+        double km = 0.5 * (kc + (1.0 - vm[a].phi) * dm[a].rho * dm[a].D[k]);
+        double kp = 0.5 * (kc + (1.0 - vp[a].phi) * dp[a].rho * dp[a].D[k]);
+        dif += kp * (vp[a].Y[k] - v0.Y[k]) - km * (v0.Y[k] - vm[a].Y[k]);
+      }
+      double rhs = -phif * d0.rho * adv + dif + phif * omega[k];
+      Yn[(size_t)k * N + c] = v0.Y[k] + rhs / (phif * d0.rho);
+    }
+
+    /* temperature */
+    if (fluid_on) {
+      double adv = 0, dif = 0, cross = 0;
+      double kc = phif * d0.lam;
+      for (int a = 0; a < dim; ++a) {
+        double ua = u[(size_t)a * N + c];
+        if (ua > 0) adv += ua * (v0.T - vm[a].T);
+        else adv += ua * (vp[a].T - v0.T);
+        double km = 0.5 * (kc + (1.0 - vm[a].phi) * dm[a].lam);
+        double kp = 0.5 * (kc + (1.0 - vp[a].phi) * dp[a].lam);
+        dif += kp * (vp[a].T - v0.T) - km * (v0.T - vm[a].T);
+        double gT = 0.5 * (vp[a].T - vm[a].T);
+        for (int k = 0; k < K; ++k)
+          cross += p->cp[k] * d0.D[k] * 0.5 * (vp[a].Y[k] - vm[a].Y[k]) * gT;
+      }
+      double rhs = -phif * d0.rho * d0.cp * adv + dif +
+                   phif * (d0.rho * cross + (P0 - P0prev) / p->rho_ref + omegaT + SI);
+      Tn[c] = v0.T + rhs / (phif * d0.rho * d0.cp);
+    } else {
+      Tn[c] = v0.Ts;
+    }
+
+    /* solid temperature (field mode) */
+    if (p->Ts_field && Tsn) {
+      if (phis >= p->phi_min) {
+        double dif = 0;
+        for (int a = 0; a < dim; ++a) {
+          double km = 0.5 * (phis + vm[a].phi) * Lams;
+          double kp = 0.5 * (phis + vp[a].phi) * Lams;
+          dif += kp * (vp[a].Ts - v0.Ts) - km * (v0.Ts - vm[a].Ts);
+        }
+        Tsn[c] = v0.Ts + (dif - phif * SI) / (phis * Cs);
+      } else {
+        Tsn[c] = v0.Ts;
+      }
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------ streaming */
+/* Pull the populations arriving at cell c from the post-collision field gs,
+ * applying the boundary rules; uw is the outlet wall-velocity estimate. */
+static void pull(const orc_params* p, lat_t L, const double* gs, int N, int c, const int xyz[3],
+                 double rho_c, double rho_in, const double* uw, double* gin) {
+  for (int i = 0; i < L.Q; ++i) {
+    int s[3] = {xyz[0] - L.c[i][0], xyz[1] - L.c[i][1], xyz[2] - L.c[i][2]};
+    int out_face[3] = {-1, -1, -1};
+    for (int a = 0; a < p->dim; ++a) {
+      int n = extent(p, a);
+      if (s[a] < 0 || s[a] >= n) {
+        int face = 2 * a + (s[a] >= n ? 1 : 0);
+        if (p->bc[face] == ORC_BC_PERIODIC) s[a] = (s[a] + n) % n;
+        else out_face[a] = face;
+      }
+    }
+    int wall = -1, inlet = 0, outlet = 0;
+    for (int a = 0; a < p->dim; ++a) {
+      if (out_face[a] < 0) continue;
+      int bc = p->bc[out_face[a]];
+      if (bc == ORC_BC_WALL && wall < 0) wall = out_face[a];
+      if (bc == ORC_BC_INLET) inlet = 1;
+      if (bc == ORC_BC_OUTLET) outlet = 1;
+    }
+    int ib = opposite(L, i);
+    if (wall >= 0) {
+      double cu = 0;
+      for (int a = 0; a < p->dim; ++a) cu += L.c[i][a] * p->wall_u[wall][a];
+      gin[i] = gs[(size_t)ib * N + c] + 2.0 * L.w[i] * rho_c * cu;
+    } else if (inlet) {
+      double cu = L.c[i][0] * inlet_u(p, xyz);
+      gin[i] = gs[(size_t)ib * N + c] + 2.0 * L.w[i] * rho_in * cu;
+    } else if (outlet) {
+      double cu = 0, uu = 0;
+      for (int a = 0; a < p->dim; ++a) { cu += L.c[i][a] * uw[a]; uu += uw[a] * uw[a]; }
+      gin[i] = -gs[(size_t)ib * N + c] + L.w[i] * (2.0 * 0.0 + rho_c * (cu * cu / CS2 - uu));
+    } else {
+      int sc = s[0] + p->nx * (s[1] + p->ny * s[2]);
+      gin[i] = gs[(size_t)i * N + sc];
+    }
+  }
+}
+
+static int is_outlet_cell(const orc_params* p, const int xyz[3]) {
+  return p->bc[1] == ORC_BC_OUTLET && xyz[0] == p->nx - 1;
+}
+
+/* Pull + moments for every cell: gin (Q*N), u (dim*N), rho (N), Kd (N). */
+static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, const double* gs,
+                               const double* T, const double* Y, double P0, double* gin_all,
+                               double* u, double* rho, double* Kd, double* mu_out) {
+  int N = ncell(p), dim = p->dim;
+  double eta2 = p->eta * p->eta;
+  double rho_in = eos_rho(p, P0, mixture_Mw(p, p->Y_in), p->T_in);
+  for (int c = 0; c < N; ++c) {
+    int xyz[3];
+    coords(p, c, xyz);
+    double Yc[ORC_KMAX];
+    for (int k = 0; k < p->K; ++k) Yc[k] = Y[(size_t)k * N + c];
+    double r = eos_rho(p, P0, mixture_Mw(p, Yc), T[c]);
+    double mu = visc(p, T[c]);
+    double phis = phi[c], phif = 1.0 - phis;
+    double kd = p->A_u * mu * phif * phis * phis / eta2;
+    double gin[ORC_QMAX], uw[3] = {0, 0, 0}, uc[3] = {0, 0, 0};
+    int passes = is_outlet_cell(p, xyz) ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+      pull(p, L, gs, N, c, xyz, r, rho_in, uw, gin);
+      for (int a = 0; a < dim; ++a) {
+        double m = 0;
+        for (int i = 0; i < L.Q; ++i) m += L.c[i][a] * gin[i];
+        m /= CS2;
+        uc[a] = (m + 0.5 * p->Fb[a]) / (r + 0.5 * kd);
+      }
+      for (int a = 0; a < dim; ++a) uw[a] = uc[a];
+    }
+    for (int i = 0; i < L.Q; ++i) gin_all[(size_t)i * N + c] = gin[i];
+    for (int a = 0; a < dim; ++a) u[(size_t)a * N + c] = uc[a];
+    rho[c] = r;
+    Kd[c] = kd;
+    mu_out[c] = mu;
+  }
+}
+
+/* ----------------------------------------------------------- public API */
+/* scal: [0] P0, [1] P0 of the previous step, [2] fluid mass m (lattice),
+ * [3] I = sum phi_f Mw / T, [4] inlet mass flux, [5] outlet mass flux,
+ * [6] step counter. */
+static double reduce_I(const orc_params* p, const double* phi, const double* T, const double* Y) {
+  int N = ncell(p);
+  double I = 0;
+  for (int c = 0; c < N; ++c) {
+    double Yc[ORC_KMAX];
+    for (int k = 0; k < p->K; ++k) Yc[k] = Y[(size_t)k * N + c];
+    I += (1.0 - phi[c]) * mixture_Mw(p, Yc) / T[c];
+  }
+  return I;
+}
+
+/* g = g_eq(P_h, rho, u) from the given T, Y, u (nullable: rest), P_h
+ * (nullable: 0) and P0; m = sum phi_f rho = P0 I / (R rho_ref). */
+int orc_init(const orc_params* p, const double* phi, double* g, const double* T, const double* Y,
+             const double* u, const double* Ph, double P0, double* scal) {
+  lat_t L = lattice_of(p->dim);
+  int N = ncell(p);
+  for (int c = 0; c < N; ++c) {
+    double Yc[ORC_KMAX], uc[3] = {0, 0, 0}, geq[ORC_QMAX];
+    for (int k = 0; k < p->K; ++k) Yc[k] = Y[(size_t)k * N + c];
+    if (u)
+      for (int a = 0; a < p->dim; ++a) uc[a] = u[(size_t)a * N + c];
+    double r = eos_rho(p, P0, mixture_Mw(p, Yc), T[c]);
+    orc_equilibrium(p->dim, Ph ? Ph[c] : 0.0, r, uc, geq);
+    for (int i = 0; i < L.Q; ++i) g[(size_t)i * N + c] = geq[i];
+  }
+  double I = reduce_I(p, phi, T, Y);
+  scal[0] = P0;
+  scal[1] = P0;
+  scal[2] = P0 * I / (ORC_R * p->rho_ref);
+  scal[3] = I;
+  scal[4] = scal[5] = 0;
+  scal[6] = 0;
+  return 0;
+}
+
+/* Velocity, density and sum-of-populations pressure that the next step will
+ * see at every cell (pull + moments of the current state, no collision). */
+int orc_moments(const orc_params* p, const double* phi, const double* g, const double* T,
+                const double* Y, const double* scal, double* u, double* rho, double* Ph) {
+  lat_t L = lattice_of(p->dim);
+  int N = ncell(p);
+  double* gin = malloc(sizeof(double) * (size_t)L.Q * N);
+  double* Kd = malloc(sizeof(double) * N);
+  double* mu = malloc(sizeof(double) * N);
+  stream_and_moments(p, L, phi, g, T, Y, scal[0], gin, u, rho, Kd, mu);
+  for (int c = 0; c < N; ++c) {
+    double s = 0;
+    for (int i = 0; i < L.Q; ++i) s += gin[(size_t)i * N + c];
+    Ph[c] = s;
+  }
+  free(gin); free(Kd); free(mu);
+  return 0;
+}
+
+/* One full time step n -> n+1 (in place on g, T, Y, Ts, scal).  diag
+ * (nullable) receives u (dim*N), rho (N), P_h (N), D (N) of step n. */
+int orc_step(const orc_params* p, const double* phi, double* g, double* T, double* Y, double* Ts,
+             double* scal, double* diag) {
+  lat_t L = lattice_of(p->dim);
+  int N = ncell(p), dim = p->dim, K = p->K;
+  double P0 = scal[0], P0prev = scal[1];
+  double* gin = malloc(sizeof(double) * (size_t)L.Q * N);
+  double* u = malloc(sizeof(double) * (size_t)dim * N);
+  double* rho = malloc(sizeof(double) * N);
+  double* Kd = malloc(sizeof(double) * N);
+  double* mu = malloc(sizeof(double) * N);
+  double* Tn = malloc(sizeof(double) * N);
+  double* Yn = malloc(sizeof(double) * (size_t)(K > 0 ? K : 1) * N);
+  double* Tsn = p->Ts_field ? malloc(sizeof(double) * N) : NULL;
+
+  /* 1-2: EOS, pull streaming with boundary rules, moments, implicit drag */
+  stream_and_moments(p, L, phi, g, T, Y, P0, gin, u, rho, Kd, mu);
+
+  /* 3: FD transport of T, Y (and Ts) with u^n, rho^n, explicit chemistry */
+  orc_fd_phase(p, phi, T, Y, p->Ts_field ? Ts : NULL, u, P0, P0prev, Tn, Yn, Tsn);
+
+  /* 4-5: divergence from the low-Mach constraint, source, collision */
+  for (int c = 0; c < N; ++c) {
+    int xyz[3];
+    coords(p, c, xyz);
+    double Yc[ORC_KMAX];
+    for (int k = 0; k < K; ++k) Yc[k] = Y[(size_t)k * N + c];
+    double Mw = mixture_Mw(p, Yc);
+    double D = (Tn[c] - T[c]) / T[c];
+    double sY = 0;
+    for (int k = 0; k < K; ++k) sY += (Yn[(size_t)k * N + c] - Yc[k]) / p->M[k];
+    D += Mw * sY;
+    D -= (P0 - P0prev) / P0;
+
+    double r = rho[c], uc[3] = {0, 0, 0}, G[3] = {0, 0, 0}, F[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) uc[a] = u[(size_t)a * N + c];
+    for (int a = 0; a < dim; ++a) {
+      cellv vm, vp;
+      neighbour(p, phi, T, Y, p->Ts_field ? Ts : NULL, N, xyz, a, -1, &vm);
+      neighbour(p, phi, T, Y, p->Ts_field ? Ts : NULL, N, xyz, a, +1, &vp);
+      double rm = eos_rho(p, P0, mixture_Mw(p, vm.Y), vm.T);
+      double rp = eos_rho(p, P0, mixture_Mw(p, vp.Y), vp.T);
+      G[a] = CS2 * 0.5 * (rp - rm);
+      F[a] = p->Fb[a] - Kd[c] * uc[a];
+    }
+    double sg = 0;
+    for (int i = 0; i < L.Q; ++i) sg += gin[(size_t)i * N + c];
+    double Ph = sg + 0.5 * r * CS2 * D;
+    double geq[ORC_QMAX], xi[ORC_QMAX];
+    orc_equilibrium(dim, Ph, r, uc, geq);
+    orc_source(dim, r, G, uc, F, D, xi);
+    double tau = 0.5 + mu[c] / (r * CS2);
+    for (int i = 0; i < L.Q; ++i) {
+      double gi = gin[(size_t)i * N + c];
+      g[(size_t)i * N + c] = gi - (gi - geq[i]) / tau + (1.0 - 1.0 / (2.0 * tau)) * xi[i];
+    }
+    if (diag) {
+      for (int a = 0; a < dim; ++a) diag[(size_t)a * N + c] = uc[a];
+      diag[(size_t)dim * N + c] = r;
+      diag[(size_t)(dim + 1) * N + c] = Ph;
+      diag[(size_t)(dim + 2) * N + c] = D;
+    }
+  }
+
+  /* 6: global FP64 reduction -> P0^{n+1} */
+  double fin = 0, fout = 0;
+  if (p->bc[0] == ORC_BC_INLET || p->bc[1] == ORC_BC_OUTLET) {
+    for (int c = 0; c < N; ++c) {
+      int x = c % p->nx;
+      double f = (1.0 - phi[c]) * rho[c] * u[c];
+      if (x == 0 && p->bc[0] == ORC_BC_INLET) fin += f;
+      if (x == p->nx - 1 && p->bc[1] == ORC_BC_OUTLET) fout += f;
+    }
+  }
+  memcpy(T, Tn, sizeof(double) * N);
+  if (K > 0) memcpy(Y, Yn, sizeof(double) * (size_t)K * N);
+  if (p->Ts_field) memcpy(Ts, Tsn, sizeof(double) * N);
+  double I = reduce_I(p, phi, T, Y);
+  double m = scal[2];
+  double P0n = P0;
+  if (p->p0_mode != ORC_P0_FIXED) P0n = m * ORC_R * p->rho_ref / I;
+  scal[1] = P0;
+  scal[0] = P0n;
+  scal[2] = m;
+  scal[3] = I;
+  scal[4] = fin;
+  scal[5] = fout;
+  scal[6] += 1;
+
+  free(gin); free(u); free(rho); free(Kd); free(mu); free(Tn); free(Yn);
+  if (Tsn) free(Tsn);
+  return 0;
+}
+
+int orc_run(const orc_params* p, const double* phi, double* g, double* T, double* Y, double* Ts,
+            double* scal, int nsteps) {
+  for (int n = 0; n < nsteps; ++n) orc_step(p, phi, g, T, Y, Ts, scal, NULL);
+  return 0;
+}
+
+int orc_params_size(void) { return (int)sizeof(orc_params); }
