@@ -1,0 +1,210 @@
+/*
+ * pflb.h -- C ABI of the GB300 PF-LB-FD time-step library (libpflb.so).
+ *
+ * The library advances the low-Mach phase-field / lattice-Boltzmann /
+ * finite-difference model of Namdar, Norouzi & Varnik (arXiv 2310.17214) on
+ * one NVIDIA GB300 GPU (sm_103a):
+ *   (a) pull-scheme D2Q9 / D3Q19 collide-stream of the pressure-based
+ *       populations g_i (Sec. 3.3, eqs. pop-g, body-force, eq-pop-f, eq-pop-g)
+ *       with the diffuse-interface drag of Sec. 3.2.1 (eq. Fdrag-empirical-law)
+ *       and the velocity-divergence source of the low-Mach constraint;
+ *   (b) explicit finite-difference transport of T and Y_k (Sec. 3.2.2 eq.
+ *       volume-averaged-species-equation-5, Sec. 3.3 eq.
+ *       energy-transport-DI-version) with the heat coupling S_I (eq.
+ *       diffusion-heat-flux-3);
+ *   (c) the per-cell reaction source (Sec. 3.2.2 eq. 8, Sec. 3.3 eq. 9);
+ *   (d) the FP64 global reduction for the thermodynamic pressure P0
+ *       (Sec. 3.1, closure P0 = m R / int(Mw/T) dV).
+ *
+ * Conventions for every entry point:
+ *   - All functions return an int status (PFLB_OK = 0 or a negative code);
+ *     no exception crosses the ABI.  pflb_last_error() gives a message.
+ *   - "where" is PFLB_HOST or PFLB_DEVICE for the caller's buffer.  Device
+ *     buffers must live on the domain's device.  The library copies what it
+ *     needs; the caller keeps ownership of every buffer it passes.
+ *   - The library owns all device memory of a domain (allocated at create,
+ *     released at destroy).  Work is queued on the domain's CUDA stream
+ *     (desc.stream, NULL = the legacy default stream).
+ *   - Field layout: cell = x + nx*(y + ny*z) (x fastest); multi-component
+ *     fields are component-major (Y[k*N + cell], u[a*N + cell]).
+ *   - A handle is not thread-safe; use one stream per domain.
+ */
+#ifndef PFLB_H
+#define PFLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PFLB_OK 0
+#define PFLB_ERR_ARG -1
+#define PFLB_ERR_OOM -2
+#define PFLB_ERR_CUDA -3
+#define PFLB_ERR_STATE -4       /* calls made in the wrong order */
+#define PFLB_ERR_UNSTABLE -5    /* tau <= 1/2 or diffusion number too large at create; NaN at run */
+#define PFLB_ERR_TIMEOUT -6     /* a bounded device wait ran out */
+#define PFLB_ERR_UNSUPPORTED -7
+
+/* precision modes */
+#define PFLB_FP64 0             /* FP64 compute and storage */
+#define PFLB_FP32 1             /* FP32 compute and storage; P0 / mass reductions in FP64 */
+#define PFLB_FP32_FP16STORE 2   /* FP32 compute, populations stored as scaled FP16 */
+
+/* boundary kinds per face (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) */
+#define PFLB_BC_PERIODIC 0
+#define PFLB_BC_WALL 1          /* half-way bounce-back (optionally moving), T Dirichlet or adiabatic */
+#define PFLB_BC_INLET 2         /* x-lo only: moving-wall bounce-back with the inlet velocity, Dirichlet T, Y */
+#define PFLB_BC_OUTLET 3        /* x-hi only: anti-bounce-back P_h = 0, zero-gradient T, Y */
+
+/* thermodynamic-pressure closure */
+#define PFLB_P0_FIXED 0         /* open domain: P0 stays at its initial (ambient) value */
+#define PFLB_P0_CLOSED 1        /* closed domain: P0 = m R / sum(phi_f Mw / T) dV with m fixed */
+
+/* chemistry */
+#define PFLB_CHEM_NONE 0
+#define PFLB_CHEM_EXPLICIT 1    /* forward-Euler Arrhenius source */
+
+#define PFLB_HOST 0
+#define PFLB_DEVICE 1
+
+#define PFLB_KMAX 8
+#define PFLB_JMAX 4
+
+/* field selectors for set/get */
+#define PFLB_FIELD_T 1u         /* temperature (K), N values */
+#define PFLB_FIELD_Y 2u         /* mass fractions, K*N values */
+#define PFLB_FIELD_TS 4u        /* solid temperature (K), N values */
+#define PFLB_FIELD_U 8u         /* velocity (lattice units), dim*N values (get only) */
+#define PFLB_FIELD_RHO 16u      /* density / rho_ref, N values (get only) */
+#define PFLB_FIELD_PH 32u       /* sum of populations (lattice pressure), N values (get only) */
+#define PFLB_FIELD_G 64u        /* post-collision populations, Q*N values (get only) */
+
+#define PFLB_DTYPE_F64 0
+#define PFLB_DTYPE_F32 1
+
+typedef struct pflb_domain pflb_domain;
+
+/* Physical description of one domain.  Units are SI except where noted; with
+ * dx = dt = 1 and rho_ref = 1 every quantity is read in lattice units. */
+typedef struct pflb_domain_desc {
+  int dim;                 /* 2 -> D2Q9, 3 -> D3Q19 */
+  int nx, ny, nz;          /* nz ignored (1) for dim == 2 */
+  int precision;           /* PFLB_FP64 / PFLB_FP32 / PFLB_FP32_FP16STORE */
+  int bc[6];
+  double wall_u[6][3];     /* wall velocity per face (lattice units) */
+  double wall_T[6];        /* wall temperature per face (K); 0 = adiabatic */
+  double dx, dt, rho_ref;  /* grid spacing (m), time step (s), reference density (kg/m^3) */
+  double M0, cp0;          /* single-gas molar mass (kg/mol), heat capacity (J/kg/K) when K = 0 */
+  double mu_ref;           /* dynamic viscosity (Pa s); Sutherland reference value if enabled */
+  int sutherland;          /* 1: mu(T) = mu_ref (T/suth_T)^1.5 (suth_T + suth_S)/(T + suth_S) */
+  double suth_T, suth_S;
+  double Pr;               /* Prandtl number: lambda = mu cp / Pr */
+  double A_u, A_T, eta;    /* coupling parameters, interface width (cells) */
+  double Fb[3];            /* body-force density (lattice units) */
+  int inlet_parabolic;     /* inlet profile: 0 uniform, 1 parabola across wall-bounded axes */
+  double u_in, T_in;       /* inlet peak velocity (lattice units), temperature (K) */
+  int p0_mode;             /* PFLB_P0_FIXED / PFLB_P0_CLOSED */
+  double P0;               /* initial thermodynamic pressure (Pa) */
+  int Ts_field;            /* 0: solid at the uniform Ts_uniform; 1: transported solid temperature */
+  double Ts_uniform;       /* K */
+  double rhocp_s, lambda_s;/* solid volumetric heat capacity (J/m^3/K), conductivity (W/m/K) */
+  double phi_min;          /* phase fraction below which a phase is frozen (e.g. 1e-6) */
+  void* stream;            /* cudaStream_t (NULL = legacy default stream) */
+  int device;              /* CUDA device ordinal */
+} pflb_domain_desc;
+
+/* Species thermochemistry and reactions (Sec. 3.2.2 eq. 8, Sec. 3.3 eq. 9).
+ * Q_j = A_j T^b_j exp(-EaR_j / T) prod_k C_k^order_jk, C_k = rho Y_k / M_k. */
+typedef struct pflb_mechanism {
+  int K;                   /* species (0, 5 or 6 are compiled) */
+  int J;                   /* reactions, <= PFLB_JMAX */
+  int chem_mode;           /* PFLB_CHEM_NONE / PFLB_CHEM_EXPLICIT */
+  double M[PFLB_KMAX];     /* kg/mol */
+  double cp[PFLB_KMAX];    /* J/kg/K (constant) */
+  double hf[PFLB_KMAX];    /* formation enthalpy, J/kg */
+  double Dref[PFLB_KMAX];  /* m^2/s at D_Tref */
+  double D_Tref, D_exp;    /* D_k = Dref_k (T / D_Tref)^D_exp */
+  double Y_in[PFLB_KMAX];  /* inlet composition */
+  double A[PFLB_JMAX], b[PFLB_JMAX], EaR[PFLB_JMAX];
+  double order[PFLB_JMAX][PFLB_KMAX];
+  double stoich[PFLB_JMAX][PFLB_KMAX];
+} pflb_mechanism;
+
+typedef struct pflb_scalars {
+  double P0;               /* thermodynamic pressure at the current step (Pa) */
+  double P0_prev;          /* at the previous step */
+  double mass;             /* fluid mass used by the closure (lattice units) */
+  double I;                /* sum phi_f Mw / T over the domain */
+  double flux_in, flux_out;/* inlet / outlet mass flux of the last step (lattice units) */
+  long long step;          /* steps taken */
+  int status;              /* latched device status (PFLB_OK or PFLB_ERR_UNSTABLE) */
+} pflb_scalars;
+
+/* Create a domain: validates the description (tau > 1/2 at T_in, bc pairing),
+ * allocates every device array (populations double-buffered for the pull
+ * scheme).  Errors: PFLB_ERR_ARG, PFLB_ERR_UNSUPPORTED, PFLB_ERR_OOM,
+ * PFLB_ERR_CUDA.  On error *out is NULL. */
+int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out);
+
+/* Static solid fraction phi_s in [0, 1] (N values, sum of phase fractions
+ * is one, Sec. 2 eq. sum-varphialpha) and, when Ts_field, the initial solid
+ * temperature (N values; NULL = Ts_uniform everywhere).  dtype: F64/F32. */
+int pflb_set_phase_field(pflb_domain* d, const void* phi_s, const void* Ts, int dtype, int where);
+
+/* Species data and reactions; must precede pflb_set_fields when K > 0.
+ * K must be one of the compiled species counts (0, 5, 6). */
+int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m);
+
+/* Initial T (and Y when K > 0; optional velocity u, dim*N values, NULL = rest).
+ * Sets g = g_eq(P_h = 0, rho, u), P0 = desc.P0 and the closure mass m.
+ * mask selects the fields present in the packed buffer `src` (T, then Y,
+ * then u), dtype F64/F32. */
+int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, int where);
+
+/* Advance nsteps time steps asynchronously on the domain's stream.  A NaN
+ * or an instability latches PFLB_ERR_UNSTABLE in the device status word;
+ * it is returned by the next synchronising call (get_fields/get_scalars). */
+int pflb_step(pflb_domain* d, int nsteps);
+
+/* Copy fields out, packed in the order T, Y, Ts, U, RHO, PH, G of the mask
+ * bits.  U, RHO and PH are the moments the next step will see (pull and
+ * boundary rules applied, no collision).  Synchronises the stream. */
+int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int dtype, int where);
+
+/* Host copy of the scalar state; synchronises the stream. */
+int pflb_get_scalars(pflb_domain* d, pflb_scalars* out);
+
+/* Size in bytes of a serialised state of this domain (header, scalars,
+ * populations in their storage precision, T, Y, Ts). */
+int pflb_state_bytes(const pflb_domain* d, size_t* bytes);
+
+/* Serialise the complete time-step state (checkpoint) into dst (host or
+ * device memory of at least pflb_state_bytes).  Restoring it with
+ * pflb_set_state and stepping reproduces an uninterrupted run bit for bit
+ * (the reductions are deterministic).  Synchronises the stream. */
+int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where);
+
+/* Restore a state written by pflb_get_state for a domain of the same shape,
+ * precision and species count (checked against the header; PFLB_ERR_ARG on
+ * mismatch).  Requires set_phase_field and set_fields to have run once.
+ * Asynchronous on the domain's stream. */
+int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
+
+/* Number of populations Q and the lattice velocities (3*Q ints) and
+ * weights (Q doubles) in the library's storage order. */
+int pflb_lattice(int dim, int* c_out, double* w_out);
+
+/* Release every device allocation of the domain. */
+int pflb_destroy(pflb_domain* d);
+
+/* Last error message of this domain (or of the last failed create when d is
+ * NULL).  The string lives until the next call on the same handle. */
+const char* pflb_last_error(const pflb_domain* d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFLB_H */

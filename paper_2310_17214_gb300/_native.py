@@ -1,0 +1,290 @@
+"""ctypes binding of libpflb.so (include/pflb.h).  Argument marshalling only:
+every step of the time-step path runs in the library's CUDA kernels.  There is
+no CPU fallback: if the library cannot be loaded this module raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KMAX, JMAX = 8, 4
+BC = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_fp16": 2}
+P0MODE = {"fixed": 0, "closed": 1}
+CHEM = {"none": 0, "explicit": 1}
+FIELD = {"T": 1, "Y": 2, "Ts": 4, "u": 8, "rho": 16, "Ph": 32, "g": 64}
+FIELD_ORDER = ["T", "Y", "Ts", "u", "rho", "Ph", "g"]
+HOST, DEVICE = 0, 1
+F64, F32 = 0, 1
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("precision", C.c_int), ("bc", C.c_int * 6),
+        ("wall_u", (C.c_double * 3) * 6), ("wall_T", C.c_double * 6),
+        ("dx", C.c_double), ("dt", C.c_double), ("rho_ref", C.c_double),
+        ("M0", C.c_double), ("cp0", C.c_double),
+        ("mu_ref", C.c_double), ("sutherland", C.c_int),
+        ("suth_T", C.c_double), ("suth_S", C.c_double), ("Pr", C.c_double),
+        ("A_u", C.c_double), ("A_T", C.c_double), ("eta", C.c_double),
+        ("Fb", C.c_double * 3),
+        ("inlet_parabolic", C.c_int), ("u_in", C.c_double), ("T_in", C.c_double),
+        ("p0_mode", C.c_int), ("P0", C.c_double),
+        ("Ts_field", C.c_int), ("Ts_uniform", C.c_double),
+        ("rhocp_s", C.c_double), ("lambda_s", C.c_double), ("phi_min", C.c_double),
+        ("stream", C.c_void_p), ("device", C.c_int),
+    ]
+
+
+class Mechanism(C.Structure):
+    _fields_ = [
+        ("K", C.c_int), ("J", C.c_int), ("chem_mode", C.c_int),
+        ("M", C.c_double * KMAX), ("cp", C.c_double * KMAX), ("hf", C.c_double * KMAX),
+        ("Dref", C.c_double * KMAX), ("D_Tref", C.c_double), ("D_exp", C.c_double),
+        ("Y_in", C.c_double * KMAX),
+        ("A", C.c_double * JMAX), ("b", C.c_double * JMAX), ("EaR", C.c_double * JMAX),
+        ("order", (C.c_double * KMAX) * JMAX), ("stoich", (C.c_double * KMAX) * JMAX),
+    ]
+
+
+class Scalars(C.Structure):
+    _fields_ = [("P0", C.c_double), ("P0_prev", C.c_double), ("mass", C.c_double),
+                ("I", C.c_double), ("flux_in", C.c_double), ("flux_out", C.c_double),
+                ("step", C.c_longlong), ("status", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpflb.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libpflb.so is missing; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp = C.c_void_p
+        L.pflb_create_domain.argtypes = [C.POINTER(Desc), C.POINTER(vp)]
+        L.pflb_set_phase_field.argtypes = [vp, vp, vp, C.c_int, C.c_int]
+        L.pflb_set_mechanism.argtypes = [vp, C.POINTER(Mechanism)]
+        L.pflb_set_fields.argtypes = [vp, C.c_uint, vp, C.c_int, C.c_int]
+        L.pflb_step.argtypes = [vp, C.c_int]
+        L.pflb_get_fields.argtypes = [vp, C.c_uint, vp, C.c_size_t, C.c_int, C.c_int]
+        L.pflb_get_scalars.argtypes = [vp, C.POINTER(Scalars)]
+        L.pflb_lattice.argtypes = [C.c_int, vp, vp]
+        L.pflb_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.pflb_get_state.argtypes = [vp, vp, C.c_size_t, C.c_int]
+        L.pflb_set_state.argtypes = [vp, vp, C.c_size_t, C.c_int]
+        L.pflb_destroy.argtypes = [vp]
+        L.pflb_last_error.argtypes = [vp]
+        L.pflb_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class PflbError(RuntimeError):
+    pass
+
+
+def _check(rc, handle=None):
+    if rc != 0:
+        msg = lib().pflb_last_error(handle)
+        raise PflbError(f"pflb error {rc}: {msg.decode() if msg else ''}")
+
+
+def make_desc(prob: dict, precision: str = "fp64", stream: int = 0, device: int = 0) -> Desc:
+    d = Desc()
+    d.dim, d.nx, d.ny = prob["dim"], prob["nx"], prob["ny"]
+    d.nz = prob.get("nz", 1) if d.dim == 3 else 1
+    d.precision = PRECISION[precision]
+    for f, name in enumerate(prob["bc"]):
+        d.bc[f] = BC[name]
+    for f, v in enumerate(prob.get("wall_u", [[0, 0, 0]] * 6)):
+        for a in range(3):
+            d.wall_u[f][a] = v[a]
+    for f, v in enumerate(prob.get("wall_T", [0.0] * 6)):
+        d.wall_T[f] = v
+    d.dx, d.dt, d.rho_ref = prob["dx"], prob["dt"], prob["rho_ref"]
+    d.M0, d.cp0 = prob.get("M0", 0.02897), prob.get("cp0", 1006.0)
+    d.mu_ref, d.sutherland = prob["mu_ref"], int(prob.get("sutherland", 0))
+    d.suth_T, d.suth_S, d.Pr = prob.get("suth_T", 273.0), prob.get("suth_S", 110.5), prob["Pr"]
+    d.A_u, d.A_T, d.eta = prob["A_u"], prob["A_T"], prob["eta"]
+    for a, v in enumerate(prob.get("Fb", [0, 0, 0])):
+        d.Fb[a] = v
+    d.inlet_parabolic = int(prob.get("inlet_parabolic", 0))
+    d.u_in, d.T_in = prob.get("u_in", 0.0), prob.get("T_in", 300.0)
+    d.p0_mode = P0MODE[prob.get("p0_mode", "fixed")]
+    d.P0 = prob["P0"]
+    d.Ts_field = int(prob.get("Ts_field", 0))
+    d.Ts_uniform = prob.get("Ts_uniform", 300.0)
+    d.rhocp_s, d.lambda_s = prob.get("rhocp_s", 1.0), prob.get("lambda_s", 0.0)
+    d.phi_min = prob.get("phi_min", 1e-6)
+    d.stream = stream
+    d.device = device
+    return d
+
+
+def make_mechanism(prob: dict) -> Mechanism:
+    m = Mechanism()
+    K = prob.get("K", 0)
+    m.K = K
+    rx = prob.get("reactions", []) if K else []
+    m.J = len(rx)
+    m.chem_mode = CHEM[prob.get("chem", "none")] if K else 0
+    for k in range(K):
+        m.M[k], m.cp[k], m.hf[k] = prob["M"][k], prob["cp"][k], prob["hf"][k]
+        m.Dref[k], m.Y_in[k] = prob["Dref"][k], prob["Y_in"][k]
+    m.D_Tref, m.D_exp = prob.get("D_Tref", 300.0), prob.get("D_exp", 0.0)
+    for j, r in enumerate(rx):
+        m.A[j], m.b[j], m.EaR[j] = r["A"], r.get("b", 0.0), r["EaR"]
+        for k in range(K):
+            m.order[j][k] = r["order"][k]
+            m.stoich[j][k] = r["stoich"][k]
+    return m
+
+
+def lattice(dim):
+    c = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19)
+    Q = lib().pflb_lattice(dim, c.ctypes.data, w.ctypes.data)
+    return c.reshape(19, 3)[:Q].copy(), w[:Q].copy()
+
+
+def _arg(a, dtype):
+    """(pointer, where, dtype code, keepalive) for a numpy array or torch tensor."""
+    code = F64 if dtype == np.float64 else F32
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        t = a.contiguous().to(torch.float64 if code == F64 else torch.float32)
+        return t.data_ptr(), (DEVICE if t.is_cuda else HOST), code, t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, HOST, code, arr
+
+
+class Domain:
+    """One simulation domain living on one GPU (handle of the C ABI)."""
+
+    def __init__(self, prob: dict, precision: str = "fp64", stream: int = 0, device: int = 0):
+        self.prob = prob
+        self.precision = precision
+        self.dim = prob["dim"]
+        self.N = prob["nx"] * prob["ny"] * (prob.get("nz", 1) if self.dim == 3 else 1)
+        self.Q = 9 if self.dim == 2 else 19
+        self.K = prob.get("K", 0)
+        self._h = C.c_void_p()
+        self._desc = make_desc(prob, precision, stream, device)
+        _check(lib().pflb_create_domain(C.byref(self._desc), C.byref(self._h)), None)
+        if self.K:
+            self._mech = make_mechanism(prob)
+            _check(lib().pflb_set_mechanism(self._h, C.byref(self._mech)), self._h)
+
+    def set_phase_field(self, phi, Ts=None, dtype=np.float64):
+        p, where, code, k1 = _arg(phi, dtype)
+        ts = None
+        if Ts is not None:
+            ts, where2, _, k2 = _arg(Ts, dtype)
+            assert where2 == where, "phi and Ts must live on the same side"
+        _check(lib().pflb_set_phase_field(self._h, p, ts, code, where), self._h)
+
+    def set_fields(self, T, Y=None, u=None, dtype=np.float64):
+        parts, mask = [T], FIELD["T"]
+        if self.K:
+            parts.append(Y)
+            mask |= FIELD["Y"]
+        if u is not None:
+            parts.append(u)
+            mask |= FIELD["u"]
+        if hasattr(T, "data_ptr"):
+            import torch
+            buf = torch.cat([torch.as_tensor(x).reshape(-1) for x in parts])
+        else:
+            buf = np.concatenate([np.asarray(x, dtype=dtype).reshape(-1) for x in parts])
+        p, where, code, keep = _arg(buf, dtype)
+        _check(lib().pflb_set_fields(self._h, mask, p, code, where), self._h)
+
+    def step(self, n: int = 1):
+        _check(lib().pflb_step(self._h, int(n)), self._h)
+
+    def _sizes(self):
+        return {"T": self.N, "Y": self.K * self.N, "Ts": self.N, "u": self.dim * self.N,
+                "rho": self.N, "Ph": self.N, "g": self.Q * self.N}
+
+    def get(self, *names, dtype=np.float64, out=None):
+        """Fields as numpy arrays (host), or written into a packed device tensor `out`."""
+        mask = 0
+        for n in names:
+            mask |= FIELD[n]
+        sizes = self._sizes()
+        order = [n for n in FIELD_ORDER if mask & FIELD[n]]
+        total = sum(sizes[n] for n in order)
+        if out is not None:
+            p, where, code, keep = _arg(out, dtype)
+            _check(lib().pflb_get_fields(self._h, mask, out.data_ptr(), out.numel() *
+                                         out.element_size(), code, DEVICE), self._h)
+            return out
+        buf = np.empty(total, dtype=dtype)
+        code = F64 if dtype == np.float64 else F32
+        _check(lib().pflb_get_fields(self._h, mask, buf.ctypes.data, buf.nbytes, code, HOST),
+               self._h)
+        res, off = {}, 0
+        for n in order:
+            res[n] = buf[off:off + sizes[n]]
+            off += sizes[n]
+        if "u" in res:
+            res["u"] = res["u"].reshape(self.dim, self.N)
+        if "Y" in res:
+            res["Y"] = res["Y"].reshape(self.K, self.N)
+        if "g" in res:
+            res["g"] = res["g"].reshape(self.Q, self.N)
+        return res if len(names) > 1 else res[names[0]]
+
+    def scalars(self) -> dict:
+        s = Scalars()
+        _check(lib().pflb_get_scalars(self._h, C.byref(s)), self._h)
+        return {f: getattr(s, f) for f, _ in Scalars._fields_}
+
+    def state_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(lib().pflb_state_bytes(self._h, C.byref(n)), self._h)
+        return n.value
+
+    def get_state(self, out=None):
+        """Serialised checkpoint into `out` (uint8 numpy array or torch tensor,
+        host or device) or a new host numpy array."""
+        nb = self.state_bytes()
+        if out is None:
+            out = np.empty(nb, dtype=np.uint8)
+        if hasattr(out, "data_ptr"):
+            where = DEVICE if out.is_cuda else HOST
+            ptr, size = out.data_ptr(), out.numel() * out.element_size()
+        else:
+            where, ptr, size = HOST, out.ctypes.data, out.nbytes
+        _check(lib().pflb_get_state(self._h, ptr, size, where), self._h)
+        return out
+
+    def set_state(self, buf):
+        if hasattr(buf, "data_ptr"):
+            where = DEVICE if buf.is_cuda else HOST
+            ptr, size = buf.data_ptr(), buf.numel() * buf.element_size()
+        else:
+            buf = np.ascontiguousarray(buf)
+            where, ptr, size = HOST, buf.ctypes.data, buf.nbytes
+        _check(lib().pflb_set_state(self._h, ptr, size, where), self._h)
+
+    def close(self):
+        if self._h:
+            lib().pflb_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

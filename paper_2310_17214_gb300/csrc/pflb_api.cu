@@ -1,0 +1,532 @@
+// pflb_api.cu -- the extern "C" boundary of libpflb.so (declared in
+// include/pflb.h): domain lifetime, field transfer, stepping, scalars.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/pflb.h"
+#include "pflb_launch.cuh"
+
+using namespace pflb;
+
+struct pflb_domain {
+  pflb_domain_desc desc;
+  pflb_mechanism mech;
+  int K = 0, Q = 0, N = 0, mode = 0, dim = 2;
+  size_t real_sz = 8, store_sz = 8;
+  cudaStream_t stream = nullptr;
+  Buffers B;
+  int cur = 0;
+  bool has_mech = false, has_phase = false, has_fields = false;
+  Launcher* L = nullptr;
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+int fail(pflb_domain* d, int code, const char* fmt, const char* a = "") {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), fmt, a);
+  if (d) d->err = buf;
+  else g_create_err = buf;
+  return code;
+}
+
+#define CK(d, call)                                                     \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return fail(d, PFLB_ERR_CUDA, "%s", cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class S, class D>
+__global__ void convert_kernel(const S* __restrict__ s, D* __restrict__ d, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    d[i] = D(s[i]);
+}
+
+struct Weights { float w_over_scale[19]; int Q; };
+
+template <class Store, class D>
+__global__ void decode_g_kernel(const Store* __restrict__ s, D* __restrict__ d, size_t N,
+                                Weights W) {
+  const size_t n = N * (size_t)W.Q;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(Store) == 2) d[i] = D(__half2float(s[i]) * W.w_over_scale[i / N]);
+    else d[i] = D(s[i]);
+  }
+}
+
+template <class D>
+__global__ void fill_kernel(D* __restrict__ d, D v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    d[i] = v;
+}
+
+template <class S, class D>
+cudaError_t convert(const void* s, void* d, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  convert_kernel<S, D><<<blocks, 256, 0, st>>>(static_cast<const S*>(s), static_cast<D*>(d), n);
+  return cudaGetLastError();
+}
+
+// copy n values of dtype `dt` at `src` (host or device) into the compute-type
+// device array `dst` (double or float)
+int upload(pflb_domain* d, const void* src, int dt, int where, void* dst, size_t n) {
+  const size_t esz = dt == PFLB_DTYPE_F64 ? 8 : 4;
+  const void* dev = src;
+  void* stage = nullptr;
+  if (where == PFLB_HOST) {
+    CK(d, cudaMallocAsync(&stage, n * esz, d->stream));
+    CK(d, cudaMemcpyAsync(stage, src, n * esz, cudaMemcpyHostToDevice, d->stream));
+    dev = stage;
+  }
+  cudaError_t e;
+  if (d->real_sz == 8) e = dt == PFLB_DTYPE_F64 ? convert<double, double>(dev, dst, n, d->stream)
+                                                : convert<float, double>(dev, dst, n, d->stream);
+  else e = dt == PFLB_DTYPE_F64 ? convert<double, float>(dev, dst, n, d->stream)
+                                : convert<float, float>(dev, dst, n, d->stream);
+  if (stage) cudaFreeAsync(stage, d->stream);
+  CK(d, e);
+  return PFLB_OK;
+}
+
+int check_dtype_where(pflb_domain* d, int dt, int where) {
+  if (dt != PFLB_DTYPE_F64 && dt != PFLB_DTYPE_F32) return fail(d, PFLB_ERR_ARG, "bad dtype");
+  if (where != PFLB_HOST && where != PFLB_DEVICE) return fail(d, PFLB_ERR_ARG, "bad where");
+  return PFLB_OK;
+}
+
+Launcher* make_launcher(const pflb_domain* d) {
+  const int K = d->K, m = d->mode;
+  if (d->dim == 2) {
+    if (m == MODE_FP64) return make_launcher_2d_fp64(K, d->desc, d->mech);
+    if (m == MODE_FP32) return make_launcher_2d_fp32(K, d->desc, d->mech);
+    return make_launcher_2d_fp16(K, d->desc, d->mech);
+  }
+  if (m == MODE_FP64) return make_launcher_3d_fp64(K, d->desc, d->mech);
+  if (m == MODE_FP32) return make_launcher_3d_fp32(K, d->desc, d->mech);
+  return make_launcher_3d_fp16(K, d->desc, d->mech);
+}
+
+void free_buffers(pflb_domain* d) {
+  void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
+                  d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  std::memset(&d->B, 0, sizeof(d->B));
+}
+
+}  // namespace
+
+extern "C" {
+
+int pflb_lattice(int dim, int* c_out, double* w_out) {
+  if (dim == 2) {
+    for (int i = 0; i < 9; ++i) {
+      for (int a = 0; a < 3; ++a) c_out[3 * i + a] = Lattice<2>::c(i, a);
+      w_out[i] = Lattice<2>::w(i);
+    }
+    return 9;
+  }
+  if (dim == 3) {
+    for (int i = 0; i < 19; ++i) {
+      for (int a = 0; a < 3; ++a) c_out[3 * i + a] = Lattice<3>::c(i, a);
+      w_out[i] = Lattice<3>::w(i);
+    }
+    return 19;
+  }
+  return PFLB_ERR_ARG;
+}
+
+const char* pflb_last_error(const pflb_domain* d) {
+  return d ? d->err.c_str() : g_create_err.c_str();
+}
+
+int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
+  if (!out) return fail(nullptr, PFLB_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(nullptr, PFLB_ERR_ARG, "desc is NULL");
+  const pflb_domain_desc& D = *desc;
+  if (D.dim != 2 && D.dim != 3) return fail(nullptr, PFLB_ERR_UNSUPPORTED, "dim must be 2 or 3");
+  if (D.nx < 2 || D.ny < 1 || (D.dim == 3 && D.nz < 1))
+    return fail(nullptr, PFLB_ERR_ARG, "bad lattice extent");
+  const long long N = (long long)D.nx * D.ny * (D.dim == 3 ? D.nz : 1);
+  if (N > (1LL << 31) / 32) return fail(nullptr, PFLB_ERR_ARG, "lattice too large for int indexing");
+  if (D.precision < PFLB_FP64 || D.precision > PFLB_FP32_FP16STORE)
+    return fail(nullptr, PFLB_ERR_ARG, "bad precision");
+  for (int a = 0; a < D.dim; ++a) {
+    int lo = D.bc[2 * a], hi = D.bc[2 * a + 1];
+    if ((lo == PFLB_BC_PERIODIC) != (hi == PFLB_BC_PERIODIC))
+      return fail(nullptr, PFLB_ERR_ARG, "periodic faces must come in pairs");
+    if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return fail(nullptr, PFLB_ERR_ARG, "bad bc kind");
+    if ((lo == PFLB_BC_INLET && a != 0) || (hi == PFLB_BC_OUTLET && a != 0) ||
+        lo == PFLB_BC_OUTLET || hi == PFLB_BC_INLET)
+      return fail(nullptr, PFLB_ERR_ARG, "inlet only at x-lo, outlet only at x-hi");
+  }
+  if (!(D.dx > 0 && D.dt > 0 && D.rho_ref > 0 && D.Pr > 0 && D.eta > 0 && D.P0 > 0 &&
+        D.mu_ref > 0))
+    return fail(nullptr, PFLB_ERR_ARG, "dx, dt, rho_ref, Pr, eta, P0, mu_ref must be positive");
+  if (D.p0_mode != PFLB_P0_FIXED && D.p0_mode != PFLB_P0_CLOSED)
+    return fail(nullptr, PFLB_ERR_ARG, "bad p0_mode");
+  if (D.Ts_field && !(D.rhocp_s > 0)) return fail(nullptr, PFLB_ERR_ARG, "rhocp_s must be > 0");
+
+  pflb_domain* d = new (std::nothrow) pflb_domain();
+  if (!d) return fail(nullptr, PFLB_ERR_OOM, "host allocation failed");
+  d->desc = D;
+  if (d->desc.dim == 2) d->desc.nz = 1;
+  std::memset(&d->mech, 0, sizeof(d->mech));
+  std::memset(&d->B, 0, sizeof(d->B));
+  d->dim = D.dim;
+  d->Q = D.dim == 2 ? 9 : 19;
+  d->N = (int)N;
+  d->B.N = (int)N;
+  d->mode = D.precision == PFLB_FP64 ? MODE_FP64 : (D.precision == PFLB_FP32 ? MODE_FP32 : MODE_FP16);
+  d->real_sz = d->mode == MODE_FP64 ? 8 : 4;
+  d->store_sz = d->mode == MODE_FP64 ? 8 : (d->mode == MODE_FP32 ? 4 : 2);
+  d->stream = static_cast<cudaStream_t>(D.stream);
+  cudaError_t e = cudaSetDevice(D.device);
+  if (e != cudaSuccess) {
+    delete d;
+    return fail(nullptr, PFLB_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  const size_t n = (size_t)N;
+  const int blocks = (int)((N + BLOCK - 1) / BLOCK);
+  bool ok = true;
+  auto al = [&](void** p, size_t bytes) {
+    if (!ok) return;
+    if (cudaMalloc(p, bytes) != cudaSuccess) { ok = false; *p = nullptr; }
+    else cudaMemset(*p, 0, bytes);
+  };
+  for (int b = 0; b < 2; ++b) {
+    al(&d->B.g[b], n * d->Q * d->store_sz);
+    al(&d->B.T[b], n * d->real_sz);
+    if (D.Ts_field) al(&d->B.Ts[b], n * d->real_sz);
+  }
+  al(&d->B.phi, n * d->real_sz);
+  al((void**)&d->B.scal, sizeof(DevScalars));
+  al((void**)&d->B.partials, (size_t)blocks * 4 * sizeof(double));
+  al((void**)&d->B.counter, sizeof(unsigned));
+  if (!ok) {
+    cudaGetLastError();
+    free_buffers(d);
+    delete d;
+    return fail(nullptr, PFLB_ERR_OOM, "device allocation failed");
+  }
+  *out = d;
+  return PFLB_OK;
+}
+
+int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
+  if (!d || !m) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  if (m->K != 0 && m->K != 5 && m->K != 6)
+    return fail(d, PFLB_ERR_UNSUPPORTED, "species count must be 0, 5 or 6");
+  if (m->J < 0 || m->J > PFLB_JMAX) return fail(d, PFLB_ERR_ARG, "bad reaction count");
+  if (m->chem_mode != PFLB_CHEM_NONE && m->chem_mode != PFLB_CHEM_EXPLICIT)
+    return fail(d, PFLB_ERR_UNSUPPORTED, "chem_mode");
+  for (int k = 0; k < m->K; ++k)
+    if (!(m->M[k] > 0 && m->cp[k] > 0 && m->Dref[k] >= 0))
+      return fail(d, PFLB_ERR_ARG, "species data must be positive");
+  if (d->has_fields) return fail(d, PFLB_ERR_STATE, "set_mechanism must precede set_fields");
+  cudaSetDevice(d->desc.device);
+  const size_t n = (size_t)d->N;
+  for (int b = 0; b < 2; ++b) {
+    if (d->B.Y[b]) { cudaFree(d->B.Y[b]); d->B.Y[b] = nullptr; }
+    if (m->K > 0 && cudaMalloc(&d->B.Y[b], n * m->K * d->real_sz) != cudaSuccess)
+      return fail(d, PFLB_ERR_OOM, "device allocation failed");
+  }
+  d->mech = *m;
+  d->K = m->K;
+  d->has_mech = true;
+  return PFLB_OK;
+}
+
+int pflb_set_phase_field(pflb_domain* d, const void* phi, const void* Ts, int dtype, int where) {
+  if (!d || !phi) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  int r = check_dtype_where(d, dtype, where);
+  if (r) return r;
+  CK(d, cudaSetDevice(d->desc.device));
+  if ((r = upload(d, phi, dtype, where, d->B.phi, d->N))) return r;
+  if (d->desc.Ts_field) {
+    if (Ts) {
+      if ((r = upload(d, Ts, dtype, where, d->B.Ts[d->cur], d->N))) return r;
+    } else {
+      const int blocks = (d->N + 255) / 256 > 4096 ? 4096 : (d->N + 255) / 256;
+      if (d->real_sz == 8)
+        fill_kernel<double><<<blocks, 256, 0, d->stream>>>((double*)d->B.Ts[d->cur],
+                                                           d->desc.Ts_uniform, d->N);
+      else
+        fill_kernel<float><<<blocks, 256, 0, d->stream>>>((float*)d->B.Ts[d->cur],
+                                                          (float)d->desc.Ts_uniform, d->N);
+      CK(d, cudaGetLastError());
+    }
+  }
+  d->has_phase = true;
+  return PFLB_OK;
+}
+
+int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, int where) {
+  if (!d || !src) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  int r = check_dtype_where(d, dtype, where);
+  if (r) return r;
+  if (!d->has_phase) return fail(d, PFLB_ERR_STATE, "set_phase_field must come first");
+  if (!(mask & PFLB_FIELD_T)) return fail(d, PFLB_ERR_ARG, "T is required");
+  if (d->K > 0 && !(mask & PFLB_FIELD_Y)) return fail(d, PFLB_ERR_ARG, "Y is required when K > 0");
+  if (mask & ~(PFLB_FIELD_T | PFLB_FIELD_Y | PFLB_FIELD_U))
+    return fail(d, PFLB_ERR_ARG, "set_fields accepts T, Y, U only");
+  CK(d, cudaSetDevice(d->desc.device));
+  const size_t esz = dtype == PFLB_DTYPE_F64 ? 8 : 4;
+  const char* p = static_cast<const char*>(src);
+  const size_t n = (size_t)d->N;
+  if ((r = upload(d, p, dtype, where, d->B.T[d->cur], n))) return r;
+  p += n * esz;
+  if (d->K > 0) {
+    if ((r = upload(d, p, dtype, where, d->B.Y[d->cur], n * d->K))) return r;
+    p += n * d->K * esz;
+  }
+  void* u = nullptr;
+  if (mask & PFLB_FIELD_U) {
+    CK(d, cudaMallocAsync(&u, n * d->dim * d->real_sz, d->stream));
+    if ((r = upload(d, p, dtype, where, u, n * d->dim))) { cudaFreeAsync(u, d->stream); return r; }
+  }
+  delete d->L;
+  d->L = make_launcher(d);
+  if (!d->L) return fail(d, PFLB_ERR_UNSUPPORTED, "no kernel compiled for this combination");
+  cudaError_t e = d->L->init(d->B, d->cur, u, d->desc.P0, d->stream);
+  if (u) cudaFreeAsync(u, d->stream);
+  CK(d, e);
+  d->has_fields = true;
+  return PFLB_OK;
+}
+
+int pflb_step(pflb_domain* d, int nsteps) {
+  if (!d) return fail(d, PFLB_ERR_ARG, "NULL domain");
+  if (!d->has_fields || !d->L) return fail(d, PFLB_ERR_STATE, "set_fields must come first");
+  if (nsteps < 0) return fail(d, PFLB_ERR_ARG, "nsteps < 0");
+  CK(d, cudaSetDevice(d->desc.device));
+  CK(d, d->L->step(d->B, d->cur, nsteps, d->stream));
+  return PFLB_OK;
+}
+
+int pflb_get_scalars(pflb_domain* d, pflb_scalars* out) {
+  if (!d || !out) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  CK(d, cudaSetDevice(d->desc.device));
+  DevScalars h;
+  CK(d, cudaMemcpyAsync(&h, d->B.scal, sizeof(h), cudaMemcpyDeviceToHost, d->stream));
+  CK(d, cudaStreamSynchronize(d->stream));
+  out->P0 = h.P0;
+  out->P0_prev = h.P0_prev;
+  out->mass = h.mass;
+  out->I = h.I;
+  out->flux_in = h.flux_in;
+  out->flux_out = h.flux_out;
+  out->step = h.step;
+  out->status = h.status;
+  if (h.status != 0) return fail(d, h.status, "instability (NaN or non-positive temperature sum)");
+  return PFLB_OK;
+}
+
+int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int dtype, int where) {
+  if (!d || !dst) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  int r = check_dtype_where(d, dtype, where);
+  if (r) return r;
+  if (!d->has_fields) return fail(d, PFLB_ERR_STATE, "no fields yet");
+  if ((mask & PFLB_FIELD_TS) && !d->desc.Ts_field)
+    return fail(d, PFLB_ERR_ARG, "no solid temperature field");
+  if ((mask & PFLB_FIELD_Y) && d->K == 0) return fail(d, PFLB_ERR_ARG, "no species");
+  const size_t n = (size_t)d->N, esz = dtype == PFLB_DTYPE_F64 ? 8 : 4;
+  size_t need = 0;
+  if (mask & PFLB_FIELD_T) need += n;
+  if (mask & PFLB_FIELD_Y) need += n * d->K;
+  if (mask & PFLB_FIELD_TS) need += n;
+  if (mask & PFLB_FIELD_U) need += n * d->dim;
+  if (mask & PFLB_FIELD_RHO) need += n;
+  if (mask & PFLB_FIELD_PH) need += n;
+  if (mask & PFLB_FIELD_G) need += n * d->Q;
+  if (bytes < need * esz) return fail(d, PFLB_ERR_ARG, "destination too small");
+  CK(d, cudaSetDevice(d->desc.device));
+  char* out = nullptr;
+  if (where == PFLB_HOST) CK(d, cudaMallocAsync((void**)&out, need * esz, d->stream));
+  else out = static_cast<char*>(dst);
+  char* p = out;
+  auto put_real = [&](const void* srcp, size_t cnt) -> cudaError_t {
+    cudaError_t e;
+    if (d->real_sz == 8) e = esz == 8 ? convert<double, double>(srcp, p, cnt, d->stream)
+                                      : convert<double, float>(srcp, p, cnt, d->stream);
+    else e = esz == 8 ? convert<float, double>(srcp, p, cnt, d->stream)
+                      : convert<float, float>(srcp, p, cnt, d->stream);
+    p += cnt * esz;
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  if (mask & PFLB_FIELD_T) e = put_real(d->B.T[d->cur], n);
+  if (e == cudaSuccess && (mask & PFLB_FIELD_Y)) e = put_real(d->B.Y[d->cur], n * d->K);
+  if (e == cudaSuccess && (mask & PFLB_FIELD_TS)) e = put_real(d->B.Ts[d->cur], n);
+  if (e == cudaSuccess && (mask & (PFLB_FIELD_U | PFLB_FIELD_RHO | PFLB_FIELD_PH))) {
+    double* mom = nullptr;
+    e = cudaMallocAsync((void**)&mom, n * (d->dim + 2) * sizeof(double), d->stream);
+    if (e == cudaSuccess) e = d->L->moments(d->B, d->cur, mom, mom + n * d->dim,
+                                            mom + n * (d->dim + 1), d->stream);
+    auto put_d = [&](const double* srcp, size_t cnt) {
+      cudaError_t ee = esz == 8 ? convert<double, double>(srcp, p, cnt, d->stream)
+                                : convert<double, float>(srcp, p, cnt, d->stream);
+      p += cnt * esz;
+      return ee;
+    };
+    if (e == cudaSuccess && (mask & PFLB_FIELD_U)) e = put_d(mom, n * d->dim);
+    if (e == cudaSuccess && (mask & PFLB_FIELD_RHO)) e = put_d(mom + n * d->dim, n);
+    if (e == cudaSuccess && (mask & PFLB_FIELD_PH)) e = put_d(mom + n * (d->dim + 1), n);
+    if (mom) cudaFreeAsync(mom, d->stream);
+  }
+  if (e == cudaSuccess && (mask & PFLB_FIELD_G)) {
+    Weights W;
+    W.Q = d->Q;
+    const float s = d->L->g_scale();
+    for (int i = 0; i < d->Q; ++i) {
+      double w = d->dim == 2 ? Lattice<2>::w(i) : Lattice<3>::w(i);
+      W.w_over_scale[i] = float(w / s);
+    }
+    const size_t cnt = n * d->Q;
+    int blocks = (int)((cnt + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    const void* g = d->B.g[d->cur];
+    if (d->mode == MODE_FP64) {
+      if (esz == 8) decode_g_kernel<double, double><<<blocks, 256, 0, d->stream>>>((const double*)g, (double*)p, n, W);
+      else decode_g_kernel<double, float><<<blocks, 256, 0, d->stream>>>((const double*)g, (float*)p, n, W);
+    } else if (d->mode == MODE_FP32) {
+      if (esz == 8) decode_g_kernel<float, double><<<blocks, 256, 0, d->stream>>>((const float*)g, (double*)p, n, W);
+      else decode_g_kernel<float, float><<<blocks, 256, 0, d->stream>>>((const float*)g, (float*)p, n, W);
+    } else {
+      if (esz == 8) decode_g_kernel<__half, double><<<blocks, 256, 0, d->stream>>>((const __half*)g, (double*)p, n, W);
+      else decode_g_kernel<__half, float><<<blocks, 256, 0, d->stream>>>((const __half*)g, (float*)p, n, W);
+    }
+    e = cudaGetLastError();
+    p += cnt * esz;
+  }
+  if (e == cudaSuccess && where == PFLB_HOST)
+    e = cudaMemcpyAsync(dst, out, need * esz, cudaMemcpyDeviceToHost, d->stream);
+  if (where == PFLB_HOST && out) cudaFreeAsync(out, d->stream);
+  CK(d, e);
+  CK(d, cudaStreamSynchronize(d->stream));
+  DevScalars h;
+  CK(d, cudaMemcpy(&h, d->B.scal, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h.status != 0) return fail(d, h.status, "instability (NaN or non-positive temperature sum)");
+  return PFLB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int version, dim, nx, ny, nz, precision, K, Ts_field;
+  long long N;
+  int reserved[4];
+};
+
+size_t state_bytes(const pflb_domain* d) {
+  const size_t n = (size_t)d->N;
+  size_t b = sizeof(StateHeader) + sizeof(DevScalars);
+  b += n * d->Q * d->store_sz + n * d->real_sz + n * d->K * d->real_sz;
+  if (d->desc.Ts_field) b += n * d->real_sz;
+  return b;
+}
+
+// (pointer into the serialised buffer, device array, bytes) for each array
+template <class F>
+int for_each_array(pflb_domain* d, F f) {
+  const size_t n = (size_t)d->N;
+  size_t off = sizeof(StateHeader) + sizeof(DevScalars);
+  struct A { void* p; size_t b; } arr[4] = {
+      {d->B.g[d->cur], n * d->Q * d->store_sz}, {d->B.T[d->cur], n * d->real_sz},
+      {d->B.Y[d->cur], n * d->K * d->real_sz},
+      {d->desc.Ts_field ? d->B.Ts[d->cur] : nullptr, d->desc.Ts_field ? n * d->real_sz : 0}};
+  for (auto& a : arr) {
+    if (!a.b) continue;
+    int r = f(off, a.p, a.b);
+    if (r) return r;
+    off += a.b;
+  }
+  return PFLB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int pflb_state_bytes(const pflb_domain* d, size_t* bytes) {
+  if (!d || !bytes) return PFLB_ERR_ARG;
+  *bytes = state_bytes(d);
+  return PFLB_OK;
+}
+
+int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where) {
+  if (!d || !dst) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  if (!d->has_fields) return fail(d, PFLB_ERR_STATE, "no state yet");
+  if (bytes < state_bytes(d)) return fail(d, PFLB_ERR_ARG, "destination too small");
+  if (where != PFLB_HOST && where != PFLB_DEVICE) return fail(d, PFLB_ERR_ARG, "bad where");
+  CK(d, cudaSetDevice(d->desc.device));
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "PFLBSTv1", 8);
+  h.version = 1;
+  h.dim = d->dim; h.nx = d->desc.nx; h.ny = d->desc.ny; h.nz = d->desc.nz;
+  h.precision = d->desc.precision; h.K = d->K; h.Ts_field = d->desc.Ts_field; h.N = d->N;
+  char* out = static_cast<char*>(dst);
+  const cudaMemcpyKind k = where == PFLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kh = where == PFLB_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+  CK(d, cudaMemcpyAsync(out, &h, sizeof(h), kh, d->stream));
+  CK(d, cudaMemcpyAsync(out + sizeof(h), d->B.scal, sizeof(DevScalars), k, d->stream));
+  int r = for_each_array(d, [&](size_t off, void* p, size_t b) {
+    CK(d, cudaMemcpyAsync(out + off, p, b, k, d->stream));
+    return PFLB_OK;
+  });
+  if (r) return r;
+  CK(d, cudaStreamSynchronize(d->stream));
+  return PFLB_OK;
+}
+
+int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
+  if (!d || !src) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  if (!d->has_fields) return fail(d, PFLB_ERR_STATE, "set_fields must run once first");
+  if (bytes < state_bytes(d)) return fail(d, PFLB_ERR_ARG, "source too small");
+  if (where != PFLB_HOST && where != PFLB_DEVICE) return fail(d, PFLB_ERR_ARG, "bad where");
+  CK(d, cudaSetDevice(d->desc.device));
+  StateHeader h;
+  if (where == PFLB_HOST) std::memcpy(&h, src, sizeof(h));
+  else CK(d, cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDeviceToHost));
+  if (std::memcmp(h.magic, "PFLBSTv1", 8) != 0 || h.dim != d->dim || h.nx != d->desc.nx ||
+      h.ny != d->desc.ny || h.nz != d->desc.nz || h.precision != d->desc.precision ||
+      h.K != d->K || h.Ts_field != d->desc.Ts_field || h.N != d->N)
+    return fail(d, PFLB_ERR_ARG, "state does not match this domain");
+  const char* in = static_cast<const char*>(src);
+  const cudaMemcpyKind k = where == PFLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(d, cudaMemcpyAsync(d->B.scal, in + sizeof(h), sizeof(DevScalars), k, d->stream));
+  return for_each_array(d, [&](size_t off, void* p, size_t b) {
+    CK(d, cudaMemcpyAsync(p, in + off, b, k, d->stream));
+    return PFLB_OK;
+  });
+}
+
+int pflb_destroy(pflb_domain* d) {
+  if (!d) return PFLB_OK;
+  cudaSetDevice(d->desc.device);
+  cudaStreamSynchronize(d->stream);
+  free_buffers(d);
+  for (int b = 0; b < 2; ++b)
+    if (d->B.Y[b]) cudaFree(d->B.Y[b]);
+  delete d->L;
+  delete d;
+  return PFLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,16 @@
+// Instantiations of the 2-D fp32 kernels (one translation unit per lattice
+// and precision so that the build compiles them in parallel).
+#include "pflb_launch.cuh"
+
+namespace pflb {
+
+Launcher* make_launcher_2d_fp32(int K, const pflb_domain_desc& d, const pflb_mechanism& m) {
+  switch (K) {
+    case 0: return new LauncherImpl<2, 0, MODE_FP32>(d, m);
+    case 5: return new LauncherImpl<2, 5, MODE_FP32>(d, m);
+    case 6: return new LauncherImpl<2, 6, MODE_FP32>(d, m);
+    default: return nullptr;
+  }
+}
+
+}  // namespace pflb

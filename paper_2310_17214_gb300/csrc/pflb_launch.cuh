@@ -1,0 +1,171 @@
+// pflb_launch.cuh -- host-side launcher of the PF-LB-FD kernels for one
+// (lattice, species count, precision) combination: converts the physical
+// description to lattice units once and queues the kernels on a stream.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "../../include/pflb.h"
+#include "pflb_kernels.cuh"
+
+namespace pflb {
+
+struct Buffers {
+  void* g[2];
+  void* T[2];
+  void* Y[2];
+  void* Ts[2];
+  void* phi;
+  DevScalars* scal;
+  double* partials;
+  unsigned* counter;
+  int N;
+};
+
+struct Launcher {
+  virtual ~Launcher() {}
+  // g = g_eq from the current T, Y (and optional u, dim*N in the compute type)
+  virtual cudaError_t init(const Buffers& B, int cur, const void* u_init, double P0,
+                           cudaStream_t st) = 0;
+  // nsteps fused steps; `cur` flips once per step
+  virtual cudaError_t step(const Buffers& B, int& cur, int nsteps, cudaStream_t st) = 0;
+  virtual cudaError_t moments(const Buffers& B, int cur, double* u, double* rho, double* ph,
+                              cudaStream_t st) = 0;
+  virtual float g_scale() const = 0;
+};
+
+constexpr double R_GAS = 8.314;  // J/(mol K), value printed in Sec. 3.1
+
+template <class Real, int K>
+Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, int mode) {
+  Params<Real, K> P;
+  std::memset(&P, 0, sizeof(P));
+  P.nx = d.nx;
+  P.ny = d.ny;
+  P.nz = d.dim == 3 ? d.nz : 1;
+  P.N = P.nx * P.ny * P.nz;
+  for (int f = 0; f < 6; ++f) {
+    P.bc[f] = d.bc[f];
+    for (int a = 0; a < 3; ++a) P.wall_u[f][a] = Real(d.wall_u[f][a]);
+    P.wall_T[f] = Real(d.wall_T[f]);
+  }
+  const double h2 = d.dt / (d.dx * d.dx);
+  P.eos_c = 1.0 / (R_GAS * d.rho_ref);
+  P.inv_rho_ref = 1.0 / d.rho_ref;
+  P.mu_lat = Real(d.mu_ref * h2 / d.rho_ref);
+  P.sutherland = d.sutherland;
+  P.inv_suth_T = Real(d.sutherland ? 1.0 / d.suth_T : 1.0);
+  P.suth_S = Real(d.suth_S);
+  P.suth_TS = Real(d.suth_T + d.suth_S);
+  P.inv_Pr = Real(1.0 / d.Pr);
+  P.Au_eta2 = Real(d.A_u / (d.eta * d.eta));
+  P.AT_eta2 = Real(d.A_T / (d.eta * d.eta));
+  for (int a = 0; a < 3; ++a) P.Fb[a] = Real(d.Fb[a]);
+  P.inlet_parabolic = d.inlet_parabolic;
+  P.u_in = Real(d.u_in);
+  P.T_in = Real(d.T_in);
+  P.M0 = Real(d.M0);
+  P.cp0 = Real(d.cp0);
+  for (int k = 0; k < K; ++k) {
+    P.Y_in[k] = Real(m.Y_in[k]);
+    P.invM[k] = Real(1.0 / m.M[k]);
+    P.cp[k] = Real(m.cp[k]);
+    P.hf[k] = Real(m.hf[k]);
+    P.Dlat[k] = Real(m.Dref[k] * h2);
+    P.rho_ref_M[k] = Real(d.rho_ref / m.M[k]);
+  }
+  P.D_Tdep = (K > 0 && m.D_exp != 0.0) ? 1 : 0;
+  P.inv_DTref = Real(K > 0 && m.D_Tref > 0 ? 1.0 / m.D_Tref : 1.0);
+  P.D_exp = Real(K > 0 ? m.D_exp : 0.0);
+  P.Ts_field = d.Ts_field;
+  P.Ts_uniform = Real(d.Ts_uniform);
+  P.Cs = Real(d.rhocp_s / d.rho_ref);
+  P.Lams = Real(d.lambda_s * h2 / d.rho_ref);
+  P.phi_min = Real(d.phi_min);
+  P.chem = K > 0 ? m.chem_mode : 0;
+  P.J = K > 0 ? m.J : 0;
+  for (int j = 0; j < P.J; ++j) {
+    P.A_lat[j] = Real(m.A[j] * d.dt / d.rho_ref);
+    P.b[j] = Real(m.b[j]);
+    P.EaR[j] = Real(m.EaR[j]);
+    for (int k = 0; k < K; ++k) {
+      P.order[j][k] = Real(m.order[j][k]);
+      P.stoichM[j][k] = Real(m.stoich[j][k] * m.M[k]);
+    }
+  }
+  const float s = mode == MODE_FP16 ? 4096.0f : 1.0f;
+  P.g_scale = Real(s);
+  P.g_inv_scale = Real(1.0f / s);
+  return P;
+}
+
+template <int MODE> struct ModeTypes;
+template <> struct ModeTypes<MODE_FP64> { using Real = double; using Store = double; };
+template <> struct ModeTypes<MODE_FP32> { using Real = float; using Store = float; };
+template <> struct ModeTypes<MODE_FP16> { using Real = float; using Store = __half; };
+
+template <int DIM, int K, int MODE>
+struct LauncherImpl final : Launcher {
+  using Real = typename ModeTypes<MODE>::Real;
+  using Store = typename ModeTypes<MODE>::Store;
+  Params<Real, K> P;
+  int p0_closed;
+
+  LauncherImpl(const pflb_domain_desc& d, const pflb_mechanism& m)
+      : P(make_params<Real, K>(d, m, MODE)), p0_closed(d.p0_mode == PFLB_P0_CLOSED) {}
+
+  State<Real, Store> state(const Buffers& B, int cur) const {
+    State<Real, Store> S;
+    const int nxt = 1 - cur;
+    S.g_in = static_cast<const Store*>(B.g[cur]);
+    S.g_out = static_cast<Store*>(B.g[nxt]);
+    S.T_in = static_cast<const Real*>(B.T[cur]);
+    S.T_out = static_cast<Real*>(B.T[nxt]);
+    S.Y_in = static_cast<const Real*>(B.Y[cur]);
+    S.Y_out = static_cast<Real*>(B.Y[nxt]);
+    S.Ts_in = static_cast<const Real*>(B.Ts[cur]);
+    S.Ts_out = static_cast<Real*>(B.Ts[nxt]);
+    S.phi = static_cast<const Real*>(B.phi);
+    S.scal = B.scal;
+    S.partials = B.partials;
+    S.counter = B.counter;
+    return S;
+  }
+  int blocks() const { return (P.N + BLOCK - 1) / BLOCK; }
+
+  cudaError_t init(const Buffers& B, int cur, const void* u_init, double P0,
+                   cudaStream_t st) override {
+    State<Real, Store> S = state(B, cur);
+    // the equilibrium is written into the current buffer
+    S.g_out = static_cast<Store*>(B.g[cur]);
+    init_kernel<DIM, K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
+        P, S, static_cast<const Real*>(u_init), P0);
+    return cudaGetLastError();
+  }
+  cudaError_t step(const Buffers& B, int& cur, int nsteps, cudaStream_t st) override {
+    for (int n = 0; n < nsteps; ++n) {
+      step_kernel<DIM, K, Real, Store><<<blocks(), BLOCK, 0, st>>>(P, state(B, cur), p0_closed);
+      cur = 1 - cur;
+    }
+    return cudaGetLastError();
+  }
+  cudaError_t moments(const Buffers& B, int cur, double* u, double* rho, double* ph,
+                      cudaStream_t st) override {
+    moments_kernel<DIM, K, Real, Store><<<blocks(), BLOCK, 0, st>>>(P, state(B, cur), u, rho, ph);
+    return cudaGetLastError();
+  }
+  float g_scale() const override { return float(P.g_scale); }
+};
+
+// factories, one per translation unit (compiled in parallel)
+Launcher* make_launcher_2d_fp64(int K, const pflb_domain_desc& d, const pflb_mechanism& m);
+Launcher* make_launcher_2d_fp32(int K, const pflb_domain_desc& d, const pflb_mechanism& m);
+Launcher* make_launcher_2d_fp16(int K, const pflb_domain_desc& d, const pflb_mechanism& m);
+Launcher* make_launcher_3d_fp64(int K, const pflb_domain_desc& d, const pflb_mechanism& m);
+Launcher* make_launcher_3d_fp32(int K, const pflb_domain_desc& d, const pflb_mechanism& m);
+Launcher* make_launcher_3d_fp16(int K, const pflb_domain_desc& d, const pflb_mechanism& m);
+
+}  // namespace pflb

@@ -52,7 +52,7 @@ DREF6 = [2.2e-5, 2.1e-5, 2.0e-5, 1.6e-5, 2.5e-5, 2.0e-5]
 
 # one-step pre-exponential factor (m^3/(mol s)); Ea/R = 15000 K, first order
 # in CH4 and O2 (project-chosen, see the design notes for its calibration).
-A_ONE_STEP = 2.0e9
+A_ONE_STEP = 3.31e8
 
 
 def lean_ch4_air(phi_eq: float, species):
@@ -157,51 +157,107 @@ def ellipse_assembly(nx, ny, count, amin, amax, porosity, eta, seed, x0, periodi
     return phi, info
 
 
+def _ellipsoid_surface(c, axes, Rm, n, inflate):
+    """n quasi-uniform points on an ellipsoid surface pushed out by `inflate`."""
+    i = np.arange(n) + 0.5
+    th = np.arccos(1 - 2 * i / n)
+    ph = np.pi * (1 + 5 ** 0.5) * i
+    unit = np.stack([np.cos(ph) * np.sin(th), np.sin(ph) * np.sin(th), np.cos(th)], axis=1)
+    pts = unit * (np.asarray(axes) + inflate)
+    return c + pts @ Rm.T
+
+
+def _inside_ellipsoid(pts, c, axes, Rm, period):
+    d = pts - c
+    for a in (1, 2):
+        d[:, a] -= period[a] * np.round(d[:, a] / period[a])
+    q = d @ Rm
+    return np.any((q[:, 0] / axes[0]) ** 2 + (q[:, 1] / axes[1]) ** 2 + (q[:, 2] / axes[2]) ** 2
+                  <= 1.0)
+
+
 def ellipsoid_assembly(nx, ny, nz, count, amin, amax, porosity, eta, seed, x0, gap=None,
-                       max_attempts=100000):
-    """Seeded non-overlapping ellipsoids (periodic in y and z) in a bed region."""
+                       per_particle=150, n_surface=300):
+    """Seeded non-overlapping ellipsoids (periodic in y and z) in a bed region.
+
+    Random sequential addition with a bounding-sphere pre-check and a
+    surface-sample overlap test (surfaces inflated by the gap).  A particle
+    that cannot be placed is retried after the bed grows by 10 %; the bed
+    length starts from the target porosity.  Returns (phi_s, info)."""
     rng = np.random.default_rng(seed)
     gap = eta if gap is None else gap
     axes = np.sort(rng.uniform(amin, amax, size=(count, 3)), axis=1)[:, ::-1]
+    rots = [_rot3(rng) for _ in range(count)]
     vol = float(np.sum(4.0 / 3.0 * math.pi * np.prod(axes, axis=1)))
-    length = min(nx - x0 - 8, int(math.ceil(vol / (1.0 - porosity) / (ny * nz))))
-    occ = np.zeros((nz, ny, nx), dtype=bool)
-    phi = np.zeros((nz, ny, nx), dtype=np.float64)
-    placed = 0
+    length = int(math.ceil(vol / (1.0 - porosity) / (ny * nz)))
+    period = np.array([0.0, ny, nz], dtype=float)
+    placed = []  # (center, idx)
+    centers = np.zeros((count, 3))
+    radii = np.zeros(count)
+    surf = {}
+    pending = list(np.argsort(-np.prod(axes, axis=1)))
     attempts = 0
-    order = np.argsort(-np.prod(axes, axis=1))
-    for idx in order:
-        a, b, c = axes[idx]
-        Rm = _rot3(rng)
-        ok = False
-        while attempts < max_attempts and not ok:
-            attempts += 1
-            cx = rng.uniform(x0 + a, x0 + length - a)
-            cy, cz = rng.uniform(0, ny), rng.uniform(0, nz)
-            r = int(math.ceil(a + gap + eta)) + 1
-            xs = np.arange(int(cx) - r, int(cx) + r + 1)
-            if xs[0] < 0 or xs[-1] >= nx:
+    for _round in range(20):
+        lim = min(nx - x0 - 8, length)
+        left = []
+        for idx in pending:
+            a = axes[idx]
+            if lim < 2 * a[0] + 1:
+                left.append(idx)
                 continue
-            ys = np.arange(int(cy) - r, int(cy) + r + 1)
-            zs = np.arange(int(cz) - r, int(cz) + r + 1)
-            Z, Y, X = np.meshgrid(zs.astype(float), ys.astype(float), xs.astype(float),
-                                  indexing="ij")
-            P = np.stack([X - cx, Y - cy, Z - cz], axis=-1) @ Rm
-            F = (P[..., 0] / a) ** 2 + (P[..., 1] / b) ** 2 + (P[..., 2] / c) ** 2
-            gF = 2.0 * np.sqrt((P[..., 0] / a ** 2) ** 2 + (P[..., 1] / b ** 2) ** 2 +
-                               (P[..., 2] / c ** 2) ** 2) + 1e-12
-            d = (F - 1.0) / gF
-            sel = np.ix_(zs % nz, ys % ny, xs)
-            if np.any(occ[sel] & (d <= gap)):
-                continue
-            ok = True
-            occ[sel] = occ[sel] | (d <= 0)
-            phi[sel] = np.maximum(phi[sel], tanh_profile(d, eta))
-            placed += 1
-        if not ok:
+            ok = False
+            for _ in range(per_particle):
+                attempts += 1
+                c = np.array([rng.uniform(x0 + a[0], x0 + lim - a[0]), rng.uniform(0, ny),
+                              rng.uniform(0, nz)])
+                n = len(placed)
+                if n:
+                    d = c[None, :] - centers[:n]
+                    d[:, 1:] -= period[1:] * np.round(d[:, 1:] / period[1:])
+                    near = np.nonzero(np.sqrt((d * d).sum(1)) < a[0] + radii[:n] + gap)[0]
+                else:
+                    near = []
+                if len(near):
+                    pts = _ellipsoid_surface(c, a, rots[idx], n_surface, gap)
+                    bad = False
+                    for m in near:
+                        cj, j = placed[m]
+                        if _inside_ellipsoid(pts, cj, axes[j], rots[j], period) or \
+                                _inside_ellipsoid(surf[j], c, a, rots[idx], period):
+                            bad = True
+                            break
+                    if bad:
+                        continue
+                ok = True
+                centers[len(placed)] = c
+                radii[len(placed)] = a[0]
+                surf[idx] = _ellipsoid_surface(c, a, rots[idx], n_surface, gap)
+                placed.append((c, idx))
+                break
+            if not ok:
+                left.append(idx)
+        if not left:
             break
-    bed = phi[:, :, x0:x0 + length]
-    info = {"placed": placed, "requested": count, "bed_x0": x0, "bed_len": length,
+        pending = left
+        length = int(length * 1.15) + 2
+    # rasterise
+    phi = np.zeros((nz, ny, nx), dtype=np.float64)
+    for (c, idx) in placed:
+        a, Rm = axes[idx], rots[idx]
+        r = int(math.ceil(a[0] + 2 * eta)) + 1
+        xs = np.arange(max(0, int(c[0]) - r), min(nx, int(c[0]) + r + 1))
+        ys = np.arange(int(c[1]) - r, int(c[1]) + r + 1)
+        zs = np.arange(int(c[2]) - r, int(c[2]) + r + 1)
+        Z, Y, X = np.meshgrid(zs.astype(float), ys.astype(float), xs.astype(float), indexing="ij")
+        P = np.stack([X - c[0], Y - c[1], Z - c[2]], axis=-1) @ Rm
+        F = (P[..., 0] / a[0]) ** 2 + (P[..., 1] / a[1]) ** 2 + (P[..., 2] / a[2]) ** 2
+        gF = 2.0 * np.sqrt((P[..., 0] / a[0] ** 2) ** 2 + (P[..., 1] / a[1] ** 2) ** 2 +
+                           (P[..., 2] / a[2] ** 2) ** 2) + 1e-12
+        sel = np.ix_(zs % nz, ys % ny, xs)
+        phi[sel] = np.maximum(phi[sel], tanh_profile((F - 1.0) / gF, eta))
+    bed_len = min(nx - x0 - 8, length)
+    bed = phi[:, :, x0:x0 + bed_len]
+    info = {"placed": len(placed), "requested": count, "bed_x0": x0, "bed_len": bed_len,
             "porosity_bed": float(1.0 - bed.mean()), "attempts": attempts}
     return phi, info
 
@@ -374,25 +430,42 @@ def with_initial_u(p, fields):
     return fields
 
 
-def random_state(p, seed, T_range=(300.0, 600.0), u_amp=0.02, phi_kind="random"):
-    """Smoothly random fields for small parity cases (seeded)."""
+def smooth_field(shape, seed, modes=5):
+    """Seeded smooth periodic field in [0, 1] (a few low Fourier modes)."""
     rng = np.random.default_rng(seed)
-    N = p["nx"] * p["ny"] * (p["nz"] if p["dim"] == 3 else 1)
-    if phi_kind == "random":
-        phi = rng.uniform(0.0, 1.0, N) ** 3
+    grids = np.meshgrid(*[np.arange(n) / n for n in shape], indexing="ij")
+    f = np.zeros(shape)
+    for _ in range(modes):
+        k = rng.integers(0, 3, size=len(shape))
+        ph = rng.uniform(0, 2 * math.pi)
+        f += rng.uniform(0.5, 1.0) * np.cos(2 * math.pi * sum(ki * g for ki, g in zip(k, grids)) + ph)
+    f -= f.min()
+    return f / max(f.max(), 1e-300)
+
+
+def random_state(p, seed, T_range=(300.0, 600.0), u_amp=0.02, phi_kind="smooth", phi_max=0.6):
+    """Seeded smooth random fields for parity cases.  Phase fields stay smooth
+    (cell-to-cell ratios of phi_f bounded) because the phi_f-weighted explicit
+    diffusion is only stable for profiles resolved on the grid."""
+    rng = np.random.default_rng(seed)
+    shape = (p["nz"], p["ny"], p["nx"]) if p["dim"] == 3 else (p["ny"], p["nx"])
+    N = int(np.prod(shape))
+    sf = lambda k: smooth_field(shape, seed * 97 + k).reshape(-1)
+    if phi_kind == "smooth":
+        phi = phi_max * sf(1)
     elif phi_kind == "zero":
         phi = np.zeros(N)
     else:
         phi = np.asarray(phi_kind, dtype=np.float64).reshape(-1)
-    T = rng.uniform(*T_range, N)
+    T = T_range[0] + (T_range[1] - T_range[0]) * sf(2)
     K = p.get("K", 0)
     Y = None
     if K:
         Y0 = np.asarray(p["Y_in"], dtype=np.float64)
-        Y = (Y0[:, None] * rng.uniform(0.8, 1.2, (K, N)))
+        Y = Y0[:, None] * (0.8 + 0.4 * np.stack([sf(10 + k) for k in range(K)]))
         Y /= Y.sum(axis=0, keepdims=True)
         Y = Y.reshape(-1)
-    u = rng.uniform(-u_amp, u_amp, (p["dim"], N))
-    Ph = rng.uniform(-1e-3, 1e-3, N)
-    Ts = rng.uniform(*T_range, N) if p.get("Ts_field") else None
+    u = u_amp * (2 * np.stack([sf(20 + a) for a in range(p["dim"])]) - 1)
+    Ph = 1e-3 * (2 * sf(30) - 1)
+    Ts = T_range[0] + (T_range[1] - T_range[0]) * sf(31) if p.get("Ts_field") else None
     return {"phi": phi, "T": T, "Y": Y, "Ts": Ts, "u": u, "Ph": Ph}

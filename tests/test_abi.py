@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares (no compute calls: runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_2310_17214_gb300 import _native as nat
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    syms = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(pflb_[a-z0-9_]+)\s*\(", text):
+            syms.add(m.group(1))
+    return syms
+
+
+def test_library_exports_every_declared_symbol():
+    L = nat.lib()
+    syms = declared_symbols()
+    assert "pflb_step" in syms and "pflb_create_domain" in syms
+    for s in sorted(syms):
+        assert hasattr(L, s), f"{s} declared in include/ but not exported"
+        assert ctypes.cast(getattr(L, s), ctypes.c_void_p).value
+
+
+def test_lattice_tables_match_oracle_order():
+    for dim in (2, 3):
+        c1, w1 = nat.lattice(dim)
+        c2, w2 = O.lattice(dim)
+        assert np.array_equal(c1, c2)
+        assert np.array_equal(w1, w2)
+
+
+def test_struct_layouts_are_plain_c():
+    # the ctypes mirrors must match the header's field order and sizes
+    assert ctypes.sizeof(nat.Scalars) == 7 * 8 + 8
+    assert ctypes.sizeof(nat.Mechanism) % 8 == 0
+
+
+def test_create_rejects_bad_descriptions_without_touching_the_gpu():
+    from paper_2310_17214_gb300 import inputs as I
+    p = I.config1()
+    d = nat.make_desc(p)
+    d.bc[0] = nat.BC["outlet"]  # outlet on x-lo is invalid
+    h = ctypes.c_void_p()
+    rc = nat.lib().pflb_create_domain(ctypes.byref(d), ctypes.byref(h))
+    assert rc == -1 and not h.value
+    assert b"inlet only" in nat.lib().pflb_last_error(None)
+    d = nat.make_desc(p)
+    d.bc[2], d.bc[3] = nat.BC["periodic"], nat.BC["wall"]
+    assert nat.lib().pflb_create_domain(ctypes.byref(d), ctypes.byref(h)) == -1
+    d = nat.make_desc(p)
+    d.dim = 4
+    assert nat.lib().pflb_create_domain(ctypes.byref(d), ctypes.byref(h)) == -7

@@ -1,0 +1,195 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle, element by
+element, on the same seeded inputs.
+
+Bars: FP64 path max relative error <= 1e-10 per field (max|a-b| / max|b|);
+FP32 path L2 relative error <= 1e-4 in u and T; FP16-stored populations as
+stated in the test.  Sizes span several 256-cell blocks with a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2310_17214_gb300 import inputs as I
+from paper_2310_17214_gb300._native import Domain
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+def maxrel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def l2rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_pair(p, f, nsteps, precision="fp64", chunks=1):
+    ora = O.OracleState(p, f["phi"], f["T"], f["Y"], f["Ts"], u=f.get("u"))
+    dom = Domain(p, precision)
+    dom.set_phase_field(f["phi"], f["Ts"])
+    dom.set_fields(f["T"], f["Y"], f.get("u"))
+    per = nsteps // chunks
+    for _ in range(chunks):
+        ora.step(per)
+        dom.step(per)
+    names = ["T", "g", "u", "rho", "Ph"] + (["Y"] if p.get("K") else []) + \
+        (["Ts"] if p.get("Ts_field") else [])
+    got = dom.get(*names)
+    u, rho, ph = ora.moments()
+    ref = {"T": ora.T, "g": ora.g.reshape(ora.Q, ora.N), "u": u, "rho": rho, "Ph": ph}
+    if p.get("K"):
+        ref["Y"] = ora.Y.reshape(ora.K, ora.N)
+    if p.get("Ts_field"):
+        ref["Ts"] = ora.Ts
+    sc = dom.scalars()
+    dom.close()
+    return got, ref, sc, ora
+
+
+def small_case(dim, nx, ny, nz=1, **kw):
+    p = I._base(dim, nx, ny, nz)
+    I.lattice_air(p, kw.pop("nu", 0.04))
+    p.update(kw)
+    return p
+
+
+def assert_fp64(got, ref, sc, ora, tol=FP64_TOL):
+    for k in ref:
+        e = maxrel(got[k], ref[k])
+        assert e <= tol, f"{k}: max rel err {e:.3e}"
+    assert abs(sc["P0"] / ora.P0 - 1) <= tol
+    assert sc["step"] == ora.scal[6]
+
+
+# ----------------------------------------------------------------- FP64 parity
+def test_fp64_config1_channel_disc_full_size():
+    """The 128x64 channel with the heated disc (drag A_u = 1, A_T from the
+    wall-temperature fit), 400 steps from a developed inlet profile."""
+    p = I.config1()
+    f = I.with_initial_u(p, I.config1_fields(p))
+    assert_fp64(*run_pair(p, f, 400, chunks=2))
+
+
+def test_fp64_ragged_2d_walls_random_state():
+    p = small_case(2, 61, 37, bc=["inlet", "outlet", "wall", "wall", "periodic", "periodic"],
+                   A_u=80.0, A_T=60.0, eta=3.0, inlet_parabolic=1, u_in=0.03,
+                   Ts_uniform=520.0, sutherland=1, wall_T=[0, 0, 410.0, 0, 0, 0],
+                   wall_u=[[0, 0, 0], [0, 0, 0], [0, 0, 0], [0.01, 0, 0], [0, 0, 0], [0, 0, 0]])
+    f = I.random_state(p, 21, T_range=(300.0, 500.0), u_amp=0.01)
+    assert_fp64(*run_pair(p, f, 60))
+
+
+def test_fp64_reactive_bed_small():
+    """Reactive 2-D bed (5 species, one-step chemistry, transported solid
+    temperature) on a reduced lattice, 300 steps through ignition."""
+    p = I.config2(nx=160, ny=48)
+    p["bed"] = {"count": 6, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 40}
+    p["reactions"] = I.one_step_mechanism(3.3e8)
+    p["ignite"] = [8, 32, 1500.0]
+    f = I.config2_fields(p)
+    f["T"][(np.arange(f["T"].size) % p["nx"] > 8) & (np.arange(f["T"].size) % p["nx"] < 32)] = 1800.0
+    assert_fp64(*run_pair(p, f, 300, chunks=3))
+
+
+def test_fp64_closed_box_p0_closure():
+    """Closed periodic box with heat release: P0 follows the closure."""
+    p = I.config2(nx=33, ny=9)
+    p["bc"] = ["periodic"] * 6
+    p["p0_mode"] = "closed"
+    p["Ts_field"] = 0
+    p["reactions"] = I.one_step_mechanism(3.3e8)
+    rng = np.random.default_rng(5)
+    f = I.reactive_fields(p, rng.uniform(0, 0.3, 33 * 9))
+    f["T"] = 1200.0 + 400.0 * rng.uniform(0, 1, 33 * 9)
+    got, ref, sc, ora = run_pair(p, f, 150)
+    assert_fp64(got, ref, sc, ora)
+    assert abs(ora.P0 / p["P0"] - 1) > 1e-3  # the closure really moved P0
+
+
+@pytest.mark.parametrize("bc", [
+    ["inlet", "outlet", "periodic", "periodic", "wall", "wall"],
+    ["periodic", "periodic", "periodic", "periodic", "periodic", "periodic"],
+])
+def test_fp64_3d_small(bc):
+    p = small_case(3, 19, 11, 7, bc=bc, A_u=60.0, A_T=50.0, eta=2.5, inlet_parabolic=1,
+                   u_in=0.02, Ts_uniform=480.0, nu=0.05)
+    f = I.random_state(p, 31, T_range=(300.0, 450.0), u_amp=0.01)
+    assert_fp64(*run_pair(p, f, 40))
+
+
+def test_fp64_3d_reactive_crop():
+    """A 64^3 crop of the 3-D reactive bed (one-step chemistry, solid field)."""
+    p = I.config3(nx=64, ny=32, nz=32, precision="fp64")
+    p["bed"] = {"count": 6, "amin": 5, "amax": 8, "porosity": 0.5, "x0": 24}
+    p["reactions"] = I.one_step_mechanism(3.3e8)
+    f = I.config3_fields(p)
+    assert_fp64(*run_pair(p, f, 12, chunks=2))
+
+
+def test_fp64_six_species_no_chemistry():
+    p = I.config2(nx=70, ny=20)
+    p["K"] = 6
+    p["species"], p["M"] = I.SPECIES6, I.M6
+    p["cp"], p["Dref"] = I.CP6, I.DREF6
+    p["hf"] = [h / m for h, m in zip(I.HF_MOL6, I.M6)]
+    p["Y_in"] = I.lean_ch4_air(0.7, I.SPECIES6)
+    p["chem"], p["reactions"] = "none", []
+    p["Ts_field"] = 0
+    f = I.random_state(p, 41, T_range=(300.0, 900.0), u_amp=0.002)
+    assert_fp64(*run_pair(p, f, 50))
+
+
+def test_fp64_degenerate_shapes():
+    # one-cell-thick periodic direction and the smallest x extent
+    p = small_case(2, 2, 1, bc=["periodic"] * 6, Fb=[1e-5, 0, 0])
+    f = I.random_state(p, 51, T_range=(300.0, 320.0), u_amp=0.005)
+    assert_fp64(*run_pair(p, f, 30))
+    p = small_case(2, 257, 1, bc=["inlet", "outlet", "periodic", "periodic", "periodic",
+                                  "periodic"], u_in=0.01)
+    f = I.random_state(p, 52, T_range=(300.0, 320.0), u_amp=0.005, phi_kind="zero")
+    assert_fp64(*run_pair(p, f, 30))
+
+
+def test_fp64_full_size_reactive_bed_first_steps():
+    """The 1024x256 reactive bed in the configuration the benchmark times:
+    the first steps agree with the oracle everywhere."""
+    p = I.config2()
+    f = I.config2_fields(p)
+    assert_fp64(*run_pair(p, f, 6, chunks=2))
+
+
+# ---------------------------------------------------------- mixed precision
+def test_fp32_config1_error_after_2000_steps():
+    """FP32 compute and storage on the 128x64 channel: L2 relative error of u
+    and T after 2000 steps <= 1e-4 (P0 reduction stays FP64)."""
+    p = I.config1()
+    f = I.with_initial_u(p, I.config1_fields(p))
+    got, ref, sc, ora = run_pair(p, f, 2000, precision="fp32", chunks=4)
+    eu = l2rel(got["u"], ref["u"])
+    eT = l2rel(got["T"] - 300.0, ref["T"] - 300.0)
+    print(f"fp32 cfg1 2000 steps: L2 rel u {eu:.3e}, T-T_in {eT:.3e}")
+    assert eu <= 1e-4 and eT <= 1e-4
+
+
+def test_fp16_storage_config1_error_after_2000_steps():
+    p = I.config1()
+    f = I.with_initial_u(p, I.config1_fields(p))
+    got, ref, sc, ora = run_pair(p, f, 2000, precision="fp32_fp16", chunks=4)
+    eu = l2rel(got["u"], ref["u"])
+    eT = l2rel(got["T"] - 300.0, ref["T"] - 300.0)
+    print(f"fp16-stored cfg1 2000 steps: L2 rel u {eu:.3e}, T-T_in {eT:.3e}")
+    assert eu <= 5e-3 and eT <= 5e-3
+
+
+def test_fp32_reactive_small():
+    p = I.config2(nx=160, ny=48, precision="fp32")
+    p["bed"] = {"count": 6, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 40}
+    p["reactions"] = I.one_step_mechanism(3.3e8)
+    f = I.config2_fields(p)
+    got, ref, sc, ora = run_pair(p, f, 200, precision="fp32")
+    assert l2rel(got["T"], ref["T"]) <= 1e-5
+    assert l2rel(got["u"], ref["u"]) <= 1e-3

@@ -296,7 +296,9 @@ def test_bruteforce_one_step(name):
     p["wall_u"] = [[0, 0, 0], [0, 0, 0], [0.01, 0, 0], [0, -0.005, 0.002], [0, 0, 0], [0, 0, 0]]
     p["wall_T"] = [350.0, 0.0, 0.0, 420.0, 0.0, 380.0]
     f = I.random_state(p, seed=11, T_range=(320.0, 900.0), u_amp=0.03)
-    f["phi"] = np.where(np.arange(f["phi"].size) % 5 == 0, 0.0, f["phi"])
+    # cover pure-fluid cells and frozen-fluid cells (phi_f < phi_min)
+    idx = np.arange(f["phi"].size)
+    f["phi"] = np.where(idx % 5 == 0, 0.0, np.where(idx % 7 == 3, 1.0, f["phi"]))
     s = O.OracleState(p, f["phi"], f["T"], f["Y"], f["Ts"], u=f["u"], Ph=f["Ph"])
     # make the state less trivial: one oracle step, then perturb P0 history
     s.step(1)
