@@ -193,6 +193,37 @@ int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where);
  * Asynchronous on the domain's stream. */
 int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
 
+/* Largest lattice (cells) that pflb_step_noalloc accepts. */
+#define PFLB_NOALLOC_MAX_CELLS (1 << 22)
+
+/* One time step on caller-owned device arrays, allocating nothing.
+ *
+ * For callers that cannot allocate device memory: code that runs while
+ * someone else captures a CUDA graph, plug-ins whose host framework owns all
+ * device memory through its own pool, loops that forbid allocator calls after
+ * start-up.  The paper has no counterpart; it is the same fused step as
+ * pflb_step.  The caller owns and passes every state array (layout as in
+ * pflb_get_fields, in the compute precision: double for PFLB_FP64, float for
+ * PFLB_FP32): phi (N), g_in/g_out (Q*N), T_in/T_out (N), Y_in/Y_out (K*N, or
+ * NULL when K = 0), Ts_in/Ts_out (N, or NULL unless desc->Ts_field).  `mech`
+ * may be NULL for K = 0.  `scalars` (host) carries P0, P0_prev, mass, step
+ * and status in, and returns the updated values (P0 of the next step, I,
+ * fluxes) after the step; the call synchronises desc->stream.
+ *
+ * The reduction scratch (per-block partials, arrival counter, scalar block)
+ * is a fixed device array inside the library, sized for at most
+ * PFLB_NOALLOC_MAX_CELLS cells (about 0.5 MB); every GPU that loads the
+ * library holds it until the process exits.  Larger lattices return
+ * PFLB_ERR_ARG.  Supported: D2Q9, K = 0 or 5, PFLB_FP64 or PFLB_FP32 (else
+ * PFLB_ERR_UNSUPPORTED).  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * host threads) race and corrupt each other's reduction -- serialise them. */
+int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechanism* mech,
+                      const void* phi, const void* g_in, void* g_out,
+                      const void* T_in, void* T_out, const void* Y_in, void* Y_out,
+                      const void* Ts_in, void* Ts_out, pflb_scalars* scalars);
+
 /* Number of populations Q and the lattice velocities (3*Q ints) and
  * weights (Q doubles) in the library's storage order. */
 int pflb_lattice(int dim, int* c_out, double* w_out);

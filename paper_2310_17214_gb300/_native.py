@@ -82,6 +82,8 @@ def lib():
         L.pflb_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.pflb_get_state.argtypes = [vp, vp, C.c_size_t, C.c_int]
         L.pflb_set_state.argtypes = [vp, vp, C.c_size_t, C.c_int]
+        L.pflb_step_noalloc.argtypes = [C.POINTER(Desc), C.POINTER(Mechanism), vp, vp, vp,
+                                        vp, vp, vp, vp, vp, vp, C.POINTER(Scalars)]
         L.pflb_destroy.argtypes = [vp]
         L.pflb_last_error.argtypes = [vp]
         L.pflb_last_error.restype = C.c_char_p
@@ -288,3 +290,29 @@ class Domain:
             self.close()
         except Exception:
             pass
+
+
+def step_noalloc(prob, precision, arrays, scalars, stream=0, device=0):
+    """One step through pflb_step_noalloc on caller-owned CUDA tensors.
+
+    For callers that cannot allocate device memory (graph capture owned by
+    someone else, host frameworks with their own memory pool): the library
+    allocates nothing here; its reduction scratch is a fixed device array.
+    `arrays` maps phi, g_in, g_out, T_in, T_out, Y_in, Y_out, Ts_in, Ts_out to
+    contiguous CUDA tensors in the compute precision (Y/Ts may be absent);
+    `scalars` is a dict with P0, P0_prev, mass, step, status and is returned
+    updated."""
+    d = make_desc(prob, precision, stream, device)
+    m = make_mechanism(prob) if prob.get("K", 0) else None
+    sc = Scalars()
+    for k in ("P0", "P0_prev", "mass", "I", "flux_in", "flux_out"):
+        setattr(sc, k, float(scalars.get(k, 0.0)))
+    sc.step, sc.status = int(scalars.get("step", 0)), int(scalars.get("status", 0))
+    ptr = lambda k: (arrays[k].data_ptr() if arrays.get(k) is not None else None)
+    rc = lib().pflb_step_noalloc(C.byref(d), C.byref(m) if m is not None else None,
+                                 ptr("phi"), ptr("g_in"), ptr("g_out"), ptr("T_in"),
+                                 ptr("T_out"), ptr("Y_in"), ptr("Y_out"), ptr("Ts_in"),
+                                 ptr("Ts_out"), C.byref(sc))
+    if rc != 0:
+        raise PflbError(f"pflb_step_noalloc error {rc}")
+    return {f: getattr(sc, f) for f, _ in Scalars._fields_}

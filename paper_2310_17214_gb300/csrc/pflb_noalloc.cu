@@ -1,0 +1,126 @@
+// pflb_noalloc.cu -- pflb_step_noalloc: one time step on caller-owned device
+// arrays without any device allocation.
+//
+// Some callers cannot call cudaMalloc at all: code running inside a CUDA
+// graph that is being captured by someone else, plug-ins living under a host
+// framework that owns every device allocation through its own pool, or
+// real-time loops that forbid allocator calls after start-up.  They own the
+// state arrays and pass them in; the only memory this entry point needs
+// besides them -- the per-block partial sums of the P0 reduction, the
+// arrival counter of the finishing block and the scalar block -- lives in the
+// fixed file-scope device array below, sized for at most
+// PFLB_NOALLOC_MAX_CELLS cells.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/pflb.h"
+#include "pflb_launch.cuh"
+
+using namespace pflb;
+
+namespace {
+
+constexpr int kMaxBlocks = PFLB_NOALLOC_MAX_CELLS / BLOCK;
+constexpr size_t kPartialDoubles = (size_t)kMaxBlocks * 4;
+
+// Layout: [DevScalars][counter + pad to 64 bytes][partials: kMaxBlocks x 4 doubles].
+// Every GPU that loads the library holds this array until the process exits.
+constexpr size_t kScalarBytes = (sizeof(DevScalars) + 63) / 64 * 64;
+constexpr size_t kScratchBytes = kScalarBytes + 64 + kPartialDoubles * sizeof(double);
+static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* scratch_ptr[kMaxDevices] = {nullptr};
+
+// status code only: this entry point keeps no per-call message state
+int err(int code, const char*) { return code; }
+
+}  // namespace
+
+extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechanism* mech,
+                                 const void* phi, const void* g_in, void* g_out,
+                                 const void* T_in, void* T_out, const void* Y_in, void* Y_out,
+                                 const void* Ts_in, void* Ts_out, pflb_scalars* scalars) {
+  if (!desc || !phi || !g_in || !g_out || !T_in || !T_out || !scalars)
+    return err(PFLB_ERR_ARG, "NULL argument");
+  const pflb_domain_desc& D = *desc;
+  const int K = mech ? mech->K : 0;
+  if (D.dim != 2) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports D2Q9 only");
+  if (K != 0 && K != 5) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports K = 0 or 5");
+  if (D.precision != PFLB_FP64 && D.precision != PFLB_FP32)
+    return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports FP64 and FP32");
+  if (K > 0 && (!Y_in || !Y_out)) return err(PFLB_ERR_ARG, "Y arrays are required when K > 0");
+  if (D.Ts_field && (!Ts_in || !Ts_out)) return err(PFLB_ERR_ARG, "Ts arrays are required");
+  if (D.nx < 2 || D.ny < 1) return err(PFLB_ERR_ARG, "bad lattice extent");
+  const long long N = (long long)D.nx * D.ny;
+  if (N > PFLB_NOALLOC_MAX_CELLS)
+    return err(PFLB_ERR_ARG, "lattice larger than PFLB_NOALLOC_MAX_CELLS cells");
+  if (D.device < 0 || D.device >= kMaxDevices) return err(PFLB_ERR_ARG, "bad device ordinal");
+
+  if (cudaSetDevice(D.device) != cudaSuccess) return err(PFLB_ERR_CUDA, "cudaSetDevice failed");
+  // once per device, with that device current: the device address of the
+  // scratch array (its host-side name is only a stand-in)
+  if (!scratch_ptr[D.device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+    if (e != cudaSuccess || !p) return err(PFLB_ERR_CUDA, "cudaGetSymbolAddress failed");
+    scratch_ptr[D.device] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(scratch_ptr[D.device]);
+  cudaStream_t st = static_cast<cudaStream_t>(D.stream);
+
+  DevScalars h;
+  std::memset(&h, 0, sizeof(h));
+  h.P0 = scalars->P0;
+  h.P0_prev = scalars->P0_prev;
+  h.mass = scalars->mass;
+  h.step = scalars->step;
+  h.status = scalars->status;
+  if (cudaMemcpyAsync(base, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(base + kScalarBytes, 0, 64, st) != cudaSuccess)
+    return err(PFLB_ERR_CUDA, "scratch set-up copy failed");
+
+  Buffers B;
+  std::memset(&B, 0, sizeof(B));
+  B.g[0] = const_cast<void*>(g_in);
+  B.g[1] = g_out;
+  B.T[0] = const_cast<void*>(T_in);
+  B.T[1] = T_out;
+  B.Y[0] = const_cast<void*>(Y_in);
+  B.Y[1] = Y_out;
+  B.Ts[0] = const_cast<void*>(Ts_in);
+  B.Ts[1] = Ts_out;
+  B.phi = const_cast<void*>(phi);
+  B.scal = reinterpret_cast<DevScalars*>(base);
+  B.counter = reinterpret_cast<unsigned*>(base + kScalarBytes);
+  B.partials = reinterpret_cast<double*>(base + kScalarBytes + 64);
+  B.N = (int)N;
+
+  pflb_mechanism none;
+  std::memset(&none, 0, sizeof(none));
+  const pflb_mechanism& M = mech ? *mech : none;
+  int cur = 0;
+  cudaError_t e;
+  if (D.precision == PFLB_FP64) {
+    if (K == 0) { LauncherImpl<2, 0, MODE_FP64> L(D, M); e = L.step(B, cur, 1, st); }
+    else { LauncherImpl<2, 5, MODE_FP64> L(D, M); e = L.step(B, cur, 1, st); }
+  } else {
+    if (K == 0) { LauncherImpl<2, 0, MODE_FP32> L(D, M); e = L.step(B, cur, 1, st); }
+    else { LauncherImpl<2, 5, MODE_FP32> L(D, M); e = L.step(B, cur, 1, st); }
+  }
+  if (e != cudaSuccess) return err(PFLB_ERR_CUDA, cudaGetErrorString(e));
+  if (cudaMemcpyAsync(&h, base, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return err(PFLB_ERR_CUDA, "scalar read-back failed");
+  scalars->P0 = h.P0;
+  scalars->P0_prev = h.P0_prev;
+  scalars->mass = h.mass;
+  scalars->I = h.I;
+  scalars->flux_in = h.flux_in;
+  scalars->flux_out = h.flux_out;
+  scalars->step = h.step;
+  scalars->status = h.status;
+  if (h.status != 0) return err(PFLB_ERR_UNSTABLE, "instability (NaN or non-positive sum)");
+  return PFLB_OK;
+}
