@@ -212,7 +212,7 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
  *
  * The reduction scratch (per-block partials, arrival counter, scalar block)
  * is a fixed device array inside the library, sized for at most
- * PFLB_NOALLOC_MAX_CELLS cells (about 0.5 MB); every GPU that loads the
+ * PFLB_NOALLOC_MAX_CELLS cells (about 1 MB); every GPU that loads the
  * library holds it until the process exits.  Larger lattices return
  * PFLB_ERR_ARG.  Supported: D2Q9, K = 0 or 5, PFLB_FP64 or PFLB_FP32 (else
  * PFLB_ERR_UNSUPPORTED).  The first call on a device looks up the array's

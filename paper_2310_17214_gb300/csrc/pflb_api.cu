@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
 
 #include "../../include/pflb.h"
 #include "pflb_launch.cuh"
@@ -201,7 +202,10 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
     return fail(nullptr, PFLB_ERR_CUDA, "%s", cudaGetErrorString(e));
   }
   const size_t n = (size_t)N;
-  const int blocks = (int)((N + BLOCK - 1) / BLOCK);
+  // partial sums: one slot per block of the 1-D init grid or the step's tile grid
+  const long long tiles = (long long)((D.nx + 31) / 32) * ((D.ny + 7) / 8) *
+                          (D.dim == 3 ? (D.nz + 15) / 16 : 1);
+  const long long blocks = std::max<long long>((N + BLOCK - 1) / BLOCK, tiles);
   bool ok = true;
   auto al = [&](void** p, size_t bytes) {
     if (!ok) return;
@@ -215,7 +219,8 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   }
   al(&d->B.phi, n * d->real_sz);
   al((void**)&d->B.scal, sizeof(DevScalars));
-  al((void**)&d->B.partials, (size_t)blocks * 4 * sizeof(double));
+  d->B.slots = blocks;
+  al((void**)&d->B.partials, (size_t)blocks * 2 * 4 * sizeof(double));
   al((void**)&d->B.counter, sizeof(unsigned));
   if (!ok) {
     cudaGetLastError();
@@ -302,6 +307,7 @@ int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, i
   delete d->L;
   d->L = make_launcher(d);
   if (!d->L) return fail(d, PFLB_ERR_UNSUPPORTED, "no kernel compiled for this combination");
+  d->B.pending = 0;
   cudaError_t e = d->L->init(d->B, d->cur, u, d->desc.P0, d->stream);
   if (u) cudaFreeAsync(u, d->stream);
   CK(d, e);
@@ -321,6 +327,7 @@ int pflb_step(pflb_domain* d, int nsteps) {
 int pflb_get_scalars(pflb_domain* d, pflb_scalars* out) {
   if (!d || !out) return fail(d, PFLB_ERR_ARG, "NULL argument");
   CK(d, cudaSetDevice(d->desc.device));
+  if (d->L) CK(d, d->L->finalize(d->B, d->stream));
   DevScalars h;
   CK(d, cudaMemcpyAsync(&h, d->B.scal, sizeof(h), cudaMemcpyDeviceToHost, d->stream));
   CK(d, cudaStreamSynchronize(d->stream));
@@ -355,6 +362,7 @@ int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int 
   if (mask & PFLB_FIELD_G) need += n * d->Q;
   if (bytes < need * esz) return fail(d, PFLB_ERR_ARG, "destination too small");
   CK(d, cudaSetDevice(d->desc.device));
+  CK(d, d->L->finalize(d->B, d->stream));
   char* out = nullptr;
   if (where == PFLB_HOST) CK(d, cudaMallocAsync((void**)&out, need * esz, d->stream));
   else out = static_cast<char*>(dst);
@@ -475,6 +483,7 @@ int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where) {
   if (bytes < state_bytes(d)) return fail(d, PFLB_ERR_ARG, "destination too small");
   if (where != PFLB_HOST && where != PFLB_DEVICE) return fail(d, PFLB_ERR_ARG, "bad where");
   CK(d, cudaSetDevice(d->desc.device));
+  CK(d, d->L->finalize(d->B, d->stream));
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "PFLBSTv1", 8);
@@ -511,6 +520,7 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
   const char* in = static_cast<const char*>(src);
   const cudaMemcpyKind k = where == PFLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(d, cudaMemcpyAsync(d->B.scal, in + sizeof(h), sizeof(DevScalars), k, d->stream));
+  d->B.pending = 0;
   return for_each_array(d, [&](size_t off, void* p, size_t b) {
     CK(d, cudaMemcpyAsync(p, in + off, b, k, d->stream));
     return PFLB_OK;

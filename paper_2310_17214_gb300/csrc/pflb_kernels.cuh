@@ -3,17 +3,23 @@
 // One fused kernel advances one time step of the low-Mach phase-field /
 // lattice-Boltzmann / finite-difference model (arXiv 2310.17214, Sec. 3.3):
 //   pull streaming of the pressure-based populations with the boundary rules,
-//   moments with the implicit diffuse-interface drag (Sec. 3.2.1), the FD
+//   moments with the implicit diffuse-interface drag (Sec. 3.2.1), FD
 //   transport of T, Y_k and the solid temperature with the reaction source
 //   (Sec. 3.2.2 eq. 8, Sec. 3.3 eqs. diffusion-heat-flux-3,
 //   energy-transport-DI-version, 9), the divergence from the low-Mach
 //   constraint, the source Xi (eq. body-force) and BGK collision (eqs.
-//   eq-pop-f, eq-pop-g), and the FP64 reduction for P0 (Sec. 3.1) finished
-//   by the last block to arrive.
+//   eq-pop-f, eq-pop-g), and the FP64 reduction for P0 (Sec. 3.1) finished by
+//   the last block to arrive.
 //
-// Storage is SoA: g[i*N + cell], Y[k*N + cell]; cell = x + nx*(y + ny*z).
-// Threads map to consecutive x so every population / field load of a warp
-// is a contiguous (or one-element-shifted) 128-byte line.
+// Layout: SoA in HBM, g[i*N + cell], Y[k*N + cell]; cell = x + nx*(y + ny*z).
+// A block owns a TX x TY tile of one or more z-planes.  It stages T, Y, phi,
+// Ts of the tile plus a one-cell halo in shared memory and evaluates the
+// per-cell properties (EOS density, viscosity, conductivity, diffusivity
+// factor) once per staged cell; the FD stencils and grad(rho) then read their
+// neighbours from shared memory.  In 3-D the block marches along z with a
+// ring of three staged planes (2.5-D blocking).  The populations are pulled
+// straight from HBM: warps map to 32 consecutive x, so every load is a
+// contiguous or one-element-shifted 128-byte line.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -23,7 +29,7 @@ namespace pflb {
 
 constexpr int KMAX = 8;
 constexpr int JMAX = 4;
-constexpr int BLOCK = 256;
+constexpr int BLOCK = 256;  // threads per block (one cell each per plane)
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
 enum { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP16 = 2 };
@@ -67,8 +73,16 @@ template <> struct Lattice<3> {
   }
 };
 
+// Tile shape: 32 x 8 cells per plane; 3-D blocks march over ZC planes.
+template <int DIM> struct Tile {
+  static constexpr int TX = 32, TY = 8;
+  static constexpr int ZC = DIM == 3 ? 16 : 1;
+  static constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
+  static constexpr int NPL = DIM == 3 ? 3 : 1;  // staged planes
+};
+
 // ------------------------------------------------------------ parameters
-// Everything in lattice units, converted once on the host (pflb_api.cu).
+// Everything in lattice units, converted once on the host (pflb_launch.cuh).
 template <class Real, int K>
 struct Params {
   static constexpr int KK = K > 0 ? K : 1;
@@ -78,6 +92,7 @@ struct Params {
   Real wall_T[6];
   double eos_c;            // rho* = P0 Mw eos_c / T, eos_c = 1 / (R rho_ref)
   double inv_rho_ref;      // dP0 / rho_ref (J/kg) in the T equation
+  Real eos_cr;             // eos_c in the compute type
   Real mu_lat;             // mu_ref dt / (rho_ref dx^2)
   int sutherland;
   Real inv_suth_T, suth_S, suth_TS;  // suth_TS = suth_T + suth_S
@@ -102,11 +117,16 @@ struct Params {
   Real g_scale, g_inv_scale;  // FP16 storage scale (power of two)
 };
 
+// Scalar state on the device.  The per-step quantities the cells need (P0,
+// dP0/P0, dP0/rho_ref) are precomputed by the block that finishes the
+// reduction, in FP64 and in FP32.
 struct DevScalars {
   double P0, P0_prev, mass, I, flux_in, flux_out, mass_now;
   long long step;
   int status;
   int pad;
+  double dlnP0, dP0r;
+  float P0_f, dlnP0_f, dP0r_f, pad_f;
 };
 
 template <class Real, class Store>
@@ -121,109 +141,101 @@ struct State {
   Real* __restrict__ Ts_out;
   const Real* __restrict__ phi;
   DevScalars* scal;
-  double* partials;        // [gridDim.x][4]
+  double* partials;        // this step's block partials: [blocks][4]
   unsigned* counter;
 };
 
 // ----------------------------------------------------- storage codecs
 template <class Store, class Real> struct Codec;
 template <> struct Codec<double, double> {
-  __device__ static double load(const double* p, double, double) { return __ldg(p); }
-  __device__ static void store(double* p, double v, double, double) { *p = v; }
+  __device__ static double load(const double* p, double) { return __ldg(p); }
+  __device__ static void store(double* p, double v, double) { *p = v; }
 };
 template <> struct Codec<float, float> {
-  __device__ static float load(const float* p, float, float) { return __ldg(p); }
-  __device__ static void store(float* p, float v, float, float) { *p = v; }
+  __device__ static float load(const float* p, float) { return __ldg(p); }
+  __device__ static void store(float* p, float v, float) { *p = v; }
 };
 // FP16: h = g / w * scale (weights folded so every direction has the same range)
 template <> struct Codec<__half, float> {
-  __device__ static float load(const __half* p, float w_over_scale, float) {
+  __device__ static float load(const __half* p, float w_over_scale) {
     return __half2float(__ldg(p)) * w_over_scale;
   }
-  __device__ static void store(__half* p, float v, float, float scale_over_w) {
+  __device__ static void store(__half* p, float v, float scale_over_w) {
     *p = __float2half_rn(v * scale_over_w);
   }
 };
 
-// ------------------------------------------------------------ helpers
-template <class Real> __device__ __forceinline__ Real rcp(Real x) { return Real(1) / x; }
+// ---------------------------------------------------------- arithmetic
+// FP32 uses the fast hardware approximations (a few ulp); FP64 stays IEEE.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float fpow(float x, float y) { return __powf(x, y); }
+__device__ __forceinline__ double fpow(double x, double y) { return pow(x, y); }
 
-template <class Real, int K>
-struct Props {
-  Real rho, cp, lam, Mw;
-  Real D[Params<Real, K>::KK];
-};
+template <class Real> __device__ __forceinline__ Real scal_P0(const DevScalars* s);
+template <> __device__ __forceinline__ double scal_P0<double>(const DevScalars* s) { return s->P0; }
+template <> __device__ __forceinline__ float scal_P0<float>(const DevScalars* s) { return s->P0_f; }
+template <class Real> __device__ __forceinline__ Real scal_dlnP0(const DevScalars* s);
+template <> __device__ __forceinline__ double scal_dlnP0<double>(const DevScalars* s) { return s->dlnP0; }
+template <> __device__ __forceinline__ float scal_dlnP0<float>(const DevScalars* s) { return s->dlnP0_f; }
+template <class Real> __device__ __forceinline__ Real scal_dP0r(const DevScalars* s);
+template <> __device__ __forceinline__ double scal_dP0r<double>(const DevScalars* s) { return s->dP0r; }
+template <> __device__ __forceinline__ float scal_dP0r<float>(const DevScalars* s) { return s->dP0r_f; }
 
-// EOS (Sec. 3.1), Sutherland / constant viscosity and lambda = mu cp / Pr
-// (Sec. 4, eqs. muT, lambdaT), D_k = Dref (T / D_Tref)^D_exp.
+// ------------------------------------------------------------ physics
+// Viscosity: Sutherland (Sec. 4, eq. muT) or constant, lattice units.
 template <class Real, int K>
 __device__ __forceinline__ Real viscosity(const Params<Real, K>& P, Real T) {
   if (!P.sutherland) return P.mu_lat;
   Real t = T * P.inv_suth_T;
-  return P.mu_lat * t * sqrt(t) * P.suth_TS / (T + P.suth_S);
+  return P.mu_lat * t * sqrt(t) * fdiv(P.suth_TS, T + P.suth_S);
 }
 
 template <class Real, int K>
-__device__ __forceinline__ void props(const Params<Real, K>& P, Real P0, Real T, const Real* Y,
-                                      bool need_D, Props<Real, K>& o) {
-  Real Mw, cp;
+__device__ __forceinline__ Real mixture_invMw(const Params<Real, K>& P, const Real* Y) {
   if constexpr (K == 0) {
-    Mw = P.M0;
-    cp = P.cp0;
-  } else {
-    Real s = 0, c = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      s += Y[k] * P.invM[k];
-      c += Y[k] * P.cp[k];
-    }
-    Mw = Real(1) / s;
-    cp = c;
-  }
-  o.Mw = Mw;
-  o.cp = cp;
-  o.rho = P0 * Mw * Real(P.eos_c) / T;
-  o.lam = viscosity(P, T) * cp * P.inv_Pr;
-  if constexpr (K > 0) {
-    if (need_D) {
-      Real f = P.D_Tdep ? pow(T * P.inv_DTref, P.D_exp) : Real(1);
-#pragma unroll
-      for (int k = 0; k < K; ++k) o.D[k] = P.Dlat[k] * f;
-    }
-  }
-}
-
-template <class Real, int K>
-__device__ __forceinline__ Real mixture_Mw(const Params<Real, K>& P, const Real* Y) {
-  if constexpr (K == 0) {
-    return P.M0;
+    return Real(1) / P.M0;
   } else {
     Real s = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) s += Y[k] * P.invM[k];
-    return Real(1) / s;
+    return s;
   }
 }
 
-// Explicit Arrhenius rates (Sec. 3.2.2 eq. 8, Sec. 3.3 eq. 9), returned per
-// lattice step per rho_ref: om[k] = omega_k dt / rho_ref, omT likewise (J/kg).
+template <class Real, int K>
+__device__ __forceinline__ Real mixture_cp(const Params<Real, K>& P, const Real* Y) {
+  if constexpr (K == 0) {
+    return P.cp0;
+  } else {
+    Real s = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) s += Y[k] * P.cp[k];
+    return s;
+  }
+}
+
+// Explicit Arrhenius rates (Sec. 3.2.2 eq. 8, Sec. 3.3 eq. 9), per lattice
+// step per rho_ref: om[k] = omega_k dt / rho_ref, omT likewise (J/kg).
 template <class Real, int K>
 __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Real* Y, Real rho,
-                                      Real* om, Real& omT) {
+                                      Real invT, Real* om, Real& omT) {
 #pragma unroll
   for (int k = 0; k < K; ++k) om[k] = 0;
   Real C[Params<Real, K>::KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) C[k] = rho * P.rho_ref_M[k] * (Y[k] > Real(0) ? Y[k] : Real(0));
   for (int j = 0; j < P.J; ++j) {
-    Real q = P.A_lat[j] * exp(-P.EaR[j] / T);
-    if (P.b[j] != Real(0)) q *= pow(T, P.b[j]);
+    Real q = P.A_lat[j] * fexp(-P.EaR[j] * invT);
+    if (P.b[j] != Real(0)) q *= fpow(T, P.b[j]);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      Real o = P.order[j][k];
+      const Real o = P.order[j][k];
       if (o == Real(1)) q *= C[k];
       else if (o == Real(2)) q *= C[k] * C[k];
-      else if (o != Real(0)) q *= pow(C[k], o);
+      else if (o != Real(0)) q *= fpow(C[k], o);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) om[k] += P.stoichM[j][k] * q;
@@ -232,46 +244,6 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
 #pragma unroll
   for (int k = 0; k < K; ++k) wt -= P.hf[k] * om[k];
   omT = wt;
-}
-
-template <class Real, int K>
-struct Nb {
-  Real T, phi, Ts;
-  Real Y[Params<Real, K>::KK];
-};
-
-// Neighbour (or ghost) state along axis a, side s.  Periodic faces wrap;
-// the inlet ghost carries (T_in, Y_in); a wall with a set temperature
-// carries it; other faces copy the cell.  phi, Ts of ghosts are the cell's.
-template <int DIM, class Real, class Store, int K>
-__device__ __forceinline__ void load_nb(const Params<Real, K>& P, const State<Real, Store>& S,
-                                        int c, const int xyz[3], int a, int s, const Nb<Real, K>& own,
-                                        Nb<Real, K>& o) {
-  const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
-  const int stride = a == 0 ? 1 : (a == 1 ? P.nx : P.nx * P.ny);
-  int q = xyz[a] + s;
-  int face = 2 * a + (s > 0 ? 1 : 0);
-  int nc;
-  if (q >= 0 && q < n) {
-    nc = c + s * stride;
-  } else if (P.bc[face] == BC_PERIODIC) {
-    nc = c + s * stride - s * n * stride;
-  } else {
-    o = own;
-    if (P.bc[face] == BC_INLET) {
-      o.T = P.T_in;
-#pragma unroll
-      for (int k = 0; k < K; ++k) o.Y[k] = P.Y_in[k];
-    } else if (P.bc[face] == BC_WALL && P.wall_T[face] > Real(0)) {
-      o.T = P.wall_T[face];
-    }
-    return;
-  }
-  o.T = __ldg(S.T_in + nc);
-  o.phi = __ldg(S.phi + nc);
-  o.Ts = P.Ts_field ? __ldg(S.Ts_in + nc) : P.Ts_uniform;
-#pragma unroll
-  for (int k = 0; k < K; ++k) o.Y[k] = __ldg(S.Y_in + (size_t)k * P.N + nc);
 }
 
 template <class Real, int K>
@@ -301,8 +273,8 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
   for (int i = 0; i < L::Q; ++i) {
     const Real wos = Real(L::w(i)) * P.g_inv_scale;
     if (!edge) {
-      int src = c - L::c(i, 0) - L::c(i, 1) * sy - (DIM == 3 ? L::c(i, 2) * sz : 0);
-      gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos, 0);
+      const int src = c - L::c(i, 0) - L::c(i, 1) * sy - (DIM == 3 ? L::c(i, 2) * sz : 0);
+      gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos);
       continue;
     }
     int sx[3] = {xyz[0] - L::c(i, 0), xyz[1] - L::c(i, 1), DIM == 3 ? xyz[2] - L::c(i, 2) : 0};
@@ -312,8 +284,8 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
     for (int a = 0; a < DIM; ++a) {
       const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
       if (sx[a] < 0 || sx[a] >= n) {
-        int face = 2 * a + (sx[a] >= n ? 1 : 0);
-        int bc = P.bc[face];
+        const int face = 2 * a + (sx[a] >= n ? 1 : 0);
+        const int bc = P.bc[face];
         if (bc == BC_PERIODIC) sx[a] = sx[a] < 0 ? sx[a] + n : sx[a] - n;
         else if (bc == BC_WALL) { if (wall < 0) wall = face; }
         else if (bc == BC_INLET) inlet = true;
@@ -323,14 +295,14 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
     const int ib = L::opp(i);
     if (wall >= 0 || inlet || outlet) {
       const Real wob = Real(L::w(ib)) * P.g_inv_scale;
-      Real own = Codec<Store, Real>::load(S.g_in + (size_t)ib * P.N + c, wob, 0);
+      const Real own = Codec<Store, Real>::load(S.g_in + (size_t)ib * P.N + c, wob);
       if (wall >= 0) {
         Real cu = 0;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) cu += Real(L::c(i, a)) * P.wall_u[wall][a];
         gin[i] = own + Real(2) * Real(L::w(i)) * rho_c * cu;
       } else if (inlet) {
-        Real cu = Real(L::c(i, 0)) * inlet_u(P, xyz, DIM);
+        const Real cu = Real(L::c(i, 0)) * inlet_u(P, xyz, DIM);
         gin[i] = own + Real(2) * Real(L::w(i)) * rho_in * cu;
       } else {
         Real cu = 0, uu = 0;
@@ -342,294 +314,528 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
         gin[i] = -own + Real(L::w(i)) * rho_c * (Real(3) * cu * cu - uu);
       }
     } else {
-      int src = sx[0] + P.nx * (sx[1] + P.ny * sx[2]);
-      gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos, 0);
+      const int src = sx[0] + P.nx * (sx[1] + P.ny * sx[2]);
+      gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos);
     }
   }
 }
 
-// Block-wide FP64 sum of 4 values; result valid in thread 0.
-__device__ __forceinline__ void block_sum4(double v[4]) {
-  __shared__ double sh[BLOCK / 32][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+// ----------------------------------------------------------- reductions
+// Error-free sum of two floats (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Block sum of one per-thread value into FP64 (result in thread 0).  FP32
+// values are summed within the warp with compensation (the pair s + e is
+// exact up to the final rounding), warps are combined in FP64.
+template <class Real>
+__device__ __forceinline__ double block_sum(Real v, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
+  double w;
+  if constexpr (sizeof(Real) == 4) {
+    float s = v, e = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sh[wid][j] = v[j];
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      double t = lane < (int)(blockDim.x >> 5) ? sh[lane][j] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      v[j] = t;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float so = __shfl_down_sync(0xffffffffu, s, o);
+      const float eo = __shfl_down_sync(0xffffffffu, e, o);
+      float t, err;
+      two_sum(s, so, t, err);
+      s = t;
+      e = e + eo + err;
     }
+    w = double(s) + double(e);
+  } else {
+    w = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
   }
+  if (lane == 0) sh[wid] = w;
+  __syncthreads();
+  double r = 0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
 }
 
-// Deterministic finish of the per-block partials by the last block to
-// arrive: a fixed-order strided sum followed by a fixed tree.  Updates the
-// scalar state (P0 closure, diagnostics) and re-arms the counter.
-__device__ __forceinline__ void finish_reduction(double* partials, unsigned* counter,
+// Combine the per-block partials (I, inlet flux, outlet flux) of one step in
+// a fixed order (lane-strided sums, then a fixed shuffle tree) and update the
+// scalar state: the P0 closure when the domain is closed, the diagnostics and
+// the per-step constants the cells of the next step read.  Run by one warp.
+__device__ __forceinline__ void combine_partials(const double* partials, unsigned nb,
                                                  DevScalars* scal, int p0_closed, bool is_init,
-                                                 double init_P0, double eos_c) {
-  __shared__ bool last;
-  __threadfence();
-  if (threadIdx.x == 0) {
-    unsigned t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
+                                                 double init_P0, double eos_c,
+                                                 double inv_rho_ref) {
+  const int lane = threadIdx.x & 31;
+  double v0 = 0, v1 = 0, v2 = 0;
+  unsigned b = lane;
+  for (; b + 96 < nb; b += 128) {
+    const double a0 = __ldcg(partials + 4 * b), a1 = __ldcg(partials + 4 * (b + 32));
+    const double a2 = __ldcg(partials + 4 * (b + 64)), a3 = __ldcg(partials + 4 * (b + 96));
+    const double f0 = __ldcg(partials + 4 * b + 1), f1 = __ldcg(partials + 4 * (b + 32) + 1);
+    const double f2 = __ldcg(partials + 4 * (b + 64) + 1), f3 = __ldcg(partials + 4 * (b + 96) + 1);
+    const double o0 = __ldcg(partials + 4 * b + 2), o1 = __ldcg(partials + 4 * (b + 32) + 2);
+    const double o2 = __ldcg(partials + 4 * (b + 64) + 2), o3 = __ldcg(partials + 4 * (b + 96) + 2);
+    v0 += a0; v0 += a1; v0 += a2; v0 += a3;
+    v1 += f0; v1 += f1; v1 += f2; v1 += f3;
+    v2 += o0; v2 += o1; v2 += o2; v2 += o3;
   }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double v[4] = {0, 0, 0, 0};
-  const volatile double* vp = partials;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+  for (; b < nb; b += 32) {
+    v0 += __ldcg(partials + 4 * b + 0);
+    v1 += __ldcg(partials + 4 * b + 1);
+    v2 += __ldcg(partials + 4 * b + 2);
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] += vp[4 * b + j];
-  block_sum4(v);
-  if (threadIdx.x == 0) {
-    const double I = v[0];
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  if (lane == 0) {
+    const double I = v0;
+    double P0, P0p;
     if (is_init) {
-      scal->P0 = init_P0;
-      scal->P0_prev = init_P0;
+      P0 = P0p = init_P0;
       scal->mass = init_P0 * I * eos_c;
-      scal->I = I;
       scal->flux_in = scal->flux_out = 0;
-      scal->mass_now = v[3];
       scal->step = 0;
       scal->status = 0;
     } else {
-      const double P0 = scal->P0;
-      double P0n = P0;
-      if (p0_closed) P0n = scal->mass / (I * eos_c);
-      scal->P0_prev = P0;
-      scal->P0 = P0n;
-      scal->I = I;
-      scal->flux_in = v[1];
-      scal->flux_out = v[2];
-      scal->mass_now = v[3];
+      P0p = scal->P0;
+      P0 = P0p;
+      if (p0_closed) P0 = scal->mass / (I * eos_c);
+      scal->flux_in = v1;
+      scal->flux_out = v2;
       scal->step += 1;
-      if (!(I == I) || !(P0n == P0n) || I <= 0.0) scal->status = -5;
+      if (!(I == I) || !(P0 == P0) || I <= 0.0) scal->status = -5;
     }
-    *counter = 0u;
+    scal->P0_prev = P0p;
+    scal->P0 = P0;
+    scal->I = I;
+    scal->mass_now = P0 * I * eos_c;
+    scal->dlnP0 = (P0 - P0p) / P0;
+    scal->dP0r = (P0 - P0p) * inv_rho_ref;
+    scal->P0_f = float(P0);
+    scal->dlnP0_f = float(scal->dlnP0);
+    scal->dP0r_f = float(scal->dP0r);
+  }
+}
+
+// Publish the block sums (valid in thread 0) of this step.  Closed domains
+// need P0 of the next step before it starts, so the warp that draws the last
+// arrival ticket combines at once (lane 0 fences its own writes before taking
+// the ticket; the other warps retire).  With a fixed P0 the combine is
+// deferred: block 0 of the next launch, or the on-demand finalize kernel,
+// does it, and the step ends without a serial tail.
+__device__ __forceinline__ void publish_partials(double sI, double sIn, double sOut,
+                                                 double* partials, unsigned* counter,
+                                                 DevScalars* scal, int p0_closed, bool is_init,
+                                                 double init_P0, double eos_c,
+                                                 double inv_rho_ref) {
+  if (threadIdx.x >= 32) return;
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const int lane = threadIdx.x;
+  const bool now = p0_closed || is_init;
+  unsigned last = 0;
+  if (lane == 0) {
+    partials[4 * bid + 0] = sI;
+    partials[4 * bid + 1] = sIn;
+    partials[4 * bid + 2] = sOut;
+    if (now) {
+      __threadfence();
+      last = (atomicAdd(counter, 1u) == nb - 1) ? 1u : 0u;
+    }
+  }
+  if (!now) return;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  combine_partials(partials, nb, scal, p0_closed, is_init, init_P0, eos_c, inv_rho_ref);
+  if (lane == 0) *counter = 0u;
+}
+
+// On-demand combine of the deferred partials of the last step (one warp).
+static __global__ void finalize_kernel(const double* partials, unsigned nb, DevScalars* scal,
+                                double eos_c, double inv_rho_ref) {
+  combine_partials(partials, nb, scal, 0, false, 0.0, eos_c, inv_rho_ref);
+}
+
+// ------------------------------------------------ staged tile (smem)
+// Fields per staged cell: T, phi_s, rho, kappa_T = phi_f lambda, mu, f_D
+// (diffusivity factor), Ts, phi_f rho f_D, then Y_k.
+enum { F_T = 0, F_PHI, F_RHO, F_KT, F_MU, F_FD, F_TS, F_RF, F_Y0 };
+
+template <class Real, int K, int HP>
+struct Plane {
+  Real f[F_Y0 + K][HP];
+};
+
+// Stage plane z (may be -1 or nz: ghost plane) of the block's tile with its
+// xy halo.  Out-of-domain halo cells follow the ghost rules: periodic faces
+// wrap; otherwise the adjacent cell's values, with the inlet state (T_in,
+// Y_in) on the inlet face and the wall temperature on a wall that has one.
+template <int DIM, class Real, class Store, int K, int HP>
+__device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const State<Real, Store>& S,
+                                            Plane<Real, K, HP>& pl, int x0, int y0, int z,
+                                            Real P0) {
+  using T_ = Tile<DIM>;
+  for (int h = threadIdx.x; h < HP; h += blockDim.x) {
+    const int hx = h % T_::HX, hy = h / T_::HX;
+    int q[3] = {x0 - 1 + hx, y0 - 1 + hy, z};
+    int ghost_face = -1;
+    int nout = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+      if (q[a] < 0 || q[a] >= n) {
+        const int face = 2 * a + (q[a] >= n ? 1 : 0);
+        if (P.bc[face] == BC_PERIODIC) {
+          q[a] = q[a] < 0 ? q[a] + n : q[a] - n;
+          if (q[a] < 0 || q[a] >= n) q[a] = q[a] < 0 ? 0 : n - 1;  // tiles wider than n
+        } else {
+          q[a] = q[a] < 0 ? 0 : n - 1;
+          ghost_face = face;
+          ++nout;
+        }
+      }
+    }
+    const int c = q[0] + P.nx * (q[1] + P.ny * q[2]);
+    Real T = __ldg(S.T_in + c);
+    const Real phis = __ldg(S.phi + c);
+    const Real Ts = P.Ts_field ? __ldg(S.Ts_in + c) : P.Ts_uniform;
+    Real Y[Params<Real, K>::KK];
+#pragma unroll
+    for (int k = 0; k < K; ++k) Y[k] = __ldg(S.Y_in + (size_t)k * P.N + c);
+    if (nout == 1) {
+      const int bc = P.bc[ghost_face];
+      if (bc == BC_INLET) {
+        T = P.T_in;
+#pragma unroll
+        for (int k = 0; k < K; ++k) Y[k] = P.Y_in[k];
+      } else if (bc == BC_WALL && P.wall_T[ghost_face] > Real(0)) {
+        T = P.wall_T[ghost_face];
+      }
+    }
+    const Real phif = Real(1) - phis;
+    const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
+    const Real mu = viscosity(P, T);
+    const Real cp = mixture_cp(P, Y);
+    Real fD = Real(1);
+    if constexpr (K > 0) {
+      if (P.D_Tdep) fD = fpow(T * P.inv_DTref, P.D_exp);
+    }
+    pl.f[F_T][h] = T;
+    pl.f[F_PHI][h] = phis;
+    pl.f[F_RHO][h] = rho;
+    pl.f[F_KT][h] = phif * (mu * cp * P.inv_Pr);
+    pl.f[F_MU][h] = mu;
+    pl.f[F_FD][h] = fD;
+    pl.f[F_TS][h] = Ts;
+    pl.f[F_RF][h] = phif * rho * fD;
+#pragma unroll
+    for (int k = 0; k < K; ++k) pl.f[F_Y0 + k][h] = Y[k];
   }
 }
 
 // ------------------------------------------------------ the fused step
+// Per cell: (a1) pull + moments + implicit drag, (c) reaction source,
+// (b) FD transport of Y_k, T, Ts, low-Mach divergence, (a) source + BGK
+// collision + store, (d) contribution to the FP64 reduction.
 template <int DIM, int K, class Real, class Store>
-__global__ void __launch_bounds__(BLOCK)
-step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed) {
+__device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const State<Real, Store>& S,
+                                            const Real* __restrict__ cen,
+                                            const Real* __restrict__ zm,
+                                            const Real* __restrict__ zp, int h, int c,
+                                            const int xyz[3], Real P0, Real dlnP0, Real dP0r,
+                                            Real& fin, Real& fout) {
   using L = Lattice<DIM>;
+  using T_ = Tile<DIM>;
   constexpr int Q = L::Q;
   constexpr int KK = Params<Real, K>::KK;
+  constexpr int HP = T_::HP;
   constexpr Real CS2 = Real(1) / Real(3);
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = c < P.N;
+  // neighbour offsets inside a staged plane (x, y) and the z planes
+  auto at = [&](int f, int a, int s) -> Real {
+    if (a == 0) return cen[f * HP + h + s];
+    if (a == 1) return cen[f * HP + h + s * T_::HX];
+    return (s < 0 ? zm : zp)[f * HP + h];
+  };
 
-  const double P0d = S.scal->P0, P0pd = S.scal->P0_prev;
-  const Real P0 = Real(P0d);
-  const Real dlnP0 = Real((P0d - P0pd) / P0d);
-  const Real dP0r = Real((P0d - P0pd) * P.inv_rho_ref);
-
-  double red[4] = {0, 0, 0, 0};
-  if (active) {
-    int xyz[3];
-    xyz[0] = c % P.nx;
-    const int yz = c / P.nx;
-    xyz[1] = yz % P.ny;
-    xyz[2] = DIM == 3 ? yz / P.ny : 0;
-    bool edge = xyz[0] == 0 || xyz[0] == P.nx - 1 || xyz[1] == 0 || xyz[1] == P.ny - 1;
-    if (DIM == 3) edge = edge || xyz[2] == 0 || xyz[2] == P.nz - 1;
-
-    // own state
-    Nb<Real, K> v0;
-    v0.T = __ldg(S.T_in + c);
-    v0.phi = __ldg(S.phi + c);
-    v0.Ts = P.Ts_field ? __ldg(S.Ts_in + c) : P.Ts_uniform;
+  const Real T0 = cen[F_T * HP + h];
+  const Real phis = cen[F_PHI * HP + h];
+  const Real phif = Real(1) - phis;
+  const Real rho = cen[F_RHO * HP + h];
+  const Real mu = cen[F_MU * HP + h];
+  const Real fD = cen[F_FD * HP + h];
+  const Real Ts0 = cen[F_TS * HP + h];
+  Real Y0[KK];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v0.Y[k] = __ldg(S.Y_in + (size_t)k * P.N + c);
-    Props<Real, K> d0;
-    props(P, P0, v0.T, v0.Y, true, d0);
-    const Real phis = v0.phi, phif = Real(1) - v0.phi;
-    const Real mu = viscosity(P, v0.T);
-    const Real Kd = P.Au_eta2 * mu * phif * phis * phis;
-    const Real rho = d0.rho;
+  for (int k = 0; k < K; ++k) Y0[k] = cen[(F_Y0 + k) * HP + h];
+  const Real invMw = mixture_invMw(P, Y0);
+  const Real cp = mixture_cp(P, Y0);
+  const Real lam = mu * cp * P.inv_Pr;
+  const Real Kd = P.Au_eta2 * mu * phif * phis * phis;
+  const Real invT = fdiv(Real(1), T0);
 
-    // (a1) pull streaming and moments, implicit drag
-    Real rho_in = 0;
-    if (edge) {
-      Real Yin[KK];
-#pragma unroll
-      for (int k = 0; k < K; ++k) Yin[k] = P.Y_in[k];
-      rho_in = P0 * mixture_Mw(P, Yin) * Real(P.eos_c) / P.T_in;
-    }
-    Real gin[Q];
-    Real u[3] = {0, 0, 0};
-    Real uw[3] = {0, 0, 0};
-    const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
-    const Real inv_rk = Real(1) / (rho + Real(0.5) * Kd);
-    for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
-      pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        Real m = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          if (L::c(i, a) != 0) m += Real(L::c(i, a)) * gin[i];
-        u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) * inv_rk;
-        uw[a] = u[a];
-      }
-    }
+  bool edge = xyz[0] == 0 || xyz[0] == P.nx - 1 || xyz[1] == 0 || xyz[1] == P.ny - 1;
+  if (DIM == 3) edge = edge || xyz[2] == 0 || xyz[2] == P.nz - 1;
 
-    // neighbours for the FD stencils and grad(rho)
-    Nb<Real, K> vm[DIM], vp[DIM];
-    Props<Real, K> dm[DIM], dp[DIM];
+  // (a1) pull streaming, moments, implicit drag
+  Real rho_in = 0;
+  if (edge && P.bc[0] == BC_INLET) {
+    Real Yin[KK];
+#pragma unroll
+    for (int k = 0; k < K; ++k) Yin[k] = P.Y_in[k];
+    rho_in = fdiv(P0 * P.eos_cr, P.T_in * mixture_invMw(P, Yin));
+  }
+  Real gin[Q];
+  Real u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
+  const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
+  const Real inv_rk = fdiv(Real(1), rho + Real(0.5) * Kd);
+  for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
+    pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      load_nb<DIM>(P, S, c, xyz, a, -1, v0, vm[a]);
-      load_nb<DIM>(P, S, c, xyz, a, +1, v0, vp[a]);
-      props(P, P0, vm[a].T, vm[a].Y, true, dm[a]);
-      props(P, P0, vp[a].T, vp[a].Y, true, dp[a]);
+      Real m = 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        if (L::c(i, a) != 0) m += Real(L::c(i, a)) * gin[i];
+      u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) * inv_rk;
+      uw[a] = u[a];
     }
+  }
 
-    const bool fluid_on = phif >= P.phi_min;
-    const bool solid_on = P.Ts_field ? (phis >= P.phi_min) : true;
-    Real SI = 0;
-    if (fluid_on && solid_on) SI = P.AT_eta2 * d0.lam * phif * phis * phis * (v0.Ts - v0.T);
+  const bool fluid_on = phif >= P.phi_min;
+  const bool solid_on = P.Ts_field ? (phis >= P.phi_min) : true;
+  Real SI = 0;
+  if (fluid_on && solid_on) SI = P.AT_eta2 * lam * phif * phis * phis * (Ts0 - T0);
 
-    // (c) reaction source
-    Real om[KK], omT = 0;
+  // (c) reaction source
+  Real om[KK], omT = 0;
 #pragma unroll
-    for (int k = 0; k < KK; ++k) om[k] = 0;
-    if constexpr (K > 0) {
-      if (P.chem == 1) rates(P, v0.T, v0.Y, rho, om, omT);
+  for (int k = 0; k < KK; ++k) om[k] = 0;
+  if constexpr (K > 0) {
+    if (P.chem == 1) rates(P, T0, Y0, rho, invT, om, omT);
+  }
+
+  const Real iphr = fluid_on ? fdiv(Real(1), phif * rho) : Real(0);
+  const Real rf0 = cen[F_RF * HP + h];
+
+  // (b) species
+  Real Yn[KK];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    Real adv = 0, dif = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const Real ym = at(F_Y0 + k, a, -1), yp = at(F_Y0 + k, a, +1);
+      adv += u[a] > Real(0) ? u[a] * (Y0[k] - ym) : u[a] * (yp - Y0[k]);
+      const Real km = Real(0.5) * P.Dlat[k] * (rf0 + at(F_RF, a, -1));
+      const Real kp = Real(0.5) * P.Dlat[k] * (rf0 + at(F_RF, a, +1));
+      dif += kp * (yp - Y0[k]) - km * (Y0[k] - ym);
     }
+    Yn[k] = fluid_on ? Y0[k] + (-phif * rho * adv + dif + phif * om[k]) * iphr : Y0[k];
+  }
 
-    // (b) FD transport: species
-    Real Yn[KK];
+  // (b) temperature
+  Real Tn = Ts0;
+  if (fluid_on) {
+    Real adv = 0, dif = 0, cross = 0;
+    const Real kc = cen[F_KT * HP + h];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!fluid_on) { Yn[k] = v0.Y[k]; continue; }
-      const Real kc = phif * rho * d0.D[k];
-      Real adv = 0, dif = 0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        adv += u[a] > Real(0) ? u[a] * (v0.Y[k] - vm[a].Y[k]) : u[a] * (vp[a].Y[k] - v0.Y[k]);
-        const Real km = Real(0.5) * (kc + (Real(1) - vm[a].phi) * dm[a].rho * dm[a].D[k]);
-        const Real kp = Real(0.5) * (kc + (Real(1) - vp[a].phi) * dp[a].rho * dp[a].D[k]);
-        dif += kp * (vp[a].Y[k] - v0.Y[k]) - km * (v0.Y[k] - vm[a].Y[k]);
-      }
-      const Real rhs = -phif * rho * adv + dif + phif * om[k];
-      Yn[k] = v0.Y[k] + rhs / (phif * rho);
-    }
-
-    // (b) FD transport: temperature
-    Real Tn;
-    if (fluid_on) {
-      Real adv = 0, dif = 0, cross = 0;
-      const Real kc = phif * d0.lam;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        adv += u[a] > Real(0) ? u[a] * (v0.T - vm[a].T) : u[a] * (vp[a].T - v0.T);
-        const Real km = Real(0.5) * (kc + (Real(1) - vm[a].phi) * dm[a].lam);
-        const Real kp = Real(0.5) * (kc + (Real(1) - vp[a].phi) * dp[a].lam);
-        dif += kp * (vp[a].T - v0.T) - km * (v0.T - vm[a].T);
-        const Real gT = Real(0.5) * (vp[a].T - vm[a].T);
+    for (int a = 0; a < DIM; ++a) {
+      const Real tm = at(F_T, a, -1), tp = at(F_T, a, +1);
+      adv += u[a] > Real(0) ? u[a] * (T0 - tm) : u[a] * (tp - T0);
+      const Real km = Real(0.5) * (kc + at(F_KT, a, -1));
+      const Real kp = Real(0.5) * (kc + at(F_KT, a, +1));
+      dif += kp * (tp - T0) - km * (T0 - tm);
+      if constexpr (K > 0) {
+        const Real gT = Real(0.5) * (tp - tm);
+        Real s = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          cross += P.cp[k] * d0.D[k] * Real(0.5) * (vp[a].Y[k] - vm[a].Y[k]) * gT;
+          s += P.cp[k] * P.Dlat[k] * (at(F_Y0 + k, a, +1) - at(F_Y0 + k, a, -1));
+        cross += Real(0.5) * fD * s * gT;
       }
-      const Real rhs = -phif * rho * d0.cp * adv + dif + phif * (rho * cross + dP0r + omT + SI);
-      Tn = v0.T + rhs / (phif * rho * d0.cp);
-    } else {
-      Tn = v0.Ts;
     }
+    const Real rhs = -phif * rho * cp * adv + dif + phif * (rho * cross + dP0r + omT + SI);
+    Tn = T0 + rhs * iphr * fdiv(Real(1), cp);
+  }
 
-    // solid temperature
-    if (P.Ts_field) {
-      Real Tsn = v0.Ts;
-      if (phis >= P.phi_min) {
-        Real dif = 0;
+  // solid temperature
+  if (P.Ts_field) {
+    Real Tsn = Ts0;
+    if (phis >= P.phi_min) {
+      Real dif = 0;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          const Real km = Real(0.5) * (phis + vm[a].phi) * P.Lams;
-          const Real kp = Real(0.5) * (phis + vp[a].phi) * P.Lams;
-          dif += kp * (vp[a].Ts - v0.Ts) - km * (v0.Ts - vm[a].Ts);
-        }
-        Tsn = v0.Ts + (dif - phif * SI) / (phis * P.Cs);
+      for (int a = 0; a < DIM; ++a) {
+        const Real km = Real(0.5) * (phis + at(F_PHI, a, -1)) * P.Lams;
+        const Real kp = Real(0.5) * (phis + at(F_PHI, a, +1)) * P.Lams;
+        dif += kp * (at(F_TS, a, +1) - Ts0) - km * (Ts0 - at(F_TS, a, -1));
       }
-      S.Ts_out[c] = Tsn;
+      Tsn = Ts0 + fdiv(dif - phif * SI, phis * P.Cs);
     }
+    S.Ts_out[c] = Tsn;
+  }
 
-    // low-Mach divergence D = (1/T) dT + Mw sum dY_k / M_k - dP0 / P0
-    Real D = (Tn - v0.T) / v0.T;
-    if constexpr (K > 0) {
-      Real sY = 0;
+  // low-Mach divergence D = (1/T) dT + Mw sum dY_k / M_k - dP0 / P0
+  Real D = (Tn - T0) * invT;
+  if constexpr (K > 0) {
+    Real sY = 0;
 #pragma unroll
-      for (int k = 0; k < K; ++k) sY += (Yn[k] - v0.Y[k]) * P.invM[k];
-      D += d0.Mw * sY;
-    }
-    D -= dlnP0;
+    for (int k = 0; k < K; ++k) sY += (Yn[k] - Y0[k]) * P.invM[k];
+    D += fdiv(sY, invMw);
+  }
+  D -= dlnP0;
 
-    // (a) source and BGK collision
-    Real G[3] = {0, 0, 0}, F[3] = {0, 0, 0};
+  // (a) source and BGK collision: omega = 1/tau = 2 rho / (rho + 6 mu)
+  Real G[3] = {0, 0, 0}, F[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    G[a] = CS2 * Real(0.5) * (at(F_RHO, a, +1) - at(F_RHO, a, -1));
+    F[a] = P.Fb[a] - Kd * u[a];
+  }
+  Real sg = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) sg += gin[i];
+  const Real Ph = sg + Real(0.5) * rho * CS2 * D;
+  const Real omega = fdiv(Real(2) * rho, rho + Real(6) * mu);
+  const Real src_w = Real(1) - Real(0.5) * omega;
+  Real uu = 0, uG = 0, uF = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    uu += u[a] * u[a];
+    uG += u[a] * G[a];
+    uF += u[a] * F[a];
+  }
+  const Real rD = rho * CS2 * D;
+  const Real rho3 = rho * CS2;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const Real w = Real(L::w(i));
+    Real cu = 0, cG = 0, cF = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      G[a] = CS2 * Real(0.5) * (dp[a].rho - dm[a].rho);
-      F[a] = P.Fb[a] - Kd * u[a];
+      if (L::c(i, a) > 0) { cu += u[a]; cG += G[a]; cF += F[a]; }
+      if (L::c(i, a) < 0) { cu -= u[a]; cG -= G[a]; cF -= F[a]; }
     }
-    Real sg = 0;
+    // f_eq / rho - w = w e with e = 3 cu + 9/2 cu^2 - 3/2 uu;
+    // g_eq = cs2 f_eq + w (P_h - rho cs2) = w (P_h + rho e / 3);
+    // Xi = w [(c - u).(G e + F (1 + e)) + rho cs2 D]
+    const Real e = cu * (Real(3) + Real(4.5) * cu) - Real(1.5) * uu;
+    const Real geq = w * (Ph + rho3 * e);
+    const Real xs = (cG - uG) * e + (cF - uF) * (Real(1) + e);
+    const Real xi = w * (xs + rD);
+    const Real g = gin[i] + omega * (geq - gin[i]) + src_w * xi;
+    Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g, P.g_scale * Real(1.0 / L::w(i)));
+  }
+
+  S.T_out[c] = Tn;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) sg += gin[i];
-    const Real Ph = sg + Real(0.5) * rho * CS2 * D;
-    const Real omega = Real(1) / (Real(0.5) + mu / (rho * CS2));
-    const Real src_w = Real(1) - Real(0.5) * omega;
-    Real uu = 0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) uu += u[a] * u[a];
-    const Real rD = rho * CS2 * D;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const Real w = Real(L::w(i));
-      Real cu = 0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a)
-        if (L::c(i, a) != 0) cu += Real(L::c(i, a)) * u[a];
-      // f_eq / rho - w = w e,   g_eq = w (P_h + rho (cu + 3/2 cu^2 - uu/2))
-      const Real e = Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * uu;
-      const Real geq = w * (Ph + rho * (cu + Real(1.5) * cu * cu - Real(0.5) * uu));
-      Real xs = 0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a)
-        xs += (Real(L::c(i, a)) - u[a]) * (G[a] * e + F[a] * (Real(1) + e));
-      const Real xi = w * (xs + rD);
-      const Real g = gin[i] + omega * (geq - gin[i]) + src_w * xi;
-      Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g, 0, P.g_scale / w);
+  for (int k = 0; k < K; ++k) S.Y_out[(size_t)k * P.N + c] = Yn[k];
+
+  // (d) contributions to the reduction
+  const Real fx = phif * rho * u[0];
+  fin = (xyz[0] == 0 && P.bc[0] == BC_INLET) ? fx : Real(0);
+  fout = outlet_cell ? fx : Real(0);
+  return phif * fdiv(Real(1), Tn * mixture_invMw(P, Yn));
+}
+
+// Resident blocks per SM requested from the register allocator (measured on
+// GB300: FP32/FP16 2-D and FP16 3-D run best at <= 64 registers, FP32 3-D at
+// <= 85; FP64 is FP64-pipe bound and keeps the registers it needs).
+template <int DIM, class Real, class Store> struct MinBlocks {
+  static constexpr int value = sizeof(Real) == 8 ? (DIM == 3 ? 1 : 2)
+                               : (DIM == 2 || sizeof(Store) == 2 ? 4 : 3);
+};
+
+template <int DIM, int K, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK, MinBlocks<DIM, Real, Store>::value)
+step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
+            const double* __restrict__ prev_partials) {
+  using T_ = Tile<DIM>;
+  constexpr int HP = T_::HP;
+  using PL = Plane<Real, K, HP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PL* planes = reinterpret_cast<PL*>(smem_raw);
+  __shared__ double red_sh[32];
+
+  const Real P0 = scal_P0<Real>(S.scal);
+  const Real dlnP0 = scal_dlnP0<Real>(S.scal);
+  const Real dP0r = scal_dP0r<Real>(S.scal);
+
+  const int tx = threadIdx.x % T_::TX, ty = threadIdx.x / T_::TX;
+  const int x0 = blockIdx.x * T_::TX, y0 = blockIdx.y * T_::TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const int h = (ty + 1) * T_::HX + (tx + 1);
+  const bool in_xy = x < P.nx && y < P.ny;
+  const int z_begin = blockIdx.z * T_::ZC;
+  const int z_end = DIM == 3 ? min(z_begin + T_::ZC, P.nz) : 1;
+  const bool flux_block = (x0 == 0 && P.bc[0] == BC_INLET) ||
+                          (x0 + T_::TX >= P.nx && P.bc[1] == BC_OUTLET);
+
+  // deferred combine of the previous step's partials (fixed P0 only): block
+  // 0's first warp does it while the other blocks start on their cells
+  if (prev_partials && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
+      threadIdx.x < 32)
+    combine_partials(prev_partials, gridDim.x * gridDim.y * gridDim.z, S.scal, 0, false, 0.0,
+                     P.eos_c, P.inv_rho_ref);
+
+  Real accI = 0, accIn = 0, accOut = 0;
+  if constexpr (DIM == 2) {
+    stage_plane<DIM>(P, S, planes[0], x0, y0, 0, P0);
+    __syncthreads();
+    if (in_xy) {
+      const int c = x + P.nx * y;
+      const int xyz[3] = {x, y, 0};
+      Real fi, fo;
+      accI = cell_update<DIM, K, Real, Store>(P, S, &planes[0].f[0][0], nullptr, nullptr, h, c, xyz, P0,
+                                 dlnP0, dP0r, fi, fo);
+      accIn = fi;
+      accOut = fo;
     }
-
-    S.T_out[c] = Tn;
-#pragma unroll
-    for (int k = 0; k < K; ++k) S.Y_out[(size_t)k * P.N + c] = Yn[k];
-
-    // (d) contributions to the FP64 reduction
-    const Real Mwn = mixture_Mw(P, Yn);
-    red[0] = double(phif) * double(Mwn) / double(Tn);
-    const double fx = double(phif) * double(rho) * double(u[0]);
-    if (xyz[0] == 0 && P.bc[0] == BC_INLET) red[1] = fx;
-    if (outlet_cell) red[2] = fx;
-    red[3] = double(phif) * double(rho);
+  } else {
+    // ring of three staged planes: slot (z mod 3)
+    stage_plane<DIM>(P, S, planes[(z_begin + 2) % 3], x0, y0, z_begin - 1, P0);
+    stage_plane<DIM>(P, S, planes[z_begin % 3], x0, y0, z_begin, P0);
+    for (int z = z_begin; z < z_end; ++z) {
+      stage_plane<DIM>(P, S, planes[(z + 1) % 3], x0, y0, z + 1, P0);
+      __syncthreads();
+      if (in_xy) {
+        const int c = x + P.nx * (y + P.ny * z);
+        const int xyz[3] = {x, y, z};
+        Real fi, fo;
+        accI += cell_update<DIM, K, Real, Store>(P, S, &planes[z % 3].f[0][0], &planes[(z + 2) % 3].f[0][0],
+                                    &planes[(z + 1) % 3].f[0][0], h, c, xyz, P0, dlnP0, dP0r,
+                                    fi, fo);
+        accIn += fi;
+        accOut += fo;
+      }
+      __syncthreads();
+    }
   }
-  block_sum4(red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) S.partials[4 * blockIdx.x + j] = red[j];
+
+  // (d) block partials in FP64, deterministic finish by the last block
+  const double sI = block_sum<Real>(accI, red_sh);
+  double sIn = 0, sOut = 0;
+  if (flux_block) {
+    sIn = block_sum<Real>(accIn, red_sh);
+    sOut = block_sum<Real>(accOut, red_sh);
   }
-  finish_reduction(S.partials, S.counter, S.scal, p0_closed, false, 0.0, P.eos_c);
+  publish_partials(sI, sIn, sOut, S.partials, S.counter, S.scal, p0_closed, false, 0.0, P.eos_c,
+                   P.inv_rho_ref);
+}
+
+template <int DIM, int K, class Real>
+constexpr size_t step_smem_bytes() {
+  return sizeof(Plane<Real, K, Tile<DIM>::HP>) * Tile<DIM>::NPL;
 }
 
 // ------------------------------------------------ initial equilibrium
@@ -639,15 +845,16 @@ __global__ void __launch_bounds__(BLOCK)
 init_kernel(const Params<Real, K> P, const State<Real, Store> S, const Real* __restrict__ u_init,
             double P0_init) {
   using L = Lattice<DIM>;
+  __shared__ double red_sh[32];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double red[4] = {0, 0, 0, 0};
+  Real acc = 0;
   if (c < P.N) {
-    Real T = S.T_in[c];
+    const Real T = S.T_in[c];
     Real Y[Params<Real, K>::KK];
 #pragma unroll
     for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
-    const Real Mw = mixture_Mw(P, Y);
-    const Real rho = Real(P0_init) * Mw * Real(P.eos_c) / T;
+    const Real invMw = mixture_invMw(P, Y);
+    const Real rho = Real(P0_init) * Real(P.eos_c) / (T * invMw);
     Real u[3] = {0, 0, 0};
     if (u_init)
       for (int a = 0; a < DIM; ++a) u[a] = u_init[(size_t)a * P.N + c];
@@ -659,17 +866,13 @@ init_kernel(const Params<Real, K> P, const State<Real, Store> S, const Real* __r
       Real cu = 0;
       for (int a = 0; a < DIM; ++a) cu += Real(L::c(i, a)) * u[a];
       const Real geq = w * rho * (cu + Real(1.5) * cu * cu - Real(0.5) * uu);
-      Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, geq, 0, P.g_scale / w);
+      Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, geq, P.g_scale * Real(1.0 / L::w(i)));
     }
-    const Real phif = Real(1) - S.phi[c];
-    red[0] = double(phif) * double(Mw) / double(T);
-    red[3] = double(phif) * double(rho);
+    acc = (Real(1) - S.phi[c]) / (T * invMw);
   }
-  block_sum4(red);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) S.partials[4 * blockIdx.x + j] = red[j];
-  finish_reduction(S.partials, S.counter, S.scal, 0, true, P0_init, P.eos_c);
+  const double s = block_sum<Real>(acc, red_sh);
+  publish_partials(s, 0.0, 0.0, S.partials, S.counter, S.scal, 0, true, P0_init, P.eos_c,
+                   P.inv_rho_ref);
 }
 
 // --------------------------------------------------- moments (get_fields)
@@ -688,17 +891,17 @@ moments_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __re
   xyz[0] = c % P.nx;
   xyz[1] = (c / P.nx) % P.ny;
   xyz[2] = DIM == 3 ? c / (P.nx * P.ny) : 0;
-  Real T = S.T_in[c];
+  const Real T = S.T_in[c];
   Real Y[KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
-  const Real rho = P0 * mixture_Mw(P, Y) * Real(P.eos_c) / T;
+  const Real rho = P0 * Real(P.eos_c) / (T * mixture_invMw(P, Y));
   const Real phis = S.phi[c];
   const Real Kd = P.Au_eta2 * viscosity(P, T) * (Real(1) - phis) * phis * phis;
   Real Yin[KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) Yin[k] = P.Y_in[k];
-  const Real rho_in = P0 * mixture_Mw(P, Yin) * Real(P.eos_c) / P.T_in;
+  const Real rho_in = P0 * Real(P.eos_c) / (P.T_in * mixture_invMw(P, Yin));
   const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
   Real gin[Q], u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
   for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {

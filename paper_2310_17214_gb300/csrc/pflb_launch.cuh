@@ -20,9 +20,12 @@ struct Buffers {
   void* Ts[2];
   void* phi;
   DevScalars* scal;
-  double* partials;
+  double* partials;        // two buffers of `slots` x 4 doubles (step parity)
   unsigned* counter;
   int N;
+  long long slots;         // partial slots per buffer (>= blocks of any launch)
+  int pending;             // the last step's partials are not combined yet
+  int last_parity;         // buffer holding them
 };
 
 struct Launcher {
@@ -31,9 +34,11 @@ struct Launcher {
   virtual cudaError_t init(const Buffers& B, int cur, const void* u_init, double P0,
                            cudaStream_t st) = 0;
   // nsteps fused steps; `cur` flips once per step
-  virtual cudaError_t step(const Buffers& B, int& cur, int nsteps, cudaStream_t st) = 0;
+  virtual cudaError_t step(Buffers& B, int& cur, int nsteps, cudaStream_t st) = 0;
   virtual cudaError_t moments(const Buffers& B, int cur, double* u, double* rho, double* ph,
                               cudaStream_t st) = 0;
+  // combine deferred partials of the last step into the scalar state
+  virtual cudaError_t finalize(Buffers& B, cudaStream_t st) = 0;
   virtual float g_scale() const = 0;
 };
 
@@ -54,6 +59,7 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
   }
   const double h2 = d.dt / (d.dx * d.dx);
   P.eos_c = 1.0 / (R_GAS * d.rho_ref);
+  P.eos_cr = Real(P.eos_c);
   P.inv_rho_ref = 1.0 / d.rho_ref;
   P.mu_lat = Real(d.mu_ref * h2 / d.rho_ref);
   P.sutherland = d.sutherland;
@@ -130,11 +136,21 @@ struct LauncherImpl final : Launcher {
     S.Ts_out = static_cast<Real*>(B.Ts[nxt]);
     S.phi = static_cast<const Real*>(B.phi);
     S.scal = B.scal;
-    S.partials = B.partials;
+    S.partials = B.partials + (size_t)4 * B.slots * cur;
     S.counter = B.counter;
     return S;
   }
   int blocks() const { return (P.N + BLOCK - 1) / BLOCK; }
+  // tile grid of the fused step (32 x 8 tiles; 3-D blocks march 16 planes)
+  dim3 step_grid() const {
+    using T_ = Tile<DIM>;
+    return dim3((P.nx + T_::TX - 1) / T_::TX, (P.ny + T_::TY - 1) / T_::TY,
+                DIM == 3 ? (P.nz + T_::ZC - 1) / T_::ZC : 1);
+  }
+  long long step_blocks() const {
+    dim3 g = step_grid();
+    return (long long)g.x * g.y * g.z;
+  }
 
   cudaError_t init(const Buffers& B, int cur, const void* u_init, double P0,
                    cudaStream_t st) override {
@@ -145,11 +161,30 @@ struct LauncherImpl final : Launcher {
         P, S, static_cast<const Real*>(u_init), P0);
     return cudaGetLastError();
   }
-  cudaError_t step(const Buffers& B, int& cur, int nsteps, cudaStream_t st) override {
+  // The partials of a step go to buffer `cur` (the parity of its input
+  // state); with a fixed P0 the next launch combines them in block 0.
+  cudaError_t step(Buffers& B, int& cur, int nsteps, cudaStream_t st) override {
+    constexpr size_t smem = step_smem_bytes<DIM, K, Real>();
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<DIM, K, Real, Store>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid = step_grid();
     for (int n = 0; n < nsteps; ++n) {
-      step_kernel<DIM, K, Real, Store><<<blocks(), BLOCK, 0, st>>>(P, state(B, cur), p0_closed);
+      const double* prev = (!p0_closed && B.pending)
+                               ? B.partials + (size_t)4 * B.slots * B.last_parity : nullptr;
+      step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
+                                                                   prev);
+      B.pending = p0_closed ? 0 : 1;
+      B.last_parity = cur;
       cur = 1 - cur;
     }
+    return cudaGetLastError();
+  }
+  cudaError_t finalize(Buffers& B, cudaStream_t st) override {
+    if (!B.pending) return cudaSuccess;
+    finalize_kernel<<<1, 32, 0, st>>>(B.partials + (size_t)4 * B.slots * B.last_parity,
+                                      (unsigned)step_blocks(), B.scal, P.eos_c, P.inv_rho_ref);
+    B.pending = 0;
     return cudaGetLastError();
   }
   cudaError_t moments(const Buffers& B, int cur, double* u, double* rho, double* ph,

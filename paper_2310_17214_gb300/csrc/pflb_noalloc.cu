@@ -22,9 +22,9 @@ using namespace pflb;
 namespace {
 
 constexpr int kMaxBlocks = PFLB_NOALLOC_MAX_CELLS / BLOCK;
-constexpr size_t kPartialDoubles = (size_t)kMaxBlocks * 4;
+constexpr size_t kPartialDoubles = (size_t)kMaxBlocks * 4 * 2;
 
-// Layout: [DevScalars][counter + pad to 64 bytes][partials: kMaxBlocks x 4 doubles].
+// Layout: [DevScalars][counter + pad to 64 bytes][partials: 2 x kMaxBlocks x 4 doubles].
 // Every GPU that loads the library holds this array until the process exits.
 constexpr size_t kScalarBytes = (sizeof(DevScalars) + 63) / 64 * 64;
 constexpr size_t kScratchBytes = kScalarBytes + 64 + kPartialDoubles * sizeof(double);
@@ -77,6 +77,12 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
   h.mass = scalars->mass;
   h.step = scalars->step;
   h.status = scalars->status;
+  // per-step constants the cells read (the finishing block refreshes them)
+  h.dlnP0 = (h.P0 - h.P0_prev) / h.P0;
+  h.dP0r = (h.P0 - h.P0_prev) / D.rho_ref;
+  h.P0_f = float(h.P0);
+  h.dlnP0_f = float(h.dlnP0);
+  h.dP0r_f = float(h.dP0r);
   if (cudaMemcpyAsync(base, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(base + kScalarBytes, 0, 64, st) != cudaSuccess)
     return err(PFLB_ERR_CUDA, "scratch set-up copy failed");
@@ -96,19 +102,30 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
   B.counter = reinterpret_cast<unsigned*>(base + kScalarBytes);
   B.partials = reinterpret_cast<double*>(base + kScalarBytes + 64);
   B.N = (int)N;
+  B.slots = kMaxBlocks;
+  B.pending = 0;
 
   pflb_mechanism none;
   std::memset(&none, 0, sizeof(none));
   const pflb_mechanism& M = mech ? *mech : none;
   int cur = 0;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  long long nblk = 0;
+  auto run = [&](auto& L) {
+    nblk = L.step_blocks();
+    if (nblk <= kMaxBlocks) {
+      e = L.step(B, cur, 1, st);
+      if (e == cudaSuccess) e = L.finalize(B, st);
+    }
+  };
   if (D.precision == PFLB_FP64) {
-    if (K == 0) { LauncherImpl<2, 0, MODE_FP64> L(D, M); e = L.step(B, cur, 1, st); }
-    else { LauncherImpl<2, 5, MODE_FP64> L(D, M); e = L.step(B, cur, 1, st); }
+    if (K == 0) { LauncherImpl<2, 0, MODE_FP64> L(D, M); run(L); }
+    else { LauncherImpl<2, 5, MODE_FP64> L(D, M); run(L); }
   } else {
-    if (K == 0) { LauncherImpl<2, 0, MODE_FP32> L(D, M); e = L.step(B, cur, 1, st); }
-    else { LauncherImpl<2, 5, MODE_FP32> L(D, M); e = L.step(B, cur, 1, st); }
+    if (K == 0) { LauncherImpl<2, 0, MODE_FP32> L(D, M); run(L); }
+    else { LauncherImpl<2, 5, MODE_FP32> L(D, M); run(L); }
   }
+  if (nblk > kMaxBlocks) return err(PFLB_ERR_ARG, "tile count exceeds the scratch array");
   if (e != cudaSuccess) return err(PFLB_ERR_CUDA, cudaGetErrorString(e));
   if (cudaMemcpyAsync(&h, base, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
