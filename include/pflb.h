@@ -193,6 +193,25 @@ int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where);
  * Asynchronous on the domain's stream. */
 int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
 
+/* Step kernels.  PFLB_KERNEL_TILED (default): 32 x 8 tiles staged in shared
+ * memory with per-cell properties evaluated once (2.5-D z-marching in 3-D).
+ * PFLB_KERNEL_TMA: persistent blocks, the next tile's fields and population
+ * windows fetched by the tensor memory accelerator into a double-buffered
+ * stage (2-D, FP32 compute, nx a multiple of 4 -- 8 with FP16 storage). */
+#define PFLB_KERNEL_TILED 0
+#define PFLB_KERNEL_TMA 1
+
+/* Select the step kernel of a domain (after pflb_set_fields).  Returns
+ * PFLB_ERR_UNSUPPORTED if the kernel cannot run this domain. */
+int pflb_select_kernel(pflb_domain* d, int kernel);
+
+/* Time every step kernel that can run this domain over `steps` steps each
+ * and keep the fastest (the domain's state is restored afterwards, so the
+ * physics is unchanged).  *chosen receives the kernel, *us_per_step (may be
+ * NULL) the time per step of each candidate in kernel order (2 values, a
+ * negative value for a kernel that cannot run).  Synchronises the stream. */
+int pflb_autotune(pflb_domain* d, int steps, int* chosen, double* us_per_step);
+
 /* Largest lattice (cells) that pflb_step_noalloc accepts. */
 #define PFLB_NOALLOC_MAX_CELLS (1 << 22)
 

@@ -84,6 +84,8 @@ def lib():
         L.pflb_set_state.argtypes = [vp, vp, C.c_size_t, C.c_int]
         L.pflb_step_noalloc.argtypes = [C.POINTER(Desc), C.POINTER(Mechanism), vp, vp, vp,
                                         vp, vp, vp, vp, vp, vp, C.POINTER(Scalars)]
+        L.pflb_select_kernel.argtypes = [vp, C.c_int]
+        L.pflb_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), vp]
         L.pflb_destroy.argtypes = [vp]
         L.pflb_last_error.argtypes = [vp]
         L.pflb_last_error.restype = C.c_char_p
@@ -251,6 +253,21 @@ class Domain:
         s = Scalars()
         _check(lib().pflb_get_scalars(self._h, C.byref(s)), self._h)
         return {f: getattr(s, f) for f, _ in Scalars._fields_}
+
+    KERNELS = {"tiled": 0, "tma": 1}
+
+    def select_kernel(self, name: str):
+        _check(lib().pflb_select_kernel(self._h, self.KERNELS[name]), self._h)
+
+    def autotune(self, steps: int = 20):
+        """Time each step kernel (state restored afterwards), keep the fastest.
+        Returns (chosen name, {name: us per step or None})."""
+        ch = C.c_int()
+        us = np.zeros(2)
+        _check(lib().pflb_autotune(self._h, int(steps), C.byref(ch), us.ctypes.data), self._h)
+        names = {v: k for k, v in self.KERNELS.items()}
+        return names[ch.value], {names[i]: (float(us[i]) if us[i] > 0 else None)
+                                 for i in range(2)}
 
     def state_bytes(self) -> int:
         n = C.c_size_t()

@@ -527,6 +527,58 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
   });
 }
 
+int pflb_select_kernel(pflb_domain* d, int kernel) {
+  if (!d) return fail(d, PFLB_ERR_ARG, "NULL domain");
+  if (!d->L) return fail(d, PFLB_ERR_STATE, "set_fields must come first");
+  CK(d, cudaSetDevice(d->desc.device));
+  if (!d->L->select_kernel(kernel, d->B, d->cur))
+    return fail(d, PFLB_ERR_UNSUPPORTED, "kernel not available for this domain");
+  return PFLB_OK;
+}
+
+int pflb_autotune(pflb_domain* d, int steps, int* chosen, double* us_per_step) {
+  if (!d || !chosen) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  if (!d->L) return fail(d, PFLB_ERR_STATE, "set_fields must come first");
+  if (steps < 1) return fail(d, PFLB_ERR_ARG, "steps < 1");
+  CK(d, cudaSetDevice(d->desc.device));
+  // snapshot the state on the device, time each candidate, restore
+  size_t nb = state_bytes(d);
+  void* snap = nullptr;
+  CK(d, cudaMallocAsync(&snap, nb, d->stream));
+  int r = pflb_get_state(d, snap, nb, PFLB_DEVICE);
+  if (r) { cudaFreeAsync(snap, d->stream); return r; }
+  const int prev = d->L->kernel();
+  int best = prev;
+  double best_us = -1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int k = 0; k < 2; ++k) {
+    double us = -1;
+    if (d->L->select_kernel(k, d->B, d->cur)) {
+      cudaError_t e = d->L->step(d->B, d->cur, 1, d->stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
+      if (e == cudaSuccess) e = d->L->step(d->B, d->cur, steps, d->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, d->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        us = 1e3 * ms / steps;
+      if ((r = pflb_set_state(d, snap, nb, PFLB_DEVICE))) break;
+      if (us > 0 && (best_us < 0 || us < best_us)) { best_us = us; best = k; }
+    }
+    if (us_per_step) us_per_step[k] = us;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(snap, d->stream);
+  if (r) return r;
+  d->L->select_kernel(best >= 0 ? best : prev, d->B, d->cur);
+  *chosen = d->L->kernel();
+  CK(d, cudaStreamSynchronize(d->stream));
+  return PFLB_OK;
+}
+
 int pflb_destroy(pflb_domain* d) {
   if (!d) return PFLB_OK;
   cudaSetDevice(d->desc.device);

@@ -73,9 +73,14 @@ template <> struct Lattice<3> {
   }
 };
 
-// Tile shape: 32 x 8 cells per plane; 3-D blocks march over ZC planes.
+// Tile shape: 32 x (8 RPT) cells per plane, 256 threads; in 2-D every thread
+// owns RPT rows (so a domain needs fewer resident blocks) and issues the
+// population loads of its cells before the staging barrier (PREFETCH), so
+// the two load phases overlap.  3-D blocks march over ZC planes.
 template <int DIM> struct Tile {
-  static constexpr int TX = 32, TY = 8;
+  static constexpr int RPT = DIM == 2 ? 2 : 1;
+  static constexpr bool PREFETCH = DIM == 2;
+  static constexpr int TX = 32, TY = 8 * RPT;
   static constexpr int ZC = DIM == 3 ? 16 : 1;
   static constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
   static constexpr int NPL = DIM == 3 ? 3 : 1;  // staged planes
@@ -147,18 +152,24 @@ struct State {
 
 // ----------------------------------------------------- storage codecs
 template <class Store, class Real> struct Codec;
+// load: from global memory (read-only path); get: from shared memory.
 template <> struct Codec<double, double> {
   __device__ static double load(const double* p, double) { return __ldg(p); }
+  __device__ static double get(const double* p, double) { return *p; }
   __device__ static void store(double* p, double v, double) { *p = v; }
 };
 template <> struct Codec<float, float> {
   __device__ static float load(const float* p, float) { return __ldg(p); }
+  __device__ static float get(const float* p, float) { return *p; }
   __device__ static void store(float* p, float v, float) { *p = v; }
 };
 // FP16: h = g / w * scale (weights folded so every direction has the same range)
 template <> struct Codec<__half, float> {
   __device__ static float load(const __half* p, float w_over_scale) {
     return __half2float(__ldg(p)) * w_over_scale;
+  }
+  __device__ static float get(const __half* p, float w_over_scale) {
+    return __half2float(*p) * w_over_scale;
   }
   __device__ static void store(__half* p, float v, float scale_over_w) {
     *p = __float2half_rn(v * scale_over_w);
@@ -544,40 +555,51 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
   }
 }
 
+// Staged-plane accessor: own and neighbour values of the staged fields and
+// properties (the populations come from global memory).
+template <int DIM, class Real, bool PRE = false>
+struct PlaneAcc {
+  static constexpr int HP = Tile<DIM>::HP;
+  static constexpr bool has_pops = PRE;  // populations prefetched into registers
+  const Real* __restrict__ cen;
+  const Real* __restrict__ zm;
+  const Real* __restrict__ zp;
+  int h;
+  const Real* pre;
+  __device__ __forceinline__ Real c(int f) const { return cen[f * HP + h]; }
+  __device__ __forceinline__ Real n(int f, int a, int s) const {
+    if (a == 0) return cen[f * HP + h + s];
+    if (a == 1) return cen[f * HP + h + s * Tile<DIM>::HX];
+    return (s < 0 ? zm : zp)[f * HP + h];
+  }
+  template <class Store>
+  __device__ __forceinline__ Real pop(int i, Real) const { return PRE ? pre[i] : Real(0); }
+};
+
 // ------------------------------------------------------ the fused step
 // Per cell: (a1) pull + moments + implicit drag, (c) reaction source,
 // (b) FD transport of Y_k, T, Ts, low-Mach divergence, (a) source + BGK
 // collision + store, (d) contribution to the FP64 reduction.
-template <int DIM, int K, class Real, class Store>
+template <int DIM, int K, class Real, class Store, class Acc>
 __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const State<Real, Store>& S,
-                                            const Real* __restrict__ cen,
-                                            const Real* __restrict__ zm,
-                                            const Real* __restrict__ zp, int h, int c,
-                                            const int xyz[3], Real P0, Real dlnP0, Real dP0r,
-                                            Real& fin, Real& fout) {
+                                            const Acc& A, int c, const int xyz[3], Real P0,
+                                            Real dlnP0, Real dP0r, Real& fin, Real& fout) {
   using L = Lattice<DIM>;
-  using T_ = Tile<DIM>;
   constexpr int Q = L::Q;
   constexpr int KK = Params<Real, K>::KK;
-  constexpr int HP = T_::HP;
   constexpr Real CS2 = Real(1) / Real(3);
-  // neighbour offsets inside a staged plane (x, y) and the z planes
-  auto at = [&](int f, int a, int s) -> Real {
-    if (a == 0) return cen[f * HP + h + s];
-    if (a == 1) return cen[f * HP + h + s * T_::HX];
-    return (s < 0 ? zm : zp)[f * HP + h];
-  };
+  auto at = [&](int f, int a, int s) -> Real { return A.n(f, a, s); };
 
-  const Real T0 = cen[F_T * HP + h];
-  const Real phis = cen[F_PHI * HP + h];
+  const Real T0 = A.c(F_T);
+  const Real phis = A.c(F_PHI);
   const Real phif = Real(1) - phis;
-  const Real rho = cen[F_RHO * HP + h];
-  const Real mu = cen[F_MU * HP + h];
-  const Real fD = cen[F_FD * HP + h];
-  const Real Ts0 = cen[F_TS * HP + h];
+  const Real rho = A.c(F_RHO);
+  const Real mu = A.c(F_MU);
+  const Real fD = A.c(F_FD);
+  const Real Ts0 = A.c(F_TS);
   Real Y0[KK];
 #pragma unroll
-  for (int k = 0; k < K; ++k) Y0[k] = cen[(F_Y0 + k) * HP + h];
+  for (int k = 0; k < K; ++k) Y0[k] = A.c(F_Y0 + k);
   const Real invMw = mixture_invMw(P, Y0);
   const Real cp = mixture_cp(P, Y0);
   const Real lam = mu * cp * P.inv_Pr;
@@ -600,7 +622,13 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
   const Real inv_rk = fdiv(Real(1), rho + Real(0.5) * Kd);
   for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
-    pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin);
+    if (Acc::has_pops && !edge) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        gin[i] = A.template pop<Store>(i, Real(L::w(i)) * P.g_inv_scale);
+    } else {
+      pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin);
+    }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       Real m = 0;
@@ -626,7 +654,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   }
 
   const Real iphr = fluid_on ? fdiv(Real(1), phif * rho) : Real(0);
-  const Real rf0 = cen[F_RF * HP + h];
+  const Real rf0 = A.c(F_RF);
 
   // (b) species
   Real Yn[KK];
@@ -648,7 +676,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   Real Tn = Ts0;
   if (fluid_on) {
     Real adv = 0, dif = 0, cross = 0;
-    const Real kc = cen[F_KT * HP + h];
+    const Real kc = A.c(F_KT);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const Real tm = at(F_T, a, -1), tp = at(F_T, a, +1);
@@ -790,16 +818,42 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
 
   Real accI = 0, accIn = 0, accOut = 0;
   if constexpr (DIM == 2) {
+    using L = Lattice<2>;
+    constexpr int RPT = T_::RPT;
+    constexpr int RS = T_::TY / RPT;  // row stride between a thread's cells
+    // population loads of the thread's interior cells, issued before staging
+    Real pre[RPT][L::Q];
+    if constexpr (T_::PREFETCH) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int yr = y0 + ty + r * RS;
+        const bool inner = x > 0 && x < P.nx - 1 && yr > 0 && yr < P.ny - 1;
+        if (inner) {
+          const int c = x + P.nx * yr;
+#pragma unroll
+          for (int i = 0; i < L::Q; ++i)
+            pre[r][i] = Codec<Store, Real>::load(
+                S.g_in + (size_t)i * P.N + c - L::c(i, 0) - L::c(i, 1) * P.nx,
+                Real(L::w(i)) * P.g_inv_scale);
+        }
+      }
+    }
     stage_plane<DIM>(P, S, planes[0], x0, y0, 0, P0);
     __syncthreads();
-    if (in_xy) {
-      const int c = x + P.nx * y;
-      const int xyz[3] = {x, y, 0};
-      Real fi, fo;
-      accI = cell_update<DIM, K, Real, Store>(P, S, &planes[0].f[0][0], nullptr, nullptr, h, c, xyz, P0,
-                                 dlnP0, dP0r, fi, fo);
-      accIn = fi;
-      accOut = fo;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int yr = y0 + ty + r * RS;
+      if (x < P.nx && yr < P.ny) {
+        const int c = x + P.nx * yr;
+        const int xyz[3] = {x, yr, 0};
+        const int hr = (ty + r * RS + 1) * T_::HX + (tx + 1);
+        Real fi, fo;
+        const PlaneAcc<DIM, Real, T_::PREFETCH> A{&planes[0].f[0][0], nullptr, nullptr, hr,
+                                                  pre[r]};
+        accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
+        accIn += fi;
+        accOut += fo;
+      }
     }
   } else {
     // ring of three staged planes: slot (z mod 3)
@@ -812,9 +866,9 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
         const int c = x + P.nx * (y + P.ny * z);
         const int xyz[3] = {x, y, z};
         Real fi, fo;
-        accI += cell_update<DIM, K, Real, Store>(P, S, &planes[z % 3].f[0][0], &planes[(z + 2) % 3].f[0][0],
-                                    &planes[(z + 1) % 3].f[0][0], h, c, xyz, P0, dlnP0, dP0r,
-                                    fi, fo);
+        const PlaneAcc<DIM, Real> A{&planes[z % 3].f[0][0], &planes[(z + 2) % 3].f[0][0],
+                                    &planes[(z + 1) % 3].f[0][0], h, nullptr};
+        accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
       }

@@ -8,8 +8,11 @@
 #include <cmath>
 #include <cstring>
 
+#include <type_traits>
+
 #include "../../include/pflb.h"
 #include "pflb_kernels.cuh"
+#include "pflb_tma.cuh"
 
 namespace pflb {
 
@@ -26,7 +29,46 @@ struct Buffers {
   long long slots;         // partial slots per buffer (>= blocks of any launch)
   int pending;             // the last step's partials are not combined yet
   int last_parity;         // buffer holding them
+  long long last_nb;       // blocks of the launch that wrote them
 };
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tiled tensor map of a row-major array with `rank` dims (x fastest).
+inline bool encode_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int esz,
+                       int rank, const unsigned long long* dims, const unsigned* box) {
+  EncodeTiledFn f = encode_tiled();
+  if (!f) return false;
+  cuuint64_t gd[3], gs[2];
+  cuuint32_t bd[3], es[3] = {1, 1, 1};
+  unsigned long long stride = (unsigned long long)esz;
+  for (int r = 0; r < rank; ++r) {
+    gd[r] = dims[r];
+    bd[r] = box[r];
+    if (r > 0) gs[r - 1] = stride;
+    stride *= dims[r];
+  }
+  return f(m, dt, rank, const_cast<void*>(base), gd, gs, bd, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 struct Launcher {
   virtual ~Launcher() {}
@@ -39,6 +81,10 @@ struct Launcher {
                               cudaStream_t st) = 0;
   // combine deferred partials of the last step into the scalar state
   virtual cudaError_t finalize(Buffers& B, cudaStream_t st) = 0;
+  // step kernel: 0 = staged tiles, 1 = TMA-pipelined persistent tiles (2-D
+  // FP32 compute with 16-byte rows); returns false if not available here
+  virtual bool select_kernel(int k, const Buffers& B, int cur) = 0;
+  virtual int kernel() const = 0;
   virtual float g_scale() const = 0;
 };
 
@@ -163,6 +209,99 @@ struct LauncherImpl final : Launcher {
   }
   // The partials of a step go to buffer `cur` (the parity of its input
   // state); with a fixed P0 the next launch combines them in block 0.
+  // ---- TMA path (2-D, FP32 compute): maps per input parity, persistent grid
+  static constexpr bool kTmaType = DIM == 2 && std::is_same<Real, float>::value;
+  TmaMaps maps[2];
+  const void* map_key[2][5] = {};
+  int tma_state = 0;  // 0 unknown, 1 usable, -1 not usable
+  int tma_grid = 0;
+  int kernel_sel = 0;
+
+  bool select_kernel(int k, const Buffers& B, int cur) override {
+    if (k == 0) { kernel_sel = 0; return true; }
+    if (k == 1 && tma_usable(B, cur) && tma_usable(B, 1 - cur)) { kernel_sel = 1; return true; }
+    return false;
+  }
+  int kernel() const override { return kernel_sel; }
+
+  bool tma_usable(const Buffers& B, int cur) {
+    if constexpr (!kTmaType) {
+      return false;
+    } else {
+      using LY = TmaLayout<K, Store>;
+      if (tma_state < 0) return false;
+      if (tma_state == 0) {
+        // rows must be whole 16-byte units for every array the boxes read
+        if (P.nx % (16 / (int)sizeof(Store)) != 0 || P.nx % 4 != 0 || !encode_tiled()) {
+          tma_state = -1;
+          return false;
+        }
+        auto kern = step_tma_kernel<K, Store>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)LY::smem_bytes) != cudaSuccess) {
+          tma_state = -1;
+          return false;
+        }
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BLOCK, LY::smem_bytes);
+        const long long tiles = (long long)((P.nx + LY::TX - 1) / LY::TX) *
+                                ((P.ny + LY::TY - 1) / LY::TY);
+        if (per < 1 || sms < 1) {
+          tma_state = -1;
+          return false;
+        }
+        tma_grid = (int)std::min<long long>(tiles, (long long)sms * per);
+        if (tma_grid > B.slots) tma_grid = (int)B.slots;
+        tma_state = 1;
+      }
+      const void* key[5] = {B.g[cur], B.T[cur], B.Y[cur], B.Ts[cur], B.phi};
+      bool same = true;
+      for (int j = 0; j < 5; ++j) same = same && map_key[cur][j] == key[j];
+      if (!same) {
+        const unsigned long long nx = P.nx, ny = P.ny;
+        const unsigned fb[3] = {(unsigned)LY::FW, (unsigned)LY::FH, (unsigned)(K > 0 ? K : 1)};
+        const unsigned long long d2[2] = {nx, ny};
+        const unsigned long long dY[3] = {nx, ny, (unsigned long long)(K > 0 ? K : 1)};
+        const unsigned long long dg[3] = {nx, ny, 9ull};
+        const unsigned pb[3] = {(unsigned)LY::PW, (unsigned)LY::PH, 1u};
+        const CUtensorMapDataType gdt = sizeof(Store) == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        TmaMaps& m = maps[cur];
+        const void* Ts = B.Ts[cur] ? B.Ts[cur] : B.T[cur];
+        const void* Y = K > 0 ? B.Y[cur] : B.T[cur];
+        bool ok = encode_map(&m.T, B.T[cur], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2, d2, fb) &&
+                  encode_map(&m.phi, B.phi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2, d2, fb) &&
+                  encode_map(&m.Ts, Ts, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2, d2, fb) &&
+                  (K > 0 ? encode_map(&m.Y, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 3, dY, fb)
+                         : encode_map(&m.Y, Y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2, d2, fb)) &&
+                  encode_map(&m.g, B.g[cur], gdt, (int)sizeof(Store), 3, dg, pb);
+        if (!ok) {
+          tma_state = -1;
+          return false;
+        }
+        for (int j = 0; j < 5; ++j) map_key[cur][j] = key[j];
+      }
+      return true;
+    }
+  }
+
+  cudaError_t step_tma(Buffers& B, int cur, cudaStream_t st, const double* prev) {
+    if constexpr (kTmaType) {
+      using LY = TmaLayout<K, Store>;
+      const int tiles_x = (P.nx + LY::TX - 1) / LY::TX;
+      const int n_tiles = tiles_x * ((P.ny + LY::TY - 1) / LY::TY);
+      const TmaMaps& m = maps[cur];
+      step_tma_kernel<K, Store><<<tma_grid, BLOCK, LY::smem_bytes, st>>>(
+          P, state(B, cur), p0_closed, prev, m.T, m.phi, m.Ts, m.Y, m.g, tiles_x, n_tiles);
+      B.last_nb = tma_grid;
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+
   cudaError_t step(Buffers& B, int& cur, int nsteps, cudaStream_t st) override {
     constexpr size_t smem = step_smem_bytes<DIM, K, Real>();
     cudaError_t e = cudaFuncSetAttribute(step_kernel<DIM, K, Real, Store>,
@@ -172,8 +311,14 @@ struct LauncherImpl final : Launcher {
     for (int n = 0; n < nsteps; ++n) {
       const double* prev = (!p0_closed && B.pending)
                                ? B.partials + (size_t)4 * B.slots * B.last_parity : nullptr;
-      step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
-                                                                   prev);
+      if (kernel_sel == 1 && tma_usable(B, cur)) {
+        e = step_tma(B, cur, st, prev);
+        if (e != cudaSuccess) return e;
+      } else {
+        step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
+                                                                     prev);
+        B.last_nb = step_blocks();
+      }
       B.pending = p0_closed ? 0 : 1;
       B.last_parity = cur;
       cur = 1 - cur;
@@ -183,7 +328,7 @@ struct LauncherImpl final : Launcher {
   cudaError_t finalize(Buffers& B, cudaStream_t st) override {
     if (!B.pending) return cudaSuccess;
     finalize_kernel<<<1, 32, 0, st>>>(B.partials + (size_t)4 * B.slots * B.last_parity,
-                                      (unsigned)step_blocks(), B.scal, P.eos_c, P.inv_rho_ref);
+                                      (unsigned)B.last_nb, B.scal, P.eos_c, P.inv_rho_ref);
     B.pending = 0;
     return cudaGetLastError();
   }

@@ -193,3 +193,86 @@ def test_fp32_reactive_small():
     got, ref, sc, ora = run_pair(p, f, 200, precision="fp32")
     assert l2rel(got["T"], ref["T"]) <= 1e-5
     assert l2rel(got["u"], ref["u"]) <= 1e-3
+
+
+# ------------------------------------------------------- kernel variants
+def _two_kernels(p, f, precision, nsteps):
+    out = {}
+    for kern in ("tiled", "tma"):
+        dom = Domain(p, precision)
+        dom.set_phase_field(f["phi"], f["Ts"])
+        dom.set_fields(f["T"], f["Y"], f.get("u"))
+        dom.select_kernel(kern)
+        dom.step(nsteps)
+        out[kern] = dom.get(*(["T", "g", "u"] + (["Y"] if p.get("K") else [])))
+        out[kern]["P0"] = dom.scalars()["P0"]
+        dom.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16"])
+def test_tma_kernel_agrees_with_tiled_kernel(precision):
+    """The TMA-pipelined kernel runs the same per-cell arithmetic on staged
+    copies of the same data: results agree to FP32 rounding."""
+    p = I.config1()
+    f = I.with_initial_u(p, I.config1_fields(p))
+    out = _two_kernels(p, f, precision, 300)
+    for k in ("T", "g", "u"):
+        assert maxrel(out["tma"][k], out["tiled"][k]) <= 1e-6, k
+    p = I.config2(nx=160, ny=48, precision=precision)
+    p["bed"] = {"count": 6, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 40}
+    p["reactions"] = I.one_step_mechanism(3.3e8)
+    f = I.config2_fields(p)
+    out = _two_kernels(p, f, precision, 200)
+    for k in ("T", "g", "u", "Y"):
+        assert maxrel(out["tma"][k], out["tiled"][k]) <= 1e-6, k
+
+
+def test_tma_kernel_against_oracle_fp32():
+    p = I.config1()
+    f = I.with_initial_u(p, I.config1_fields(p))
+    ora = O.OracleState(p, f["phi"], f["T"], u=f["u"])
+    ora.step(1000)
+    u_ref, _, _ = ora.moments()
+    dom = Domain(p, "fp32")
+    dom.set_phase_field(f["phi"])
+    dom.set_fields(f["T"], None, f["u"])
+    dom.select_kernel("tma")
+    dom.step(1000)
+    got = dom.get("T", "u")
+    dom.close()
+    assert l2rel(got["u"], u_ref) <= 1e-4
+    assert l2rel(got["T"] - 300.0, ora.T - 300.0) <= 1e-4
+
+
+def test_autotune_keeps_the_physics():
+    p = I.config2(nx=256, ny=64, precision="fp32")
+    p["bed"] = {"count": 8, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 80}
+    f = I.config2_fields(p)
+    ref = Domain(p, "fp32")
+    ref.set_phase_field(f["phi"], f["Ts"])
+    ref.set_fields(f["T"], f["Y"])
+    ref.step(50)
+    a = ref.get("T", "g")
+    ref.close()
+    dom = Domain(p, "fp32")
+    dom.set_phase_field(f["phi"], f["Ts"])
+    dom.set_fields(f["T"], f["Y"])
+    chosen, times = dom.autotune(10)
+    assert chosen in ("tiled", "tma") and times["tiled"] is not None
+    assert dom.scalars()["step"] == 0
+    dom.select_kernel("tiled")
+    dom.step(50)
+    b = dom.get("T", "g")
+    dom.close()
+    assert np.array_equal(a["T"], b["T"]) and np.array_equal(a["g"], b["g"])
+    # a lattice whose rows are not 16-byte multiples cannot use the TMA kernel
+    q = I.config2(nx=250, ny=40, precision="fp32")
+    q["bed"] = {"count": 4, "amin": 6, "amax": 9, "porosity": 0.6, "x0": 80}
+    g = I.config2_fields(q)
+    d2 = Domain(q, "fp32")
+    d2.set_phase_field(g["phi"], g["Ts"])
+    d2.set_fields(g["T"], g["Y"])
+    chosen, times = d2.autotune(5)
+    assert chosen == "tiled" and times["tma"] is None
+    d2.close()
