@@ -74,11 +74,13 @@ template <> struct Lattice<3> {
 };
 
 // Tile shape: 32 x (8 RPT) cells per plane, 256 threads; in 2-D every thread
-// owns RPT rows (so a domain needs fewer resident blocks) and issues the
-// population loads of its cells before the staging barrier (PREFETCH), so
-// the two load phases overlap.  3-D blocks march over ZC planes.
+// can own RPT rows and issues the population loads of its cells before the
+// staging barrier (PREFETCH), so the two load phases overlap.  Measured on
+// GB300: one row per thread is fastest (two rows spill at the 64-register
+// cap); the prefetch helps the FP16-stored path.  3-D blocks march over ZC
+// planes.
 template <int DIM> struct Tile {
-  static constexpr int RPT = DIM == 2 ? 2 : 1;
+  static constexpr int RPT = 1;
   static constexpr bool PREFETCH = DIM == 2;
   static constexpr int TX = 32, TY = 8 * RPT;
   static constexpr int ZC = DIM == 3 ? 16 : 1;
