@@ -66,6 +66,7 @@ extern "C" {
 /* chemistry */
 #define PFLB_CHEM_NONE 0
 #define PFLB_CHEM_EXPLICIT 1    /* forward-Euler Arrhenius source */
+#define PFLB_CHEM_IMPLICIT 2    /* per-cell backward Euler + Newton, FP64 (operator split) */
 
 #define PFLB_HOST 0
 #define PFLB_DEVICE 1
@@ -117,11 +118,13 @@ typedef struct pflb_domain_desc {
 } pflb_domain_desc;
 
 /* Species thermochemistry and reactions (Sec. 3.2.2 eq. 8, Sec. 3.3 eq. 9).
- * Q_j = A_j T^b_j exp(-EaR_j / T) prod_k C_k^order_jk, C_k = rho Y_k / M_k. */
+ * Q_j = A_j T^b_j exp(-EaR_j / T) prod_k C_k^order_jk, C_k = rho Y_k / M_k,
+ * minus, for a reversible reaction, Q_j,r = (k_f / K_c) prod_k C_k^rorder_jk with
+ * K_c = exp(dS_j/R - dH_j/(R T)) (p_ref/(R T))^(sum_k stoich_jk). */
 typedef struct pflb_mechanism {
   int K;                   /* species (0, 5 or 6 are compiled) */
   int J;                   /* reactions, <= PFLB_JMAX */
-  int chem_mode;           /* PFLB_CHEM_NONE / PFLB_CHEM_EXPLICIT */
+  int chem_mode;           /* PFLB_CHEM_NONE / _EXPLICIT / _IMPLICIT */
   double M[PFLB_KMAX];     /* kg/mol */
   double cp[PFLB_KMAX];    /* J/kg/K (constant) */
   double hf[PFLB_KMAX];    /* formation enthalpy, J/kg */
@@ -131,6 +134,10 @@ typedef struct pflb_mechanism {
   double A[PFLB_JMAX], b[PFLB_JMAX], EaR[PFLB_JMAX];
   double order[PFLB_JMAX][PFLB_KMAX];
   double stoich[PFLB_JMAX][PFLB_KMAX];
+  int rev[PFLB_JMAX];      /* 1: reversible */
+  double dH[PFLB_JMAX], dS[PFLB_JMAX];    /* standard reaction enthalpy (J/mol), entropy (J/mol/K) */
+  double rorder[PFLB_JMAX][PFLB_KMAX];    /* reverse orders */
+  double p_ref;            /* standard pressure of K_c (Pa) */
 } pflb_mechanism;
 
 typedef struct pflb_scalars {

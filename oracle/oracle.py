@@ -52,6 +52,8 @@ class OrcParams(C.Structure):
         ("chem_mode", C.c_int), ("J", C.c_int),
         ("A", C.c_double * JMAX), ("b", C.c_double * JMAX), ("EaR", C.c_double * JMAX),
         ("order", (C.c_double * KMAX) * JMAX), ("stoich", (C.c_double * KMAX) * JMAX),
+        ("rev", C.c_int * JMAX), ("dH", C.c_double * JMAX), ("dS", C.c_double * JMAX),
+        ("rorder", (C.c_double * KMAX) * JMAX), ("p_ref", C.c_double),
     ]
 
 
@@ -81,6 +83,9 @@ def lib():
         L.orc_equilibrium.argtypes = [C.c_int, C.c_double, C.c_double, dp, dp]
         L.orc_source.argtypes = [C.c_int, C.c_double, dp, dp, dp, C.c_double, dp]
         L.orc_chem_rates.argtypes = [P, C.c_double, dp, C.c_double, dp, C.POINTER(C.c_double)]
+        L.orc_chem_implicit.argtypes = [P, C.c_double, dp, C.c_double, dp,
+                                        C.POINTER(C.c_double)]
+        L.orc_chem_implicit.restype = C.c_int
         L.orc_fd_phase.argtypes = [P, dp, dp, dp, C.c_void_p, dp, C.c_double, C.c_double,
                                    dp, dp, C.c_void_p]
         L.orc_init.argtypes = [P, dp, dp, dp, dp, C.c_void_p, C.c_void_p, C.c_double, dp]
@@ -140,6 +145,12 @@ def make_params(prob: dict) -> OrcParams:
         for k in range(K):
             p.order[j][k] = r["order"][k]
             p.stoich[j][k] = r["stoich"][k]
+        if r.get("reverse"):
+            p.rev[j] = 1
+            p.dH[j], p.dS[j] = r["reverse"]["dH"], r["reverse"]["dS"]
+            for k in range(K):
+                p.rorder[j][k] = r["reverse"]["order"][k]
+    p.p_ref = prob.get("p_ref", 101325.0)
     return p
 
 
@@ -247,3 +258,13 @@ def fd_phase(prob, phi, T, Y, Ts, u, P0, P0prev):
     lib().orc_fd_phase(C.byref(p), f64(phi), f64(T), Yin, _ptr(None if Ts is None else f64(Ts)),
                        f64(u), float(P0), float(P0prev), Tn, Yn, _ptr(Tsn))
     return Tn, (Yn[: K * N] if K > 0 else None), Tsn
+
+
+def chem_implicit(prob, T, Y, rho_lat):
+    """Backward-Euler chemistry increments (dY[K], dT) over one step."""
+    p = make_params(prob)
+    dY = np.zeros(KMAX)
+    dT = C.c_double()
+    rc = lib().orc_chem_implicit(C.byref(p), float(T), np.ascontiguousarray(Y, dtype=np.float64),
+                                 float(rho_lat), dY, C.byref(dT))
+    return dY[: prob["K"]].copy(), dT.value, rc

@@ -76,6 +76,10 @@ typedef struct {
   int chem_mode, J;
   double A[ORC_JMAX], b[ORC_JMAX], EaR[ORC_JMAX];
   double order[ORC_JMAX][ORC_KMAX], stoich[ORC_JMAX][ORC_KMAX];
+  /* reversible reactions: K_c from standard dH, dS (ideal gas, p_ref) */
+  int rev[ORC_JMAX];
+  double dH[ORC_JMAX], dS[ORC_JMAX], rorder[ORC_JMAX][ORC_KMAX];
+  double p_ref;
 } orc_params;
 
 /* ---------------------------------------------------------------- lattices */
@@ -191,6 +195,22 @@ static void derive(const orc_params* p, const cellv* v, double P0, derv* d) {
   }
 }
 
+/* Rate constants of reaction j at T: forward k_f = A T^b exp(-Ea/RT) and,
+ * for a reversible reaction, k_r = k_f / K_c with
+ * K_c = exp(dS/R - dH/(R T)) (p_ref/(R T))^(sum_k s_kj)  (mass action, ideal gas). */
+static void rate_constants(const orc_params* p, int j, double T, double* kf, double* kr) {
+  double k = p->A[j] * exp(-p->EaR[j] / T);
+  if (p->b[j] != 0.0) k *= pow(T, p->b[j]);
+  *kf = k;
+  *kr = 0.0;
+  if (p->rev[j]) {
+    double dn = 0;
+    for (int m = 0; m < p->K; ++m) dn += p->stoich[j][m];
+    double Kc = exp(p->dS[j] / ORC_R - p->dH[j] / (ORC_R * T)) * pow(p->p_ref / (ORC_R * T), dn);
+    *kr = k / Kc;
+  }
+}
+
 /* Explicit rates: Q_j = A T^b exp(-Ea/RT) prod C_k^order, C_k = rho Y_k / M_k
  * (mol/m^3); omega_k = M_k sum_j s_kj Q_j (Sec. 3.2.2, eq. 8), omega_T =
  * -sum hf_k omega_k (Sec. 3.3, eq. 9).  Outputs are per lattice step per
@@ -208,10 +228,17 @@ void orc_chem_rates(const orc_params* p, double T, const double* Y, double rho_l
   for (int k = 0; k < p->K; ++k) C[k] = rho * (Y[k] > 0 ? Y[k] : 0.0) / p->M[k];
   for (int k = 0; k < p->K; ++k) omega[k] = 0;
   for (int j = 0; j < p->J; ++j) {
-    double q = p->A[j] * exp(-p->EaR[j] / T);
-    if (p->b[j] != 0.0) q *= pow(T, p->b[j]);
+    double kf, kr;
+    rate_constants(p, j, T, &kf, &kr);
+    double q = kf;
     for (int k = 0; k < p->K; ++k)
       if (p->order[j][k] != 0.0) q *= powi_or_pow(C[k], p->order[j][k]);
+    if (p->rev[j]) {
+      double qr = kr;
+      for (int k = 0; k < p->K; ++k)
+        if (p->rorder[j][k] != 0.0) qr *= powi_or_pow(C[k], p->rorder[j][k]);
+      q -= qr;
+    }
     for (int k = 0; k < p->K; ++k) omega[k] += p->M[k] * p->stoich[j][k] * q;
   }
   double wt = 0;
@@ -220,6 +247,149 @@ void orc_chem_rates(const orc_params* p, double T, const double* Y, double rho_l
     wt -= p->hf[k] * omega[k];
   }
   *omegaT = wt;
+}
+
+/* ------------------------------------------------- implicit chemistry
+ * Backward Euler over one step for the chemistry alone at frozen density
+ * (operator splitting): with z = (Y_1..Y_K, T),
+ *   dY_k/dt = omega_k / rho,   dT/dt = omega_T / (rho cp(Y))   (Sec. 3.2.2 eq. 8,
+ *   Sec. 3.3 eqs. energy-transport-DI-version and 9, chemistry terms only),
+ * solve G(z) = z - z0 - dt F(z) = 0 by Newton with the analytic Jacobian and a
+ * dense Gaussian elimination with partial pivoting.  If Newton does not
+ * converge (or leaves the physical range) the step is split into 2, 4, ...,
+ * 64 equal backward-Euler sub-steps. */
+#define ORC_NMAX (ORC_KMAX + 1)
+
+/* physical rates and their Jacobian: w[k] = omega_k (kg/m^3/s), dw[k][m] =
+ * d omega_k / d z_m (z = Y..., T) at density rho (kg/m^3) */
+static void rates_and_jacobian(const orc_params* p, const double* z, double rho, double* w,
+                               double dw[ORC_KMAX][ORC_NMAX]) {
+  int K = p->K;
+  double T = z[K];
+  double C[ORC_KMAX], dC[ORC_KMAX];
+  for (int k = 0; k < K; ++k) {
+    C[k] = z[k] > 0 ? rho * z[k] / p->M[k] : 0.0;
+    dC[k] = z[k] > 0 ? rho / p->M[k] : 0.0;
+    w[k] = 0;
+    for (int m = 0; m <= K; ++m) dw[k][m] = 0;
+  }
+  for (int j = 0; j < p->J; ++j) {
+    double kf, kr;
+    rate_constants(p, j, T, &kf, &kr);
+    /* d ln kf / dT and d ln kr / dT */
+    double dlkf = p->EaR[j] / (T * T) + p->b[j] / T;
+    double dlkr = dlkf;
+    if (p->rev[j]) {
+      double dn = 0;
+      for (int m = 0; m < K; ++m) dn += p->stoich[j][m];
+      dlkr = dlkf - (p->dH[j] / (ORC_R * T * T) + dn / T);
+    }
+    double dq[ORC_NMAX];
+    for (int m = 0; m <= K; ++m) dq[m] = 0;
+    for (int dir = 0; dir < (p->rev[j] ? 2 : 1); ++dir) {
+      const double* ord = dir == 0 ? p->order[j] : p->rorder[j];
+      double kk = dir == 0 ? kf : kr, sign = dir == 0 ? 1.0 : -1.0;
+      double prod = 1.0;
+      for (int k = 0; k < K; ++k)
+        if (ord[k] != 0.0) prod *= powi_or_pow(C[k], ord[k]);
+      double q = sign * kk * prod;
+      for (int k = 0; k < K; ++k) w[k] += p->M[k] * p->stoich[j][k] * q;
+      dq[K] += q * (dir == 0 ? dlkf : dlkr);
+      for (int m = 0; m < K; ++m) {
+        if (ord[m] == 0.0 || dC[m] == 0.0) continue;
+        double rest = 1.0;
+        for (int k = 0; k < K; ++k)
+          if (k != m && ord[k] != 0.0) rest *= powi_or_pow(C[k], ord[k]);
+        double dpow = ord[m] == 1.0 ? 1.0 : ord[m] * pow(C[m], ord[m] - 1.0);
+        dq[m] += sign * kk * rest * dpow * dC[m];
+      }
+    }
+    for (int k = 0; k < K; ++k)
+      for (int m = 0; m <= K; ++m) dw[k][m] += p->M[k] * p->stoich[j][k] * dq[m];
+  }
+}
+
+static int solve_dense(int n, double A[ORC_NMAX][ORC_NMAX], double* b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (A[piv][c] == 0.0) return -1;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) { double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t; }
+      double t = b[c]; b[c] = b[piv]; b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r][c] / A[c][c];
+      for (int k = c; k < n; ++k) A[r][k] -= f * A[c][k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s2 = b[r];
+    for (int k = r + 1; k < n; ++k) s2 -= A[r][k] * b[k];
+    b[r] = s2 / A[r][r];
+  }
+  return 0;
+}
+
+/* one backward-Euler step of length h from z0; returns 0 on convergence */
+static int be_newton(const orc_params* p, const double* z0, double rho, double h, double* z) {
+  int K = p->K, n = K + 1;
+  for (int m = 0; m < n; ++m) z[m] = z0[m];
+  for (int it = 0; it < 30; ++it) {
+    double w[ORC_KMAX], dw[ORC_KMAX][ORC_NMAX], A[ORC_NMAX][ORC_NMAX], r[ORC_NMAX];
+    rates_and_jacobian(p, z, rho, w, dw);
+    double cp = mixture_cp(p, z), hw = 0;
+    for (int k = 0; k < K; ++k) hw += p->hf[k] * w[k];
+    /* F_T = -hw / (rho cp) */
+    for (int k = 0; k < K; ++k) {
+      r[k] = -(z[k] - z0[k] - h * w[k] / rho);
+      for (int m = 0; m < n; ++m) A[k][m] = (k == m ? 1.0 : 0.0) - h * dw[k][m] / rho;
+    }
+    r[K] = -(z[K] - z0[K] - h * (-hw / (rho * cp)));
+    for (int m = 0; m < n; ++m) {
+      double dhw = 0;
+      for (int k = 0; k < K; ++k) dhw += p->hf[k] * dw[k][m];
+      double dFT = -dhw / (rho * cp);
+      if (m < K) dFT += hw * p->cp[m] / (rho * cp * cp);
+      A[K][m] = (m == K ? 1.0 : 0.0) - h * dFT;
+    }
+    if (solve_dense(n, A, r)) return -1;
+    double big = 0;
+    for (int m = 0; m < n; ++m) {
+      z[m] += r[m];
+      double sc = m < K ? 1.0 : z0[K];
+      double e = fabs(r[m]) / sc;
+      if (!(e == e)) return -1;
+      if (e > big) big = e;
+    }
+    if (!(z[K] > 0)) return -1;
+    if (big < 1e-13) return 0;
+  }
+  return -1;
+}
+
+/* chemistry increments over one lattice step: dY[k], dT (K) */
+int orc_chem_implicit(const orc_params* p, double T, const double* Y, double rho_lat, double* dY,
+                      double* dT) {
+  int K = p->K;
+  double rho = rho_lat * p->rho_ref;
+  double z0[ORC_NMAX], z[ORC_NMAX], zs[ORC_NMAX];
+  for (int k = 0; k < K; ++k) z0[k] = Y[k];
+  z0[K] = T;
+  int ok = -1;
+  for (int nsub = 1; nsub <= 64 && ok; nsub *= 2) {
+    for (int m = 0; m <= K; ++m) zs[m] = z0[m];
+    ok = 0;
+    for (int s2 = 0; s2 < nsub && !ok; ++s2) {
+      ok = be_newton(p, zs, rho, p->dt / nsub, z);
+      for (int m = 0; m <= K; ++m) zs[m] = z[m];
+    }
+  }
+  for (int k = 0; k < K; ++k) dY[k] = zs[k] - Y[k];
+  *dT = zs[K] - T;
+  return ok;
 }
 
 /* ----------------------------------------------------------- grid helpers */
@@ -327,8 +497,15 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
 
     /* species */
     double omega[ORC_KMAX] = {0}, omegaT = 0;
-    if (p->chem_mode == ORC_CHEM_EXPLICIT && K > 0)
+    if (p->chem_mode == ORC_CHEM_EXPLICIT && K > 0 && fluid_on)
       orc_chem_rates(p, v0.T, v0.Y, d0.rho, omega, &omegaT);
+    if (p->chem_mode == ORC_CHEM_IMPLICIT && K > 0 && fluid_on) {
+      /* the implicit increments enter the FD update as rho dY_k and rho cp dT */
+      double dY[ORC_KMAX], dT;
+      orc_chem_implicit(p, v0.T, v0.Y, d0.rho, dY, &dT);
+      for (int k = 0; k < K; ++k) omega[k] = d0.rho * dY[k];
+      omegaT = d0.rho * d0.cp * dT;
+    }
     for (int k = 0; k < K; ++k) {
       if (!fluid_on) { Yn[(size_t)k * N + c] = v0.Y[k]; continue; }
       double adv = 0, dif = 0;

@@ -14,7 +14,7 @@ KMAX, JMAX = 8, 4
 BC = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_fp16": 2}
 P0MODE = {"fixed": 0, "closed": 1}
-CHEM = {"none": 0, "explicit": 1}
+CHEM = {"none": 0, "explicit": 1, "implicit": 2}
 FIELD = {"T": 1, "Y": 2, "Ts": 4, "u": 8, "rho": 16, "Ph": 32, "g": 64}
 FIELD_ORDER = ["T", "Y", "Ts", "u", "rho", "Ph", "g"]
 HOST, DEVICE = 0, 1
@@ -48,6 +48,8 @@ class Mechanism(C.Structure):
         ("Y_in", C.c_double * KMAX),
         ("A", C.c_double * JMAX), ("b", C.c_double * JMAX), ("EaR", C.c_double * JMAX),
         ("order", (C.c_double * KMAX) * JMAX), ("stoich", (C.c_double * KMAX) * JMAX),
+        ("rev", C.c_int * JMAX), ("dH", C.c_double * JMAX), ("dS", C.c_double * JMAX),
+        ("rorder", (C.c_double * KMAX) * JMAX), ("p_ref", C.c_double),
     ]
 
 
@@ -151,6 +153,12 @@ def make_mechanism(prob: dict) -> Mechanism:
         for k in range(K):
             m.order[j][k] = r["order"][k]
             m.stoich[j][k] = r["stoich"][k]
+        if r.get("reverse"):
+            m.rev[j] = 1
+            m.dH[j], m.dS[j] = r["reverse"]["dH"], r["reverse"]["dS"]
+            for k in range(K):
+                m.rorder[j][k] = r["reverse"]["order"][k]
+    m.p_ref = prob.get("p_ref", 101325.0)
     return m
 
 

@@ -122,7 +122,8 @@ Launcher* make_launcher(const pflb_domain* d) {
 
 void free_buffers(pflb_domain* d) {
   void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
-                  d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter};
+                  d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
+                  d->B.src};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::memset(&d->B, 0, sizeof(d->B));
@@ -237,8 +238,11 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
   if (m->K != 0 && m->K != 5 && m->K != 6)
     return fail(d, PFLB_ERR_UNSUPPORTED, "species count must be 0, 5 or 6");
   if (m->J < 0 || m->J > PFLB_JMAX) return fail(d, PFLB_ERR_ARG, "bad reaction count");
-  if (m->chem_mode != PFLB_CHEM_NONE && m->chem_mode != PFLB_CHEM_EXPLICIT)
+  if (m->chem_mode != PFLB_CHEM_NONE && m->chem_mode != PFLB_CHEM_EXPLICIT &&
+      m->chem_mode != PFLB_CHEM_IMPLICIT)
     return fail(d, PFLB_ERR_UNSUPPORTED, "chem_mode");
+  for (int j = 0; j < m->J; ++j)
+    if (m->rev[j] && !(m->p_ref > 0)) return fail(d, PFLB_ERR_ARG, "p_ref must be > 0");
   for (int k = 0; k < m->K; ++k)
     if (!(m->M[k] > 0 && m->cp[k] > 0 && m->Dref[k] >= 0))
       return fail(d, PFLB_ERR_ARG, "species data must be positive");
@@ -250,6 +254,10 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
     if (m->K > 0 && cudaMalloc(&d->B.Y[b], n * m->K * d->real_sz) != cudaSuccess)
       return fail(d, PFLB_ERR_OOM, "device allocation failed");
   }
+  if (d->B.src) { cudaFree(d->B.src); d->B.src = nullptr; }
+  if (m->K > 0 && m->chem_mode >= PFLB_CHEM_IMPLICIT &&
+      cudaMalloc(&d->B.src, n * (m->K + 1) * d->real_sz) != cudaSuccess)
+    return fail(d, PFLB_ERR_OOM, "device allocation failed");
   d->mech = *m;
   d->K = m->K;
   d->has_mech = true;

@@ -89,6 +89,17 @@ template <int DIM> struct Tile {
 };
 
 // ------------------------------------------------------------ parameters
+// FP64 chemistry data of the implicit integrator.
+template <int K>
+struct Chem64 {
+  static constexpr int KK = K > 0 ? K : 1;
+  double A[JMAX], b[JMAX], EaR[JMAX], dH[JMAX], dS[JMAX], dn[JMAX];
+  int rev[JMAX];
+  double order[JMAX][KK], rorder[JMAX][KK], stoich[JMAX][KK];
+  double M[KK], cp[KK], hf[KK];
+  double p_ref, rho_ref, dt;
+};
+
 // Everything in lattice units, converted once on the host (pflb_launch.cuh).
 template <class Real, int K>
 struct Params {
@@ -122,6 +133,13 @@ struct Params {
   Real order[JMAX][KK], stoichM[JMAX][KK];  // stoichM = s_kj M_k
   Real rho_ref_M[KK];      // rho_ref / M_k (concentration from rho* Y_k)
   Real g_scale, g_inv_scale;  // FP16 storage scale (power of two)
+  // reversible reactions in the compute type (explicit rates)
+  int rev[JMAX];
+  Real rorder[JMAX][KK];
+  Real dS_R[JMAX], dH_R[JMAX], dn[JMAX], p_ref_R;  // dS/R, dH/R, sum_k s_kj, p_ref/R
+  // FP64 copy of the chemistry for the implicit Newton integrator (FP64 in
+  // every precision mode: the stiff chemistry keeps double precision)
+  Chem64<K> c64;
 };
 
 // Scalar state on the device.  The per-step quantities the cells need (P0,
@@ -147,6 +165,7 @@ struct State {
   const Real* __restrict__ Ts_in;
   Real* __restrict__ Ts_out;
   const Real* __restrict__ phi;
+  const Real* __restrict__ src;  // precomputed chemistry increments [K+1][N] (implicit/surrogate)
   DevScalars* scal;
   double* partials;        // this step's block partials: [blocks][4]
   unsigned* counter;
@@ -241,14 +260,28 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
 #pragma unroll
   for (int k = 0; k < K; ++k) C[k] = rho * P.rho_ref_M[k] * (Y[k] > Real(0) ? Y[k] : Real(0));
   for (int j = 0; j < P.J; ++j) {
-    Real q = P.A_lat[j] * fexp(-P.EaR[j] * invT);
-    if (P.b[j] != Real(0)) q *= fpow(T, P.b[j]);
+    Real kf = P.A_lat[j] * fexp(-P.EaR[j] * invT);
+    if (P.b[j] != Real(0)) kf *= fpow(T, P.b[j]);
+    Real q = kf;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const Real o = P.order[j][k];
       if (o == Real(1)) q *= C[k];
       else if (o == Real(2)) q *= C[k] * C[k];
       else if (o != Real(0)) q *= fpow(C[k], o);
+    }
+    if (P.rev[j]) {
+      // k_r = k_f / K_c, K_c = exp(dS/R - dH/(R T)) (p_ref/(R T))^(sum s)
+      const Real Kc = fexp(P.dS_R[j] - P.dH_R[j] * invT) * fpow(P.p_ref_R * invT, P.dn[j]);
+      Real qr = fdiv(kf, Kc);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const Real o = P.rorder[j][k];
+        if (o == Real(1)) qr *= C[k];
+        else if (o == Real(2)) qr *= C[k] * C[k];
+        else if (o != Real(0)) qr *= fpow(C[k], o);
+      }
+      q -= qr;
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) om[k] += P.stoichM[j][k] * q;
@@ -257,6 +290,143 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
 #pragma unroll
   for (int k = 0; k < K; ++k) wt -= P.hf[k] * om[k];
   omT = wt;
+}
+
+// ----------------------------------------------- implicit chemistry (FP64)
+// One lattice step of the chemistry alone at frozen density (operator
+// splitting), backward Euler: z = (Y_1..Y_K, T), dY/dt = omega/rho,
+// dT/dt = -sum hf omega / (rho cp(Y)).  Newton with the analytic Jacobian and
+// Gaussian elimination with partial pivoting (tolerance 1e-13, <= 30
+// iterations); if it fails the step is split into 2, 4, ..., 64 backward-Euler
+// sub-steps.  Kept out of line so that it does not weigh on the register
+// allocation of the rest of the step.
+template <int K>
+__device__ __noinline__ void chem_be_newton(const Chem64<K>* C0,
+                                            double T0, const double* Y0, double rho,
+                                            double* dY, double* dT) {
+  constexpr int KK = K > 0 ? K : 1;
+  constexpr int n = K + 1;
+  const auto& c = *C0;
+  const double R = 8.314;
+  double zs[K + 1], z[K + 1];
+  int ok = -1;
+  for (int nsub = 1; nsub <= 64 && ok != 0; nsub *= 2) {
+    for (int k = 0; k < K; ++k) zs[k] = Y0[k];
+    zs[K] = T0;
+    ok = 0;
+    const double h = c.dt / nsub;
+    for (int sub = 0; sub < nsub && ok == 0; ++sub) {
+      for (int m = 0; m < n; ++m) z[m] = zs[m];
+      ok = -1;
+      for (int it = 0; it < 30; ++it) {
+        // rates and Jacobian at z
+        const double T = z[K];
+        double Cc[KK], dC[KK], w[KK], dw[KK][K + 1];
+        for (int k = 0; k < K; ++k) {
+          Cc[k] = z[k] > 0 ? rho * z[k] / c.M[k] : 0.0;
+          dC[k] = z[k] > 0 ? rho / c.M[k] : 0.0;
+          w[k] = 0;
+          for (int m = 0; m < n; ++m) dw[k][m] = 0;
+        }
+        for (int j = 0; j < 4; ++j) {
+          if (c.A[j] == 0.0) continue;
+          double kf = c.A[j] * exp(-c.EaR[j] / T);
+          if (c.b[j] != 0.0) kf *= pow(T, c.b[j]);
+          double kr = 0, dlkf = c.EaR[j] / (T * T) + c.b[j] / T, dlkr = dlkf;
+          if (c.rev[j]) {
+            const double Kc = exp(c.dS[j] / R - c.dH[j] / (R * T)) * pow(c.p_ref / (R * T), c.dn[j]);
+            kr = kf / Kc;
+            dlkr = dlkf - (c.dH[j] / (R * T * T) + c.dn[j] / T);
+          }
+          double dq[K + 1];
+          for (int m = 0; m < n; ++m) dq[m] = 0;
+          for (int dir = 0; dir < (c.rev[j] ? 2 : 1); ++dir) {
+            const double* ord = dir == 0 ? c.order[j] : c.rorder[j];
+            const double kk = dir == 0 ? kf : kr, sg = dir == 0 ? 1.0 : -1.0;
+            double prod = 1.0;
+            for (int k = 0; k < K; ++k) {
+              const double o = ord[k];
+              if (o == 1.0) prod *= Cc[k];
+              else if (o == 2.0) prod *= Cc[k] * Cc[k];
+              else if (o != 0.0) prod *= pow(Cc[k], o);
+            }
+            const double q = sg * kk * prod;
+            for (int k = 0; k < K; ++k) w[k] += c.M[k] * c.stoich[j][k] * q;
+            dq[K] += q * (dir == 0 ? dlkf : dlkr);
+            for (int m = 0; m < K; ++m) {
+              if (ord[m] == 0.0 || dC[m] == 0.0) continue;
+              double rest = 1.0;
+              for (int k = 0; k < K; ++k) {
+                if (k == m) continue;
+                const double o = ord[k];
+                if (o == 1.0) rest *= Cc[k];
+                else if (o == 2.0) rest *= Cc[k] * Cc[k];
+                else if (o != 0.0) rest *= pow(Cc[k], o);
+              }
+              const double dp = ord[m] == 1.0 ? 1.0 : ord[m] * pow(Cc[m], ord[m] - 1.0);
+              dq[m] += sg * kk * rest * dp * dC[m];
+            }
+          }
+          for (int k = 0; k < K; ++k)
+            for (int m = 0; m < n; ++m) dw[k][m] += c.M[k] * c.stoich[j][k] * dq[m];
+        }
+        double cp = 0, hw = 0;
+        for (int k = 0; k < K; ++k) {
+          cp += z[k] * c.cp[k];
+          hw += c.hf[k] * w[k];
+        }
+        // Newton system (I - h dF/dz) dz = -(z - zs - h F)
+        double A[K + 1][K + 1], r[K + 1];
+        for (int k = 0; k < K; ++k) {
+          r[k] = -(z[k] - zs[k] - h * w[k] / rho);
+          for (int m = 0; m < n; ++m) A[k][m] = (k == m ? 1.0 : 0.0) - h * dw[k][m] / rho;
+        }
+        r[K] = -(z[K] - zs[K] + h * hw / (rho * cp));
+        for (int m = 0; m < n; ++m) {
+          double dhw = 0;
+          for (int k = 0; k < K; ++k) dhw += c.hf[k] * dw[k][m];
+          double dFT = -dhw / (rho * cp);
+          if (m < K) dFT += hw * c.cp[m] / (rho * cp * cp);
+          A[K][m] = (m == K ? 1.0 : 0.0) - h * dFT;
+        }
+        bool sing = false;
+        for (int col = 0; col < n && !sing; ++col) {
+          int piv = col;
+          for (int rr = col + 1; rr < n; ++rr)
+            if (fabs(A[rr][col]) > fabs(A[piv][col])) piv = rr;
+          if (A[piv][col] == 0.0) { sing = true; break; }
+          if (piv != col) {
+            for (int k = 0; k < n; ++k) { const double t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
+            const double t = r[col]; r[col] = r[piv]; r[piv] = t;
+          }
+          for (int rr = col + 1; rr < n; ++rr) {
+            const double f = A[rr][col] / A[col][col];
+            for (int k = col; k < n; ++k) A[rr][k] -= f * A[col][k];
+            r[rr] -= f * r[col];
+          }
+        }
+        if (sing) break;
+        for (int rr = n - 1; rr >= 0; --rr) {
+          double sacc = r[rr];
+          for (int k = rr + 1; k < n; ++k) sacc -= A[rr][k] * r[k];
+          r[rr] = sacc / A[rr][rr];
+        }
+        double big = 0;
+        bool bad = false;
+        for (int m = 0; m < n; ++m) {
+          z[m] += r[m];
+          const double e = fabs(r[m]) / (m < K ? 1.0 : zs[K]);
+          if (!(e == e)) bad = true;
+          if (e > big) big = e;
+        }
+        if (bad || !(z[K] > 0)) break;
+        if (big < 1e-13) { ok = 0; break; }
+      }
+      for (int m = 0; m < n; ++m) zs[m] = z[m];
+    }
+  }
+  for (int k = 0; k < K; ++k) dY[k] = zs[k] - Y0[k];
+  *dT = zs[K] - T0;
 }
 
 template <class Real, int K>
@@ -653,6 +823,12 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   for (int k = 0; k < KK; ++k) om[k] = 0;
   if constexpr (K > 0) {
     if (P.chem == 1) rates(P, T0, Y0, rho, invT, om, omT);
+    if (P.chem >= 2) {
+      // increments of the chemistry pre-pass (implicit integrator or surrogate)
+#pragma unroll
+      for (int k = 0; k < K; ++k) om[k] = __ldg(S.src + (size_t)k * P.N + c);
+      omT = __ldg(S.src + (size_t)K * P.N + c);
+    }
   }
 
   const Real iphr = fluid_on ? fdiv(Real(1), phif * rho) : Real(0);
@@ -892,6 +1068,39 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
 template <int DIM, int K, class Real>
 constexpr size_t step_smem_bytes() {
   return sizeof(Plane<Real, K, Tile<DIM>::HP>) * Tile<DIM>::NPL;
+}
+
+// ------------------------------------------- chemistry pre-pass (implicit)
+// Per cell: backward-Euler Newton increments over the step at (T^n, Y^n,
+// rho^n), stored as the FD source terms rho* dY_k and rho* cp dT.
+template <int K, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK)
+chem_implicit_kernel(const Params<Real, K> P, const State<Real, Store> S, Real* __restrict__ src) {
+  constexpr int KK = K > 0 ? K : 1;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.N) return;
+  const Real T = S.T_in[c];
+  Real Y[KK];
+#pragma unroll
+  for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
+  const Real phif = Real(1) - S.phi[c];
+  Real om[KK], omT = 0;
+#pragma unroll
+  for (int k = 0; k < KK; ++k) om[k] = 0;
+  if (phif >= P.phi_min) {
+    const Real P0 = scal_P0<Real>(S.scal);
+    const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
+    double Yd[KK], dY[KK], dT;
+#pragma unroll
+    for (int k = 0; k < K; ++k) Yd[k] = double(Y[k]);
+    chem_be_newton<K>(&P.c64, double(T), Yd, double(rho) * P.c64.rho_ref, dY, &dT);
+#pragma unroll
+    for (int k = 0; k < K; ++k) om[k] = rho * Real(dY[k]);
+    omT = rho * mixture_cp(P, Y) * Real(dT);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) src[(size_t)k * P.N + c] = om[k];
+  src[(size_t)K * P.N + c] = omT;
 }
 
 // ------------------------------------------------ initial equilibrium

@@ -22,6 +22,7 @@ struct Buffers {
   void* Y[2];
   void* Ts[2];
   void* phi;
+  void* src;               // chemistry increments [K+1][N] (implicit / surrogate modes)
   DevScalars* scal;
   double* partials;        // two buffers of `slots` x 4 doubles (step parity)
   unsigned* counter;
@@ -148,6 +149,39 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
       P.stoichM[j][k] = Real(m.stoich[j][k] * m.M[k]);
     }
   }
+  for (int j = 0; j < P.J; ++j) {
+    P.rev[j] = m.rev[j];
+    double dn = 0;
+    for (int k = 0; k < K; ++k) {
+      P.rorder[j][k] = Real(m.rorder[j][k]);
+      dn += m.stoich[j][k];
+    }
+    P.dS_R[j] = Real(m.dS[j] / R_GAS);
+    P.dH_R[j] = Real(m.dH[j] / R_GAS);
+    P.dn[j] = Real(dn);
+    auto& c = P.c64;
+    c.A[j] = m.A[j];
+    c.b[j] = m.b[j];
+    c.EaR[j] = m.EaR[j];
+    c.dH[j] = m.dH[j];
+    c.dS[j] = m.dS[j];
+    c.dn[j] = dn;
+    c.rev[j] = m.rev[j];
+    for (int k = 0; k < K; ++k) {
+      c.order[j][k] = m.order[j][k];
+      c.rorder[j][k] = m.rorder[j][k];
+      c.stoich[j][k] = m.stoich[j][k];
+    }
+  }
+  P.p_ref_R = Real(K > 0 && m.p_ref > 0 ? m.p_ref / R_GAS : 101325.0 / R_GAS);
+  for (int k = 0; k < K; ++k) {
+    P.c64.M[k] = m.M[k];
+    P.c64.cp[k] = m.cp[k];
+    P.c64.hf[k] = m.hf[k];
+  }
+  P.c64.p_ref = m.p_ref > 0 ? m.p_ref : 101325.0;
+  P.c64.rho_ref = d.rho_ref;
+  P.c64.dt = d.dt;
   const float s = mode == MODE_FP16 ? 4096.0f : 1.0f;
   P.g_scale = Real(s);
   P.g_inv_scale = Real(1.0f / s);
@@ -181,6 +215,7 @@ struct LauncherImpl final : Launcher {
     S.Ts_in = static_cast<const Real*>(B.Ts[cur]);
     S.Ts_out = static_cast<Real*>(B.Ts[nxt]);
     S.phi = static_cast<const Real*>(B.phi);
+    S.src = static_cast<const Real*>(B.src);
     S.scal = B.scal;
     S.partials = B.partials + (size_t)4 * B.slots * cur;
     S.counter = B.counter;
@@ -309,6 +344,13 @@ struct LauncherImpl final : Launcher {
     if (e != cudaSuccess) return e;
     const dim3 grid = step_grid();
     for (int n = 0; n < nsteps; ++n) {
+      if constexpr (K > 0) {
+        if (P.chem == 2) {
+          if (!B.src) return cudaErrorInvalidValue;
+          chem_implicit_kernel<K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
+              P, state(B, cur), static_cast<Real*>(B.src));
+        }
+      }
       const double* prev = (!p0_closed && B.pending)
                                ? B.partials + (size_t)4 * B.slots * B.last_parity : nullptr;
       if (kernel_sel == 1 && tma_usable(B, cur)) {

@@ -51,6 +51,8 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
   if (D.precision != PFLB_FP64 && D.precision != PFLB_FP32)
     return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports FP64 and FP32");
   if (K > 0 && (!Y_in || !Y_out)) return err(PFLB_ERR_ARG, "Y arrays are required when K > 0");
+  if (mech && mech->chem_mode > PFLB_CHEM_EXPLICIT)
+    return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports explicit chemistry only");
   if (D.Ts_field && (!Ts_in || !Ts_out)) return err(PFLB_ERR_ARG, "Ts arrays are required");
   if (D.nx < 2 || D.ny < 1) return err(PFLB_ERR_ARG, "bad lattice extent");
   const long long N = (long long)D.nx * D.ny;

@@ -359,6 +359,8 @@ def burnt_composition(Y_in, species, M):
     """Complete combustion of the CH4 in Y_in to CO2 and H2O (lean mixture)."""
     Y = dict(zip(species, Y_in))
     mm = dict(zip(species, M))
+    if "CO" in Y:
+        Y["CO"] = Y.get("CO", 0.0)
     n = Y["CH4"] / mm["CH4"]
     Y["O2"] -= 2.0 * n * mm["O2"]
     Y["CO2"] += n * mm["CO2"]
@@ -399,6 +401,41 @@ def config2_fields(p):
     f = reactive_fields(p, phi)
     f["info"] = info
     return f
+
+
+def two_step_mechanism(A1=3.31e8, A2=1.0e8):
+    """Project-chosen two-step CH4 mechanism on (CH4, O2, CO, CO2, H2O, N2):
+    R1  CH4 + 1.5 O2 -> CO + 2 H2O,  Q1 = A1 exp(-15000/T) [CH4][O2];
+    R2  CO + 0.5 O2 <-> CO2,         Q2 = A2 exp(-12000/T) ([CO][O2]^0.5 - [CO2]/K_c),
+    K_c from the standard reaction enthalpy and entropy of CO + 1/2 O2 -> CO2
+    (-283.0 kJ/mol, -86.5 J/(mol K)).  The rate constants of the paper's
+    mechanism are not printed in the paper and are not used here."""
+    return [{"A": A1, "b": 0.0, "EaR": 15000.0, "order": [1, 1, 0, 0, 0, 0],
+             "stoich": [-1, -1.5, 1, 0, 2, 0]},
+            {"A": A2, "b": 0.0, "EaR": 12000.0, "order": [0, 0.5, 1, 0, 0, 0],
+             "stoich": [0, -0.5, -1, 1, 0, 0],
+             "reverse": {"dH": -283.0e3, "dS": -86.5, "order": [0, 0, 0, 1, 0, 0]}}]
+
+
+def config4(nx=2048, ny=512, precision="fp64", steps=2000, seed=4, chem="implicit"):
+    """2-D bed with the two-step six-species mechanism integrated per cell by
+    backward Euler with Newton iterations (FP64), 60 seeded ellipses."""
+    p = config2(nx, ny, precision=precision, steps=steps, seed=seed)
+    p["K"] = 6
+    p["species"], p["M"] = list(SPECIES6), list(M6)
+    p["cp"], p["Dref"] = list(CP6), list(DREF6)
+    p["hf"] = [h / m for h, m in zip(HF_MOL6, M6)]
+    p["Y_in"] = lean_ch4_air(0.7, SPECIES6)
+    p["chem"] = chem
+    p["reactions"] = two_step_mechanism()
+    p["bed"] = {"count": 60, "amin": 8, "amax": 20, "porosity": 0.6, "x0": 160}
+    p["ignite"] = [16, 64, 1500.0]
+    p["name"] = f"cfg4_two_step_bed_{nx}x{ny}_d2q9_{precision}"
+    return p
+
+
+def config4_fields(p):
+    return config2_fields(p)
 
 
 def config3(nx=256, ny=128, nz=128, precision="fp32_fp16", steps=2000, seed=3):
