@@ -67,6 +67,7 @@ extern "C" {
 #define PFLB_CHEM_NONE 0
 #define PFLB_CHEM_EXPLICIT 1    /* forward-Euler Arrhenius source */
 #define PFLB_CHEM_IMPLICIT 2    /* per-cell backward Euler + Newton, FP64 (operator split) */
+#define PFLB_CHEM_SURROGATE 3   /* learned MLP increments, Newton fallback (six species) */
 
 #define PFLB_HOST 0
 #define PFLB_DEVICE 1
@@ -218,6 +219,67 @@ int pflb_select_kernel(pflb_domain* d, int kernel);
  * NULL) the time per step of each candidate in kernel order (2 values, a
  * negative value for a kernel that cannot run).  Synchronises the stream. */
 int pflb_autotune(pflb_domain* d, int steps, int* chosen, double* us_per_step);
+
+/* ------------------------------------------------------------------------
+ * Learned chemistry surrogate.  Not in the paper: an added pattern that
+ * replaces the per-cell implicit chemistry by a small network where it is
+ * trustworthy.  Network: 8 -> 64 -> 64 -> 64 -> 6, tanh hidden layers, BF16
+ * weights and FP32 accumulation on tensor cores; inputs the normalised
+ * (T, Y_1..Y_6, P0), outputs the normalised species change over one step.
+ * Parameters: PFLB_MLP_PARAMS floats, W1 (8x64, input-major), b1, W2, b2,
+ * W3, b3, W4 (64x6), b4 with y = x W + b.  All X / Y / out pointers below are
+ * device pointers (row-major, 8 / 6 floats per row, normalised values).
+ * ------------------------------------------------------------------------ */
+#define PFLB_MLP_PARAMS 9286
+typedef struct pflb_mlp pflb_mlp;
+
+/* New network on `device`, work queued on `stream`; parameters zero. */
+int pflb_mlp_create(int device, void* stream, pflb_mlp** out);
+/* Load FP32 parameters from host memory (resets the Adam state); synchronises. */
+int pflb_mlp_set_params(pflb_mlp* m, const float* theta);
+/* Copy the FP32 master parameters to host memory; synchronises. */
+int pflb_mlp_get_params(pflb_mlp* m, float* theta);
+/* out[n][6] = network(X[n][8]) (asynchronous); X 16-byte aligned. */
+int pflb_mlp_forward(pflb_mlp* m, const float* X, float* out, long long n);
+/* Gradient of the mean squared error over the n rows (host grad[PFLB_MLP_PARAMS],
+ * may be NULL) and the loss; synchronises. */
+int pflb_mlp_gradient(pflb_mlp* m, const float* X, const float* Y, long long n, float* grad,
+                      double* loss);
+/* `steps` Adam steps (lr, beta 0.9 / 0.999, eps 1e-8) over consecutive mini-batches of
+ * `batch` rows (wrapping); *last_loss = loss of the last mini-batch (may be NULL). */
+int pflb_mlp_train(pflb_mlp* m, const float* X, const float* Y, long long n, int batch,
+                   int steps, float lr, double* last_loss);
+int pflb_mlp_destroy(pflb_mlp* m);
+
+/* How a domain uses a trained network (PFLB_CHEM_SURROGATE). */
+typedef struct pflb_surrogate {
+  double x_mean[8], x_std[8];   /* input normalisation (std 0: feature ignored) */
+  double y_mean[6], y_std[6];   /* output normalisation */
+  double theta_s;               /* output scale temperature: dY = exp(-theta_s / T) *
+                                   (y_mean + y_std * out); 0 for no scaling */
+  double lo[8], hi[8];          /* training bounding box of the raw inputs */
+  int n_elem;                   /* elements checked (<= 4) */
+  double elem[4][PFLB_KMAX];    /* atoms of element e in species k */
+  double elem_mass[4];          /* element molar masses (kg/mol) */
+  double tol;                   /* element residual tolerance, e.g. 1e-6 */
+} pflb_surrogate;
+
+/* Attach a trained network to a domain whose mechanism has chem_mode
+ * PFLB_CHEM_SURROGATE and six species.  A cell uses the network when its
+ * inputs are inside [lo, hi] and |sum_k elem[e][k] M_e / M_k dY_k| <= tol for
+ * every element; the increment is then projected onto the element-conserving
+ * subspace.  Other fluid cells take the backward-Euler Newton integrator.
+ * The network must outlive the domain's use of it. */
+int pflb_set_surrogate(pflb_domain* d, const pflb_mlp* m, const pflb_surrogate* s);
+
+/* Chemistry increments over one step of the CURRENT state with the domain's
+ * chemistry mode (implicit or surrogate): dst receives (K+1)*N values, dY_k
+ * then dT, in dtype; synchronises.  The state is not advanced. */
+int pflb_chem_increments(pflb_domain* d, void* dst, size_t bytes, int dtype, int where);
+
+/* Surrogate counters since the mechanism was set: cells that fell back to
+ * the integrator and cells the network evaluated.  Synchronises. */
+int pflb_chem_stats(pflb_domain* d, double* fallback_cells, double* evaluated_cells);
 
 /* Largest lattice (cells) that pflb_step_noalloc accepts. */
 #define PFLB_NOALLOC_MAX_CELLS (1 << 22)

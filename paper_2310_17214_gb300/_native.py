@@ -14,7 +14,8 @@ KMAX, JMAX = 8, 4
 BC = {"periodic": 0, "wall": 1, "inlet": 2, "outlet": 3}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_fp16": 2}
 P0MODE = {"fixed": 0, "closed": 1}
-CHEM = {"none": 0, "explicit": 1, "implicit": 2}
+CHEM = {"none": 0, "explicit": 1, "implicit": 2, "surrogate": 3}
+MLP_PARAMS = 9286
 FIELD = {"T": 1, "Y": 2, "Ts": 4, "u": 8, "rho": 16, "Ph": 32, "g": 64}
 FIELD_ORDER = ["T", "Y", "Ts", "u", "rho", "Ph", "g"]
 HOST, DEVICE = 0, 1
@@ -59,6 +60,17 @@ class Scalars(C.Structure):
                 ("step", C.c_longlong), ("status", C.c_int)]
 
 
+class Surrogate(C.Structure):
+    _fields_ = [
+        ("x_mean", C.c_double * 8), ("x_std", C.c_double * 8),
+        ("y_mean", C.c_double * 6), ("y_std", C.c_double * 6),
+        ("theta_s", C.c_double),
+        ("lo", C.c_double * 8), ("hi", C.c_double * 8),
+        ("n_elem", C.c_int), ("elem", (C.c_double * KMAX) * 4), ("elem_mass", C.c_double * 4),
+        ("tol", C.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -89,6 +101,17 @@ def lib():
         L.pflb_select_kernel.argtypes = [vp, C.c_int]
         L.pflb_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), vp]
         L.pflb_destroy.argtypes = [vp]
+        L.pflb_mlp_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
+        L.pflb_mlp_set_params.argtypes = [vp, vp]
+        L.pflb_mlp_get_params.argtypes = [vp, vp]
+        L.pflb_mlp_forward.argtypes = [vp, vp, vp, C.c_longlong]
+        L.pflb_mlp_gradient.argtypes = [vp, vp, vp, C.c_longlong, vp, C.POINTER(C.c_double)]
+        L.pflb_mlp_train.argtypes = [vp, vp, vp, C.c_longlong, C.c_int, C.c_int, C.c_float,
+                                     C.POINTER(C.c_double)]
+        L.pflb_mlp_destroy.argtypes = [vp]
+        L.pflb_set_surrogate.argtypes = [vp, vp, C.POINTER(Surrogate)]
+        L.pflb_chem_increments.argtypes = [vp, vp, C.c_size_t, C.c_int, C.c_int]
+        L.pflb_chem_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pflb_last_error.argtypes = [vp]
         L.pflb_last_error.restype = C.c_char_p
         _lib = L
@@ -277,6 +300,26 @@ class Domain:
         return names[ch.value], {names[i]: (float(us[i]) if us[i] > 0 else None)
                                  for i in range(2)}
 
+    def set_surrogate(self, net: "Mlp", surr: Surrogate):
+        """Attach a trained network (chem mode "surrogate", six species)."""
+        self._net = net  # the network must outlive its use by this domain
+        self._surr = surr
+        _check(lib().pflb_set_surrogate(self._h, net._h, C.byref(surr)), self._h)
+
+    def chem_increments(self):
+        """(dY [K, N], dT [N]) of one chemistry step of the current state."""
+        buf = np.empty((self.K + 1) * self.N)
+        _check(lib().pflb_chem_increments(self._h, buf.ctypes.data, buf.nbytes, F64, HOST),
+               self._h)
+        buf = buf.reshape(self.K + 1, self.N)
+        return buf[:self.K], buf[self.K]
+
+    def chem_stats(self):
+        """(cells that fell back to the integrator, cells the network evaluated)."""
+        fb, ev = C.c_double(), C.c_double()
+        _check(lib().pflb_chem_stats(self._h, C.byref(fb), C.byref(ev)), self._h)
+        return fb.value, ev.value
+
     def state_bytes(self) -> int:
         n = C.c_size_t()
         _check(lib().pflb_state_bytes(self._h, C.byref(n)), self._h)
@@ -341,3 +384,74 @@ def step_noalloc(prob, precision, arrays, scalars, stream=0, device=0):
     if rc != 0:
         raise PflbError(f"pflb_step_noalloc error {rc}")
     return {f: getattr(sc, f) for f, _ in Scalars._fields_}
+
+
+def _dev_f32(t, cols):
+    """Pointer of a contiguous float32 CUDA tensor with `cols` columns."""
+    import torch
+    if not (hasattr(t, "data_ptr") and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous() and t.dim() == 2 and t.shape[1] == cols):
+        raise ValueError(f"expected a contiguous float32 CUDA tensor [n, {cols}]")
+    return t.data_ptr()
+
+
+class Mlp:
+    """The chemistry-surrogate network (8 -> 64 -> 64 -> 64 -> 6) on one GPU:
+    BF16 tensor-core forward, backward and Adam kernels with FP32 master
+    parameters.  Inputs and targets are float32 CUDA tensors."""
+
+    def __init__(self, device: int = 0, stream: int = 0):
+        self._h = C.c_void_p()
+        rc = lib().pflb_mlp_create(device, stream, C.byref(self._h))
+        if rc != 0:
+            raise PflbError(f"pflb_mlp_create error {rc}")
+
+    def _rc(self, rc, what):
+        if rc != 0:
+            raise PflbError(f"{what} error {rc}")
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == MLP_PARAMS
+        self._rc(lib().pflb_mlp_set_params(self._h, th.ctypes.data), "pflb_mlp_set_params")
+
+    def get_params(self):
+        th = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._rc(lib().pflb_mlp_get_params(self._h, th.ctypes.data), "pflb_mlp_get_params")
+        return th
+
+    def forward(self, X, out=None):
+        import torch
+        n = X.shape[0]
+        if out is None:
+            out = torch.empty((n, 6), dtype=torch.float32, device=X.device)
+        self._rc(lib().pflb_mlp_forward(self._h, _dev_f32(X, 8), _dev_f32(out, 6), n),
+                 "pflb_mlp_forward")
+        return out
+
+    def gradient(self, X, Y):
+        """(mean squared error, flat FP32 gradient) over all rows."""
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = C.c_double()
+        self._rc(lib().pflb_mlp_gradient(self._h, _dev_f32(X, 8), _dev_f32(Y, 6), X.shape[0],
+                                         g.ctypes.data, C.byref(loss)), "pflb_mlp_gradient")
+        return loss.value, g
+
+    def train(self, X, Y, batch: int, steps: int, lr: float) -> float:
+        """`steps` Adam steps over consecutive mini-batches; last mini-batch loss."""
+        loss = C.c_double()
+        self._rc(lib().pflb_mlp_train(self._h, _dev_f32(X, 8), _dev_f32(Y, 6), X.shape[0],
+                                      int(batch), int(steps), float(lr), C.byref(loss)),
+                 "pflb_mlp_train")
+        return loss.value
+
+    def close(self):
+        if self._h:
+            lib().pflb_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

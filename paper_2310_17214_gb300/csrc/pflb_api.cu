@@ -8,6 +8,8 @@
 #include <new>
 #include <string>
 #include <algorithm>
+#include <cmath>
+#include <utility>
 
 #include "../../include/pflb.h"
 #include "pflb_launch.cuh"
@@ -123,7 +125,7 @@ Launcher* make_launcher(const pflb_domain* d) {
 void free_buffers(pflb_domain* d) {
   void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
                   d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
-                  d->B.src};
+                  d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::memset(&d->B, 0, sizeof(d->B));
@@ -239,8 +241,10 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
     return fail(d, PFLB_ERR_UNSUPPORTED, "species count must be 0, 5 or 6");
   if (m->J < 0 || m->J > PFLB_JMAX) return fail(d, PFLB_ERR_ARG, "bad reaction count");
   if (m->chem_mode != PFLB_CHEM_NONE && m->chem_mode != PFLB_CHEM_EXPLICIT &&
-      m->chem_mode != PFLB_CHEM_IMPLICIT)
+      m->chem_mode != PFLB_CHEM_IMPLICIT && m->chem_mode != PFLB_CHEM_SURROGATE)
     return fail(d, PFLB_ERR_UNSUPPORTED, "chem_mode");
+  if (m->chem_mode == PFLB_CHEM_SURROGATE && m->K != 6)
+    return fail(d, PFLB_ERR_UNSUPPORTED, "the surrogate needs the six-species mechanism");
   for (int j = 0; j < m->J; ++j)
     if (m->rev[j] && !(m->p_ref > 0)) return fail(d, PFLB_ERR_ARG, "p_ref must be > 0");
   for (int k = 0; k < m->K; ++k)
@@ -254,10 +258,24 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
     if (m->K > 0 && cudaMalloc(&d->B.Y[b], n * m->K * d->real_sz) != cudaSuccess)
       return fail(d, PFLB_ERR_OOM, "device allocation failed");
   }
-  if (d->B.src) { cudaFree(d->B.src); d->B.src = nullptr; }
+  void* old_bufs[] = {d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats};
+  for (void* q : old_bufs)
+    if (q) cudaFree(q);
+  d->B.src = nullptr;
+  d->B.fb_idx = nullptr;
+  d->B.fb_count = nullptr;
+  d->B.chem_stats = nullptr;
   if (m->K > 0 && m->chem_mode >= PFLB_CHEM_IMPLICIT &&
       cudaMalloc(&d->B.src, n * (m->K + 1) * d->real_sz) != cudaSuccess)
     return fail(d, PFLB_ERR_OOM, "device allocation failed");
+  if (m->chem_mode == PFLB_CHEM_SURROGATE) {
+    if (cudaMalloc((void**)&d->B.fb_idx, n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&d->B.fb_count, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void**)&d->B.chem_stats, 2 * sizeof(double)) != cudaSuccess)
+      return fail(d, PFLB_ERR_OOM, "device allocation failed");
+    cudaMemset(d->B.fb_count, 0, sizeof(unsigned));
+    cudaMemset(d->B.chem_stats, 0, 2 * sizeof(double));
+  }
   d->mech = *m;
   d->K = m->K;
   d->has_mech = true;
@@ -584,6 +602,126 @@ int pflb_autotune(pflb_domain* d, int steps, int* chosen, double* us_per_step) {
   d->L->select_kernel(best >= 0 ? best : prev, d->B, d->cur);
   *chosen = d->L->kernel();
   CK(d, cudaStreamSynchronize(d->stream));
+  return PFLB_OK;
+}
+
+}  // extern "C"
+
+namespace pflb {
+mlp::Net mlp_net(const pflb_mlp* m);
+}
+
+extern "C" {
+
+int pflb_set_surrogate(pflb_domain* d, const pflb_mlp* net, const pflb_surrogate* s) {
+  if (!d || !net || !s) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  if (!d->L) return fail(d, PFLB_ERR_STATE, "set_fields must come first");
+  if (d->mech.chem_mode != PFLB_CHEM_SURROGATE || d->K != 6)
+    return fail(d, PFLB_ERR_STATE, "mechanism is not in surrogate mode");
+  if (s->n_elem < 0 || s->n_elem > 4) return fail(d, PFLB_ERR_ARG, "n_elem");
+  SurrArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.net = mlp_net(net);
+  for (int f = 0; f < 8; ++f) {
+    a.x_mean[f] = float(s->x_mean[f]);
+    a.x_istd[f] = s->x_std[f] > 0 ? float(1.0 / s->x_std[f]) : 0.f;
+    a.lo[f] = float(s->lo[f]);
+    a.hi[f] = float(s->hi[f]);
+  }
+  for (int k = 0; k < 6; ++k) {
+    a.y_mean[k] = float(s->y_mean[k]);
+    a.y_std[k] = float(s->y_std[k]);
+  }
+  a.n_elem = s->n_elem;
+  a.tol = s->tol;
+  a.theta_s = s->theta_s;
+  a.tol_f = float(s->tol);
+  a.theta_f = float(s->theta_s);
+  // residual weights a_ek M_e / M_k and the orthogonal projection onto
+  // {dY : sum_k a_ek dY_k / M_k = 0 for every element}
+  double B[4][6] = {};
+  for (int e = 0; e < s->n_elem; ++e)
+    for (int k = 0; k < 6; ++k) {
+      a.E[e][k] = s->elem[e][k] * s->elem_mass[e] / d->mech.M[k];
+      a.E_f[e][k] = float(a.E[e][k]);
+      B[e][k] = s->elem[e][k] / d->mech.M[k];
+    }
+  const int ne = s->n_elem;
+  double G[4][4] = {}, Gi[4][4] = {};
+  for (int i = 0; i < ne; ++i)
+    for (int j = 0; j < ne; ++j) {
+      for (int k = 0; k < 6; ++k) G[i][j] += B[i][k] * B[j][k];
+      Gi[i][j] = i == j ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < ne; ++c) {  // Gauss-Jordan inverse of the element Gram matrix
+    int piv = c;
+    for (int r = c + 1; r < ne; ++r)
+      if (std::fabs(G[r][c]) > std::fabs(G[piv][c])) piv = r;
+    if (G[piv][c] == 0.0) return fail(d, PFLB_ERR_ARG, "element matrix is rank deficient");
+    for (int k = 0; k < ne; ++k) {
+      std::swap(G[c][k], G[piv][k]);
+      std::swap(Gi[c][k], Gi[piv][k]);
+    }
+    const double inv = 1.0 / G[c][c];
+    for (int k = 0; k < ne; ++k) { G[c][k] *= inv; Gi[c][k] *= inv; }
+    for (int r = 0; r < ne; ++r) {
+      if (r == c) continue;
+      const double f = G[r][c];
+      for (int k = 0; k < ne; ++k) { G[r][k] -= f * G[c][k]; Gi[r][k] -= f * Gi[c][k]; }
+    }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double v = i == j ? 1.0 : 0.0;
+      for (int p = 0; p < ne; ++p)
+        for (int q = 0; q < ne; ++q) v -= B[p][i] * Gi[p][q] * B[q][j];
+      a.Pj[i][j] = v;
+      a.Pj_f[i][j] = float(v);
+    }
+  if (!d->L->set_surrogate(a)) return fail(d, PFLB_ERR_UNSUPPORTED, "surrogate not available");
+  return PFLB_OK;
+}
+
+int pflb_chem_increments(pflb_domain* d, void* dst, size_t bytes, int dtype, int where) {
+  if (!d || !dst) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  int r = check_dtype_where(d, dtype, where);
+  if (r) return r;
+  if (!d->L || d->K == 0 || d->mech.chem_mode < PFLB_CHEM_IMPLICIT)
+    return fail(d, PFLB_ERR_STATE, "needs implicit or surrogate chemistry");
+  const size_t n = (size_t)d->N * (d->K + 1), esz = dtype == PFLB_DTYPE_F64 ? 8 : 4;
+  if (bytes < n * esz) return fail(d, PFLB_ERR_ARG, "destination too small");
+  CK(d, cudaSetDevice(d->desc.device));
+  double* tmp = nullptr;
+  CK(d, cudaMallocAsync((void**)&tmp, n * sizeof(double), d->stream));
+  cudaError_t e = d->L->chem_pass(d->B, d->cur, tmp, d->stream);
+  void* out = dst;
+  void* stage = nullptr;
+  if (e == cudaSuccess && where == PFLB_HOST) {
+    e = cudaMallocAsync(&stage, n * esz, d->stream);
+    out = stage;
+  }
+  if (e == cudaSuccess)
+    e = esz == 8 ? convert<double, double>(tmp, out, n, d->stream)
+                 : convert<double, float>(tmp, out, n, d->stream);
+  if (e == cudaSuccess && where == PFLB_HOST)
+    e = cudaMemcpyAsync(dst, stage, n * esz, cudaMemcpyDeviceToHost, d->stream);
+  if (stage) cudaFreeAsync(stage, d->stream);
+  cudaFreeAsync(tmp, d->stream);
+  CK(d, e);
+  CK(d, cudaStreamSynchronize(d->stream));
+  return PFLB_OK;
+}
+
+int pflb_chem_stats(pflb_domain* d, double* fallback_cells, double* evaluated_cells) {
+  if (!d) return fail(d, PFLB_ERR_ARG, "NULL domain");
+  double h[2] = {0, 0};
+  if (d->B.chem_stats) {
+    CK(d, cudaSetDevice(d->desc.device));
+    CK(d, cudaMemcpyAsync(h, d->B.chem_stats, sizeof(h), cudaMemcpyDeviceToHost, d->stream));
+    CK(d, cudaStreamSynchronize(d->stream));
+  }
+  if (fallback_cells) *fallback_cells = h[0];
+  if (evaluated_cells) *evaluated_cells = h[1];
   return PFLB_OK;
 }
 

@@ -96,8 +96,10 @@ struct Chem64 {
   double A[JMAX], b[JMAX], EaR[JMAX], dH[JMAX], dS[JMAX], dn[JMAX];
   int rev[JMAX];
   double order[JMAX][KK], rorder[JMAX][KK], stoich[JMAX][KK];
-  double M[KK], cp[KK], hf[KK];
-  double p_ref, rho_ref, dt;
+  double Ms[JMAX][KK];          // M_k s_kj
+  double dS_R[JMAX], dH_R[JMAX];  // dS / R, dH / R
+  double M[KK], invM[KK], cp[KK], hf[KK];
+  double p_ref, ln_pref_R, rho_ref, dt;  // ln_pref_R = ln(p_ref / R)
 };
 
 // Everything in lattice units, converted once on the host (pflb_launch.cuh).
@@ -292,6 +294,133 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
   omT = wt;
 }
 
+// Power C^o of a concentration for the reaction orders that occur (0, 1, 2,
+// 1/2: multiplications and a square root), pow() otherwise; d = dC^o/dC for
+// C > 0.
+__device__ __forceinline__ double conc_power(double C, double o, double& d) {
+  if (o == 1.0) { d = 1.0; return C; }
+  if (o == 0.0) { d = 0.0; return 1.0; }
+  if (o == 2.0) { d = 2.0 * C; return C * C; }
+  if (o == 0.5) {
+    const double s = sqrt(C);
+    d = s > 0.0 ? 0.5 / s : 0.0;
+    return s;
+  }
+  d = C > 0.0 ? o * pow(C, o - 1.0) : 0.0;
+  return pow(C, o);
+}
+
+// Rates w_k (kg/(m^3 s)) and their Jacobian dw_k/dz_m, z = (Y_1..Y_K, T).
+template <int K>
+__device__ __forceinline__ void rates_jacobian64(const Chem64<K>& c, const double* z, double rho,
+                                                 double* w, double (*dw)[K + 1]) {
+  constexpr int KK = K > 0 ? K : 1;
+  constexpr int n = K + 1;
+  const double T = z[K], invT = 1.0 / T;
+  double Cc[KK], dC[KK];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    dC[k] = z[k] > 0 ? rho * c.invM[k] : 0.0;
+    Cc[k] = z[k] > 0 ? z[k] * dC[k] : 0.0;
+    w[k] = 0;
+#pragma unroll
+    for (int m = 0; m < n; ++m) dw[k][m] = 0;
+  }
+  double lnT = 0.0;
+  bool have_lnT = false;
+#pragma unroll
+  for (int j = 0; j < JMAX; ++j) {
+    if (c.A[j] == 0.0) continue;
+    double kf = c.A[j] * exp(-c.EaR[j] * invT);
+    if (c.b[j] != 0.0) kf *= pow(T, c.b[j]);
+    const double dlkf = (c.EaR[j] * invT + c.b[j]) * invT;
+    double kr = 0.0, dlkr = dlkf;
+    if (c.rev[j]) {
+      // K_c = exp(dS/R - dH/(R T)) (p_ref / (R T))^dn
+      double lnKc = c.dS_R[j] - c.dH_R[j] * invT;
+      if (c.dn[j] != 0.0) {
+        if (!have_lnT) { lnT = log(T); have_lnT = true; }
+        lnKc += c.dn[j] * (c.ln_pref_R - lnT);
+      }
+      kr = kf * exp(-lnKc);
+      dlkr = dlkf - (c.dH_R[j] * invT + c.dn[j]) * invT;
+    }
+    double dq[K + 1];
+#pragma unroll
+    for (int m = 0; m < n; ++m) dq[m] = 0;
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      if (dir == 1 && !c.rev[j]) break;
+      const double kk = dir == 0 ? kf : -kr;
+      double Pw[KK], Dp[KK], pre[K + 1], suf[K + 1];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        Pw[k] = conc_power(Cc[k], dir == 0 ? c.order[j][k] : c.rorder[j][k], Dp[k]);
+      // prefix / suffix products: the product without factor m, no division
+      pre[0] = 1.0;
+      suf[K] = 1.0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] * Pw[k];
+#pragma unroll
+      for (int k = K - 1; k >= 0; --k) suf[k] = Pw[k] * suf[k + 1];
+      const double q = kk * pre[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) w[k] += c.Ms[j][k] * q;
+      dq[K] += q * (dir == 0 ? dlkf : dlkr);
+#pragma unroll
+      for (int m = 0; m < K; ++m) dq[m] += kk * (pre[m] * suf[m + 1]) * Dp[m] * dC[m];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int m = 0; m < n; ++m) dw[k][m] += c.Ms[j][k] * dq[m];
+  }
+}
+
+// Solve A x = r in place (r <- x) by Gaussian elimination with partial
+// pivoting, every index a compile-time constant so that A stays in
+// registers; false if a pivot is zero.
+template <int n>
+__device__ __forceinline__ bool solve_pivoted(double (*A)[n], double* r) {
+  double dinv[n];
+#pragma unroll
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    double best = fabs(A[col][col]);
+#pragma unroll
+    for (int rr = col + 1; rr < n; ++rr) {
+      const double v = fabs(A[rr][col]);
+      if (v > best) { best = v; piv = rr; }
+    }
+    if (best == 0.0) return false;
+#pragma unroll
+    for (int rr = col + 1; rr < n; ++rr) {
+      if (rr == piv) {
+#pragma unroll
+        for (int k = col; k < n; ++k) { const double t = A[col][k]; A[col][k] = A[rr][k]; A[rr][k] = t; }
+        const double t = r[col]; r[col] = r[rr]; r[rr] = t;
+      }
+    }
+    const double inv = 1.0 / A[col][col];
+    dinv[col] = inv;
+#pragma unroll
+    for (int rr = col + 1; rr < n; ++rr) {
+      const double f = A[rr][col] * inv;
+#pragma unroll
+      for (int k = col + 1; k < n; ++k) A[rr][k] -= f * A[col][k];
+      r[rr] -= f * r[col];
+    }
+  }
+#pragma unroll
+  for (int rr = n - 1; rr >= 0; --rr) {
+    double s = r[rr];
+#pragma unroll
+    for (int k = rr + 1; k < n; ++k) s -= A[rr][k] * r[k];
+    r[rr] = s * dinv[rr];
+  }
+  return true;
+}
+
 // ----------------------------------------------- implicit chemistry (FP64)
 // One lattice step of the chemistry alone at frozen density (operator
 // splitting), backward Euler: z = (Y_1..Y_K, T), dY/dt = omega/rho,
@@ -299,133 +428,78 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
 // Gaussian elimination with partial pivoting (tolerance 1e-13, <= 30
 // iterations); if it fails the step is split into 2, 4, ..., 64 backward-Euler
 // sub-steps.  Kept out of line so that it does not weigh on the register
-// allocation of the rest of the step.
+// allocation of the rest of the step.  The arithmetic is laid out for a short
+// dependency chain (FP64 latency sets the time of a warp): reciprocals taken
+// once, square roots for half orders, no dynamic array indices.
 template <int K>
-__device__ __noinline__ void chem_be_newton(const Chem64<K>* C0,
+__device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
                                             double T0, const double* Y0, double rho,
                                             double* dY, double* dT) {
-  constexpr int KK = K > 0 ? K : 1;
   constexpr int n = K + 1;
   const auto& c = *C0;
-  const double R = 8.314;
-  double zs[K + 1], z[K + 1];
+  const double inv_rho = 1.0 / rho;
+  double zs[K + 1], z[K + 1], y0[K + 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) y0[k] = Y0[k];
+  y0[K] = T0;
   int ok = -1;
   for (int nsub = 1; nsub <= 64 && ok != 0; nsub *= 2) {
-    for (int k = 0; k < K; ++k) zs[k] = Y0[k];
-    zs[K] = T0;
+#pragma unroll
+    for (int m = 0; m < n; ++m) zs[m] = y0[m];
     ok = 0;
-    const double h = c.dt / nsub;
+    const double h = c.dt / nsub, hr = h * inv_rho;
     for (int sub = 0; sub < nsub && ok == 0; ++sub) {
+#pragma unroll
       for (int m = 0; m < n; ++m) z[m] = zs[m];
+      const double inv_Ts = 1.0 / zs[K];  // temperature scale of the update test
       ok = -1;
       for (int it = 0; it < 30; ++it) {
-        // rates and Jacobian at z
-        const double T = z[K];
-        double Cc[KK], dC[KK], w[KK], dw[KK][K + 1];
-        for (int k = 0; k < K; ++k) {
-          Cc[k] = z[k] > 0 ? rho * z[k] / c.M[k] : 0.0;
-          dC[k] = z[k] > 0 ? rho / c.M[k] : 0.0;
-          w[k] = 0;
-          for (int m = 0; m < n; ++m) dw[k][m] = 0;
-        }
-        for (int j = 0; j < 4; ++j) {
-          if (c.A[j] == 0.0) continue;
-          double kf = c.A[j] * exp(-c.EaR[j] / T);
-          if (c.b[j] != 0.0) kf *= pow(T, c.b[j]);
-          double kr = 0, dlkf = c.EaR[j] / (T * T) + c.b[j] / T, dlkr = dlkf;
-          if (c.rev[j]) {
-            const double Kc = exp(c.dS[j] / R - c.dH[j] / (R * T)) * pow(c.p_ref / (R * T), c.dn[j]);
-            kr = kf / Kc;
-            dlkr = dlkf - (c.dH[j] / (R * T * T) + c.dn[j] / T);
-          }
-          double dq[K + 1];
-          for (int m = 0; m < n; ++m) dq[m] = 0;
-          for (int dir = 0; dir < (c.rev[j] ? 2 : 1); ++dir) {
-            const double* ord = dir == 0 ? c.order[j] : c.rorder[j];
-            const double kk = dir == 0 ? kf : kr, sg = dir == 0 ? 1.0 : -1.0;
-            double prod = 1.0;
-            for (int k = 0; k < K; ++k) {
-              const double o = ord[k];
-              if (o == 1.0) prod *= Cc[k];
-              else if (o == 2.0) prod *= Cc[k] * Cc[k];
-              else if (o != 0.0) prod *= pow(Cc[k], o);
-            }
-            const double q = sg * kk * prod;
-            for (int k = 0; k < K; ++k) w[k] += c.M[k] * c.stoich[j][k] * q;
-            dq[K] += q * (dir == 0 ? dlkf : dlkr);
-            for (int m = 0; m < K; ++m) {
-              if (ord[m] == 0.0 || dC[m] == 0.0) continue;
-              double rest = 1.0;
-              for (int k = 0; k < K; ++k) {
-                if (k == m) continue;
-                const double o = ord[k];
-                if (o == 1.0) rest *= Cc[k];
-                else if (o == 2.0) rest *= Cc[k] * Cc[k];
-                else if (o != 0.0) rest *= pow(Cc[k], o);
-              }
-              const double dp = ord[m] == 1.0 ? 1.0 : ord[m] * pow(Cc[m], ord[m] - 1.0);
-              dq[m] += sg * kk * rest * dp * dC[m];
-            }
-          }
-          for (int k = 0; k < K; ++k)
-            for (int m = 0; m < n; ++m) dw[k][m] += c.M[k] * c.stoich[j][k] * dq[m];
-        }
+        double w[K + 1], dw[K + 1][K + 1];
+        rates_jacobian64<K>(c, z, rho, w, dw);
         double cp = 0, hw = 0;
+#pragma unroll
         for (int k = 0; k < K; ++k) {
           cp += z[k] * c.cp[k];
           hw += c.hf[k] * w[k];
         }
+        const double inv_rcp = inv_rho / cp;
         // Newton system (I - h dF/dz) dz = -(z - zs - h F)
         double A[K + 1][K + 1], r[K + 1];
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-          r[k] = -(z[k] - zs[k] - h * w[k] / rho);
-          for (int m = 0; m < n; ++m) A[k][m] = (k == m ? 1.0 : 0.0) - h * dw[k][m] / rho;
+          r[k] = -(z[k] - zs[k] - hr * w[k]);
+#pragma unroll
+          for (int m = 0; m < n; ++m) A[k][m] = (k == m ? 1.0 : 0.0) - hr * dw[k][m];
         }
-        r[K] = -(z[K] - zs[K] + h * hw / (rho * cp));
+        r[K] = -(z[K] - zs[K] + h * hw * inv_rcp);
+#pragma unroll
         for (int m = 0; m < n; ++m) {
           double dhw = 0;
+#pragma unroll
           for (int k = 0; k < K; ++k) dhw += c.hf[k] * dw[k][m];
-          double dFT = -dhw / (rho * cp);
-          if (m < K) dFT += hw * c.cp[m] / (rho * cp * cp);
+          double dFT = -dhw * inv_rcp;
+          if (m < K) dFT += hw * c.cp[m] * inv_rcp / cp;
           A[K][m] = (m == K ? 1.0 : 0.0) - h * dFT;
         }
-        bool sing = false;
-        for (int col = 0; col < n && !sing; ++col) {
-          int piv = col;
-          for (int rr = col + 1; rr < n; ++rr)
-            if (fabs(A[rr][col]) > fabs(A[piv][col])) piv = rr;
-          if (A[piv][col] == 0.0) { sing = true; break; }
-          if (piv != col) {
-            for (int k = 0; k < n; ++k) { const double t = A[col][k]; A[col][k] = A[piv][k]; A[piv][k] = t; }
-            const double t = r[col]; r[col] = r[piv]; r[piv] = t;
-          }
-          for (int rr = col + 1; rr < n; ++rr) {
-            const double f = A[rr][col] / A[col][col];
-            for (int k = col; k < n; ++k) A[rr][k] -= f * A[col][k];
-            r[rr] -= f * r[col];
-          }
-        }
-        if (sing) break;
-        for (int rr = n - 1; rr >= 0; --rr) {
-          double sacc = r[rr];
-          for (int k = rr + 1; k < n; ++k) sacc -= A[rr][k] * r[k];
-          r[rr] = sacc / A[rr][rr];
-        }
+        if (!solve_pivoted<K + 1>(A, r)) break;
         double big = 0;
         bool bad = false;
+#pragma unroll
         for (int m = 0; m < n; ++m) {
           z[m] += r[m];
-          const double e = fabs(r[m]) / (m < K ? 1.0 : zs[K]);
+          const double e = fabs(r[m]) * (m < K ? 1.0 : inv_Ts);
           if (!(e == e)) bad = true;
           if (e > big) big = e;
         }
         if (bad || !(z[K] > 0)) break;
         if (big < 1e-13) { ok = 0; break; }
       }
+#pragma unroll
       for (int m = 0; m < n; ++m) zs[m] = z[m];
     }
   }
-  for (int k = 0; k < K; ++k) dY[k] = zs[k] - Y0[k];
+#pragma unroll
+  for (int k = 0; k < K; ++k) dY[k] = zs[k] - y0[k];
   *dT = zs[K] - T0;
 }
 
@@ -1075,7 +1149,8 @@ constexpr size_t step_smem_bytes() {
 // rho^n), stored as the FD source terms rho* dY_k and rho* cp dT.
 template <int K, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK)
-chem_implicit_kernel(const Params<Real, K> P, const State<Real, Store> S, Real* __restrict__ src) {
+chem_implicit_kernel(const __grid_constant__ Params<Real, K> P, const State<Real, Store> S,
+                     Real* __restrict__ src) {
   constexpr int KK = K > 0 ? K : 1;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= P.N) return;

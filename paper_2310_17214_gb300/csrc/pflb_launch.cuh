@@ -12,6 +12,7 @@
 
 #include "../../include/pflb.h"
 #include "pflb_kernels.cuh"
+#include "pflb_surrogate.cuh"
 #include "pflb_tma.cuh"
 
 namespace pflb {
@@ -23,6 +24,9 @@ struct Buffers {
   void* Ts[2];
   void* phi;
   void* src;               // chemistry increments [K+1][N] (implicit / surrogate modes)
+  int* fb_idx;             // surrogate fallback list [N]
+  unsigned* fb_count;
+  double* chem_stats;      // [0] fallback cells, [1] cells evaluated by the network
   DevScalars* scal;
   double* partials;        // two buffers of `slots` x 4 doubles (step parity)
   unsigned* counter;
@@ -86,6 +90,11 @@ struct Launcher {
   // FP32 compute with 16-byte rows); returns false if not available here
   virtual bool select_kernel(int k, const Buffers& B, int cur) = 0;
   virtual int kernel() const = 0;
+  // learned chemistry (six-species mechanism only)
+  virtual bool set_surrogate(const SurrArgs& a) = 0;
+  // chemistry pre-pass of the current state into B.src; increments (dY, dT)
+  // into `out` ([K+1][N] doubles) when non-null
+  virtual cudaError_t chem_pass(Buffers& B, int cur, double* out, cudaStream_t st) = 0;
   virtual float g_scale() const = 0;
 };
 
@@ -171,15 +180,20 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
       c.order[j][k] = m.order[j][k];
       c.rorder[j][k] = m.rorder[j][k];
       c.stoich[j][k] = m.stoich[j][k];
+      c.Ms[j][k] = m.M[k] * m.stoich[j][k];
     }
+    c.dS_R[j] = m.dS[j] / R_GAS;
+    c.dH_R[j] = m.dH[j] / R_GAS;
   }
   P.p_ref_R = Real(K > 0 && m.p_ref > 0 ? m.p_ref / R_GAS : 101325.0 / R_GAS);
   for (int k = 0; k < K; ++k) {
     P.c64.M[k] = m.M[k];
+    P.c64.invM[k] = 1.0 / m.M[k];
     P.c64.cp[k] = m.cp[k];
     P.c64.hf[k] = m.hf[k];
   }
   P.c64.p_ref = m.p_ref > 0 ? m.p_ref : 101325.0;
+  P.c64.ln_pref_R = std::log(P.c64.p_ref / R_GAS);
   P.c64.rho_ref = d.rho_ref;
   P.c64.dt = d.dt;
   const float s = mode == MODE_FP16 ? 4096.0f : 1.0f;
@@ -251,6 +265,55 @@ struct LauncherImpl final : Launcher {
   int tma_state = 0;  // 0 unknown, 1 usable, -1 not usable
   int tma_grid = 0;
   int kernel_sel = 0;
+  SurrArgs surr;
+  bool has_surr = false;
+
+  bool set_surrogate(const SurrArgs& a) override {
+    if constexpr (K != 6) {
+      return false;
+    } else {
+      surr = a;
+      has_surr = true;
+      return true;
+    }
+  }
+
+  cudaError_t chem_pass(Buffers& B, int cur, double* out, cudaStream_t st) override {
+    if constexpr (K == 0) {
+      return cudaErrorNotSupported;
+    } else {
+      if (!B.src) return cudaErrorInvalidValue;
+      if (P.chem == 2) {
+        chem_implicit_kernel<K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
+            P, state(B, cur), static_cast<Real*>(B.src));
+      } else if (P.chem == 3) {
+        if constexpr (K == 6) {
+          if (!has_surr || !B.fb_idx) return cudaErrorInvalidValue;
+          SurrArgs a = surr;
+          a.fb_idx = B.fb_idx;
+          a.fb_count = B.fb_count;
+          a.stats = B.chem_stats;
+          cudaMemsetAsync(B.fb_count, 0, sizeof(unsigned), st);
+          // persistent grid: each block loads the network once
+          int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, 152 * 4);
+          chem_surrogate_kernel<K, Real, Store><<<nb, 256, 0, st>>>(
+              P, state(B, cur), static_cast<Real*>(B.src), a);
+          const int fb_blocks = (int)std::min<long long>(
+              ((long long)P.N + FALLBACK_BLOCK - 1) / FALLBACK_BLOCK, 152 * 16);
+          chem_fallback_kernel<K, Real, Store><<<fb_blocks, FALLBACK_BLOCK, 0, st>>>(
+              P, state(B, cur), static_cast<Real*>(B.src), B.fb_idx, B.fb_count);
+        } else {
+          return cudaErrorNotSupported;
+        }
+      } else {
+        return cudaErrorInvalidValue;
+      }
+      if (out)
+        src_to_increments_kernel<K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
+            P, state(B, cur), static_cast<const Real*>(B.src), out);
+      return cudaGetLastError();
+    }
+  }
 
   bool select_kernel(int k, const Buffers& B, int cur) override {
     if (k == 0) { kernel_sel = 0; return true; }
@@ -345,10 +408,9 @@ struct LauncherImpl final : Launcher {
     const dim3 grid = step_grid();
     for (int n = 0; n < nsteps; ++n) {
       if constexpr (K > 0) {
-        if (P.chem == 2) {
-          if (!B.src) return cudaErrorInvalidValue;
-          chem_implicit_kernel<K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
-              P, state(B, cur), static_cast<Real*>(B.src));
+        if (P.chem >= 2) {
+          e = chem_pass(B, cur, nullptr, st);
+          if (e != cudaSuccess) return e;
         }
       }
       const double* prev = (!p0_closed && B.pending)

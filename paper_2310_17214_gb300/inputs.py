@@ -36,6 +36,12 @@ def molar_mass(sp):
     return sum(n * _AW[e] for e, n in _COMP[sp].items())
 
 
+def element_matrix(species, elements=("C", "H", "O", "N")):
+    """Atoms of each element in each species ([E][K]) and element molar masses."""
+    return ([[float(_COMP[sp].get(e, 0)) for sp in species] for e in elements],
+            [_AW[e] for e in elements])
+
+
 # one-step CH4 mechanism species order
 SPECIES5 = ["CH4", "O2", "CO2", "H2O", "N2"]
 M5 = [molar_mass(s) for s in SPECIES5]
@@ -429,7 +435,9 @@ def config4(nx=2048, ny=512, precision="fp64", steps=2000, seed=4, chem="implici
     p["chem"] = chem
     p["reactions"] = two_step_mechanism()
     p["bed"] = {"count": 60, "amin": 8, "amax": 20, "porosity": 0.6, "x0": 160}
-    p["ignite"] = [16, 64, 1500.0]
+    # the two-step mechanism releases part of its heat later, through CO: a
+    # 1500 K slab quenches within 2000 steps, one near T_ad (1822 K) lights
+    p["ignite"] = [16, 64, 1800.0]
     p["name"] = f"cfg4_two_step_bed_{nx}x{ny}_d2q9_{precision}"
     return p
 

@@ -1,0 +1,203 @@
+"""The surrogate network's kernels (forward, backward, Adam) against the FP64
+reference MLP, and the surrogate chemistry mode against the Newton
+integrator it falls back to.
+
+Bars: forward and per-tensor gradients within 2e-2 relative of the FP64
+reference evaluated at the BF16-rounded parameters (BF16 operands, FP32
+accumulation); the first Adam step moves each parameter by -lr sign(g)
+exactly where the gradient is clearly non-zero; a surrogate that rejects
+every cell reproduces the Newton chemistry bit for bit; a surrogate whose
+network predicts no change reproduces the run without chemistry."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_2310_17214_gb300 import inputs as I
+from paper_2310_17214_gb300 import surrogate as S
+from paper_2310_17214_gb300._native import Domain, Mlp, MLP_PARAMS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float64."""
+    x = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((x + 0x7FFF + ((x >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def tensors(flat):
+    """Per-tensor slices (W1, b1, ..., W4, b4) of a flat parameter vector."""
+    out, o = [], 0
+    for a, b in zip(M.DIMS[:-1], M.DIMS[1:]):
+        out += [flat[o:o + a * b], flat[o + a * b:o + a * b + b]]
+        o += a * b + b
+    return out
+
+
+def case(n, seed):
+    rng = np.random.default_rng(seed)
+    theta = (M.init(seed) + rng.normal(0, 0.02, M.n_params())).astype(np.float32)
+    X = rng.normal(0, 1, (n, 8)).astype(np.float32)
+    Y = (np.tanh(X[:, :6] * 0.8) + 0.2 * X[:, 2:8]).astype(np.float32)
+    return theta, X, Y
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [1, 16, 1000, 4133])
+def test_mlp_forward_matches_reference(n):
+    theta, X, _ = case(n, 1)
+    net = Mlp()
+    net.set_params(theta)
+    got = net.forward(dev(X)).cpu().numpy().astype(np.float64)
+    ref, _ = M.forward(bf16_round(theta), bf16_round(X))
+    assert np.max(np.abs(got - ref)) <= 2e-2 * np.max(np.abs(ref))
+    assert np.array_equal(net.get_params(), theta)
+    net.close()
+
+
+@pytest.mark.parametrize("n", [37, 4096, 20011])
+def test_mlp_gradient_matches_reference(n):
+    theta, X, Y = case(n, 2)
+    net = Mlp()
+    net.set_params(theta)
+    loss, g = net.gradient(dev(X), dev(Y))
+    Lr, gr = M.gradient(bf16_round(theta), bf16_round(X), Y.astype(np.float64))
+    assert abs(loss - Lr) <= 1e-2 * Lr
+    for t, (a, b) in enumerate(zip(tensors(g.astype(np.float64)), tensors(gr))):
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 2e-2, (t, rel)
+    net.close()
+
+
+def test_first_adam_step_moves_by_signed_learning_rate():
+    """Adam's first bias-corrected step is lr g / (|g| + eps): -lr sign(g)
+    wherever |g| is well above eps and the BF16 gradient has the sign of the
+    FP64 one."""
+    theta, X, Y = case(2048, 3)
+    lr = 1e-3
+    net = Mlp()
+    net.set_params(theta)
+    net.train(dev(X), dev(Y), batch=2048, steps=1, lr=lr)
+    step = net.get_params().astype(np.float64) - theta.astype(np.float64)
+    _, gr = M.gradient(bf16_round(theta), bf16_round(X), Y.astype(np.float64))
+    for a, b in zip(tensors(step), tensors(gr)):
+        clear = np.abs(b) > 0.2 * np.max(np.abs(b))
+        assert clear.sum() > 0
+        assert np.allclose(a[clear], -lr * np.sign(b[clear]), rtol=1e-3, atol=0)
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    theta, X, Y = case(65536, 4)
+    net = Mlp()
+    net.set_params(M.init(5).astype(np.float32))
+    Xd, Yd = dev(X), dev(Y)
+    L0, _ = net.gradient(Xd, Yd)
+    net.train(Xd, Yd, batch=4096, steps=400, lr=3e-3)
+    L1, _ = net.gradient(Xd, Yd)
+    assert L1 < 0.1 * L0
+    # the trained network's loss agrees with the reference at its own parameters
+    Lr = M.loss(bf16_round(net.get_params()), bf16_round(X), Y.astype(np.float64))
+    assert abs(L1 - Lr) <= 0.05 * Lr
+    net.close()
+
+
+# --------------------------------------------------- surrogate chemistry mode
+def _flame_case(nx=128, ny=40, chem="implicit", precision="fp32"):
+    p = I.config4(nx=nx, ny=ny, precision=precision, chem=chem)
+    p["bed"] = {"count": 4, "amin": 5, "amax": 8, "porosity": 0.6, "x0": nx // 2}
+    p["ignite"] = [8, 40, 1800.0]
+    return p, I.config4_fields(p)
+
+
+def _domain(p, f, precision):
+    d = Domain(p, precision)
+    d.set_phase_field(f["phi"], f["Ts"])
+    d.set_fields(f["T"], f["Y"])
+    return d
+
+
+def _surrogate_record(p, theta_s=0.0, tol=1e-6):
+    X = np.array([[300.0] + list(p["Y_in"]) + [p["P0"]]] * 2)
+    X[1, 0] = 2500.0
+    stats = (X.mean(axis=0), X.std(axis=0), np.zeros(6), np.zeros(6))
+    s = S.make_surrogate(stats, X, theta_s, p["species"], tol)
+    return s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_surrogate_rejecting_every_cell_equals_newton(precision):
+    """Tolerance -1 sends every fluid cell through the fallback list: the run
+    must be the Newton run exactly."""
+    p, f = _flame_case(precision=precision)
+    ref = _domain(p, f, precision)
+    ref.step(60)
+    a = ref.get("T", "Y", "g")
+    ps = dict(p, chem="surrogate")
+    dom = _domain(ps, f, precision)
+    net = Mlp()
+    net.set_params(np.zeros(MLP_PARAMS, dtype=np.float32))
+    dom.set_surrogate(net, _surrogate_record(p, tol=-1.0))
+    dom.step(60)
+    b = dom.get("T", "Y", "g")
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    fb, ev = dom.chem_stats()
+    assert ev > 0 and fb == ev
+    dom.close()
+    ref.close()
+    net.close()
+
+
+def test_surrogate_predicting_no_change_equals_no_chemistry():
+    p, f = _flame_case(precision="fp64")
+    ref = _domain(dict(p, chem="none"), f, "fp64")
+    ref.step(40)
+    a = ref.get("T", "Y", "u")
+    dom = _domain(dict(p, chem="surrogate"), f, "fp64")
+    net = Mlp()
+    net.set_params(np.zeros(MLP_PARAMS, dtype=np.float32))
+    rec = _surrogate_record(p)
+    rec.lo[0], rec.hi[0] = 0.0, 1e4
+    for k in range(1, 7):
+        rec.lo[k], rec.hi[k] = -1.0, 2.0
+    dom.set_surrogate(net, rec)
+    dom.step(40)
+    b = dom.get("T", "Y", "u")
+    for k in a:
+        assert np.max(np.abs(a[k] - b[k])) <= 1e-13 * max(np.max(np.abs(a[k])), 1.0), k
+    fb, ev = dom.chem_stats()
+    assert fb == 0 and ev > 0
+    dom.close()
+    ref.close()
+    net.close()
+
+
+def test_chem_increments_of_newton_mode_match_one_step():
+    """pflb_chem_increments in the Newton mode against the oracle's
+    backward-Euler integrator, cell by cell, on a state after ignition."""
+    from oracle import oracle as O
+    p, f = _flame_case(nx=96, ny=24, precision="fp64")
+    dom = _domain(p, f, "fp64")
+    dom.step(5)
+    dY, dT = dom.chem_increments()
+    g = dom.get("T", "Y")
+    P0 = dom.scalars()["P0"]
+    rng = np.random.default_rng(0)
+    fluid = np.flatnonzero(1.0 - f["phi"] >= 1e-6)
+    cells = np.concatenate([rng.choice(fluid, 40, replace=False),
+                            fluid[np.argsort(-np.abs(dT[fluid]))[:20]]])
+    for c in cells:
+        T, Y = g["T"][c], g["Y"][:, c]
+        rho_lat = P0 / (I.R_GAS * T * np.sum(Y / np.asarray(p["M"]))) / p["rho_ref"]
+        ry, rt, rc = O.chem_implicit(p, T, Y, rho_lat)
+        assert rc == 0
+        assert abs(dT[c] - rt) <= 1e-9 * max(abs(rt), 1e-3)
+        assert np.max(np.abs(dY[:, c] - ry)) <= 1e-9 * max(np.max(np.abs(ry)), 1e-12)
+    dom.close()

@@ -1,0 +1,72 @@
+"""Host-side logic of the surrogate driver (no GPU): the element table, the
+sample selection and the normalisation."""
+import numpy as np
+
+from paper_2310_17214_gb300 import inputs as I
+from paper_2310_17214_gb300 import surrogate as S
+
+
+def test_element_matrix_annihilates_every_reaction():
+    """Each reaction conserves every element: sum_k a_ek s_kj = 0.  A wrong
+    atom count in the table breaks one of these sums."""
+    elem, emass = I.element_matrix(I.SPECIES6)
+    for r in I.two_step_mechanism():
+        for e in range(4):
+            assert abs(sum(a * s for a, s in zip(elem[e], r["stoich"]))) < 1e-12
+    # element masses rebuild the species molar masses
+    for k in range(6):
+        assert abs(sum(elem[e][k] * emass[e] for e in range(4)) - I.M6[k]) < 1e-15
+
+
+def test_residual_weights_vanish_on_reaction_increments():
+    """dY_k = M_k s_kj xi is an exact reaction increment: its element
+    residual sum_k a_ek M_e / M_k dY_k is zero."""
+    elem, emass = I.element_matrix(I.SPECIES6)
+    for r in I.two_step_mechanism():
+        dY = np.array([m * s for m, s in zip(I.M6, r["stoich"])]) * 1e-4
+        for e in range(4):
+            res = sum(elem[e][k] * emass[e] / I.M6[k] * dY[k] for k in range(6))
+            assert abs(res) < 1e-18
+
+
+def test_selection_keeps_active_cells_and_a_uniform_rest():
+    rng = np.random.default_rng(0)
+    n = 10000
+    dT = np.zeros(n)
+    act = rng.choice(n, 300, replace=False)
+    dT[act] = rng.uniform(0.5, 1.0, 300)
+    fluid = np.ones(n, bool)
+    fluid[:100] = False
+    dY = np.zeros((6, n))
+    sel = S.select_samples(dY, dT, fluid, rng, 1000, active_frac=0.5)
+    assert len(sel) == 1000 and len(np.unique(sel)) == 1000
+    assert np.all(fluid[sel])
+    n_act = np.isin(sel, act[fluid[act]]).sum()
+    assert n_act == min(500, fluid[act].sum())
+
+
+def test_normalisation_round_trips_and_marks_constants():
+    rng = np.random.default_rng(1)
+    X = np.column_stack([rng.uniform(300, 2200, 500), rng.uniform(0, 0.2, (500, 6)),
+                         np.full(500, 101325.0)])
+    theta = 12000.0
+    # increments shaped like Arrhenius rates: exp(-theta / T) times O(1e-2)
+    D = np.exp(-theta / X[:, :1]) * rng.normal(0, 1e-2, (500, 6))
+    D[:, 5] = 0.0
+    (xm, xs, ym, ys), Xn, Yn = S.normalisation(X, D, theta)
+    assert xs[7] == 0.0 and np.all(Xn[:, 7] == 0.0)
+    assert ys[5] == 0.0 and ym[5] == 0.0
+    rebuilt = np.exp(-theta / X[:, 0])[:, None] * (ym + ys * Yn.astype(np.float64))
+    assert np.max(np.abs(rebuilt - D)) <= 1e-6 * np.max(np.abs(D))
+    assert np.allclose(Xn[:, :7].mean(axis=0), 0, atol=1e-5)
+
+
+def test_surrogate_record_layout():
+    p = I.config4(nx=64, ny=32)
+    X = np.array([[300.0] + list(p["Y_in"]) + [p["P0"]], [2000.0] + list(p["Y_in"]) + [p["P0"]]])
+    stats = (X.mean(0), X.std(0), np.zeros(6), np.ones(6))
+    s = S.make_surrogate(stats, X, 12000.0, p["species"], 1e-6)
+    assert s.n_elem == 4 and s.tol == 1e-6 and s.theta_s == 12000.0
+    assert s.lo[0] == 300.0 - 17.0 and s.hi[0] == 2000.0 + 17.0
+    assert s.lo[7] < p["P0"] < s.hi[7] and s.hi[7] - s.lo[7] < 1e-5 * p["P0"]
+    assert s.elem[1][0] == 4.0 and s.elem[3][5] == 2.0
