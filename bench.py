@@ -324,6 +324,79 @@ def error_vs_fp64(prob, fields, steps, dev):
             "T_l2_rel": l2(out["fp32"]["T"] - prob["T_in"], out["fp64"]["T"] - prob["T_in"])}
 
 
+def _ms_per_step(dom, steps, flush, st):
+    """Mean device time of one step (CUDA events, L2 flushed between steps)."""
+    import torch
+    for _ in range(3):
+        flush.zero_()
+        dom.step(1)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        dom.step(1)
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6):
+    """The learned chemistry on the two-step bed (2048 x 512, six species):
+    sample the Newton run (FP32 transport), train on the GPU, run the
+    surrogate from the same initial state, and compare it with the Newton
+    run after `steps` steps; then time the plain FP64 step (FP64 transport
+    and Newton), the FP32 + Newton step and the FP32 + surrogate step."""
+    import torch
+    from paper_2310_17214_gb300 import surrogate as S
+    from paper_2310_17214_gb300._native import Domain
+    st = torch.cuda.current_stream(dev)
+    p = I.config4(precision="fp32")
+    f = I.config4_fields(p)
+
+    def dom_of(chem, prec):
+        d = Domain(dict(p, chem=chem), prec, stream=st.cuda_stream, device=dev.index)
+        d.set_phase_field(f["phi"], f["Ts"])
+        d.set_fields(f["T"], f["Y"])
+        return d
+
+    ref = dom_of("implicit", "fp32")
+    t0 = time.perf_counter()
+    X, D = S.collect(ref, f["phi"], samples, 8, steps // 8, seed=0)
+    t_collect = time.perf_counter() - t0
+    ref.step(steps - 7 * (steps // 8))
+    theta = S.theta_scale(p)
+    stats, Xn, Yn = S.normalisation(X, D, theta)
+    t0 = time.perf_counter()
+    net, loss = S.train(Xn, Yn, epochs=epochs, batch=8192, seed=0, device=dev.index)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    sur = dom_of("surrogate", "fp32")
+    sur.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], tol))
+    sur.step(steps)
+    err = S.flame_errors(sur.get("T"), ref.get("T"), f["phi"], p)
+    fb, ev = sur.chem_stats()
+    t_newton32 = _ms_per_step(ref, 30, flush, st)
+    t_sur = _ms_per_step(sur, 100, flush, st)
+    d64 = dom_of("implicit", "fp64")
+    t_plain64 = _ms_per_step(d64, 20, flush, st)
+    for d in (ref, sur, d64):
+        d.close()
+    net.close()
+    N = f["phi"].size
+    return {"workload": f"two_step_bed_{p['nx']}x{p['ny']}_d2q9_k6",
+            "plain_fp64_ms_per_step": t_plain64, "fp32_newton_ms_per_step": t_newton32,
+            "fp32_surrogate_ms_per_step": t_sur,
+            "surrogate_mlups": N / t_sur / 1e3, "plain_fp64_mlups": N / t_plain64 / 1e3,
+            "speedup_vs_plain_fp64": t_plain64 / t_sur,
+            "speedup_vs_fp32_newton": t_newton32 / t_sur,
+            "error_after_steps": steps, "error_vs": "FP32 + Newton run from the same state",
+            **err, "fallback_frac": fb / ev if ev else None, "residual_tol": tol,
+            "samples": int(len(X)), "sample_s": t_collect, "train_epochs": epochs,
+            "train_s": t_train, "train_loss": loss}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,6 +449,7 @@ def main():
                               "achieved_gbs": alg_bytes_per_cell(prob, "fp64") * N / t64 / 1e9}
         extra["speedup_vs_fp64"] = t64 / per_launch
         extra["error_vs_fp64"] = error_vs_fp64(prob, fields, 500, dev)
+        extra["surrogate"] = surrogate_leg(dev, flush)
         e2e_v, nb = e2e_measure(prob, fields, args.precision, 30, dev)
         e2e = {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb,

@@ -163,3 +163,52 @@ def build(prob, dom, phi, n_samples=1_000_000, snapshots=8, steps_between=100, e
     net, loss = train(Xn, Yn, device=device, epochs=epochs, batch=batch, seed=seed, log=log)
     surr = make_surrogate(stats, X, theta_s, prob["species"], tol)
     return net, surr, {"samples": len(X), "loss": loss, "theta_s": theta_s}
+
+
+# ------------------------------------------------------------ error measures
+def adiabatic_temperature(prob) -> float:
+    """T_in plus the heat of complete combustion of the inlet mixture over
+    the burnt mixture's heat capacity (constant c_p,k)."""
+    from .inputs import burnt_composition
+    Yin = np.asarray(prob["Y_in"])
+    Yb = np.asarray(burnt_composition(list(Yin), prob["species"], prob["M"]))
+    hf, cp = np.asarray(prob["hf"]), np.asarray(prob["cp"])
+    return float(prob["T_in"] - np.sum(hf * (Yb - Yin)) / np.sum(cp * Yb))
+
+
+def front_positions(T, level):
+    """Per row of a [ny, nx] temperature field, the first and the last x
+    where T crosses `level`, linearly interpolated (NaN where it does not)."""
+    ny, nx = T.shape
+    out = np.full((ny, 2), np.nan)
+    for r in range(ny):
+        hot = np.flatnonzero(T[r] >= level)
+        if hot.size == 0:
+            continue
+        x0, x1 = hot.min(), hot.max()
+        if x0 > 0:
+            out[r, 0] = x0 - (T[r, x0] - level) / (T[r, x0] - T[r, x0 - 1])
+        if x1 < nx - 1:
+            out[r, 1] = x1 + (T[r, x1] - level) / (T[r, x1] - T[r, x1 + 1])
+    return out
+
+
+def flame_errors(T_test, T_ref, phi, prob):
+    """Flame-front shift (cells; the progress variable (T - T_in) / (T_ad -
+    T_in) crossing 1/2, per row, both edges, maximum over rows) and the
+    temperature error over fluid cells (phi_f > 1/2) of a run against a
+    reference run."""
+    ny, nx = prob["ny"], prob["nx"]
+    level = prob["T_in"] + 0.5 * (adiabatic_temperature(prob) - prob["T_in"])
+    fa = front_positions(np.asarray(T_test).reshape(ny, nx), level)
+    fb = front_positions(np.asarray(T_ref).reshape(ny, nx), level)
+    both = ~np.isnan(fa) & ~np.isnan(fb)
+    one = np.isnan(fa) != np.isnan(fb)
+    fluid = (1.0 - np.asarray(phi).reshape(-1)) > 0.5
+    d = np.abs(np.asarray(T_test) - np.asarray(T_ref))[fluid]
+    ref = np.asarray(T_ref)[fluid] - prob["T_in"]
+    return {"front_max_diff_cells": float(np.max(np.abs(fa - fb)[both])) if both.any() else None,
+            "rows_with_front": int(both[:, 1].sum()),
+            "rows_front_mismatch": int(one.sum()),
+            "T_max_abs_diff_K": float(d.max()),
+            "T_l2_rel": float(np.linalg.norm(d) / np.linalg.norm(ref))}

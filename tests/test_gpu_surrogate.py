@@ -201,3 +201,47 @@ def test_chem_increments_of_newton_mode_match_one_step():
         assert abs(dT[c] - rt) <= 1e-9 * max(abs(rt), 1e-3)
         assert np.max(np.abs(dY[:, c] - ry)) <= 1e-9 * max(np.max(np.abs(ry)), 1e-12)
     dom.close()
+
+
+def _ms_per_step(dom, steps=40):
+    dom.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    dom.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def test_trained_surrogate_tracks_the_flame_and_beats_newton():
+    """What the trained network gains: on a 1024 x 256 two-step bed, a network
+    trained by the library's kernels on samples of the Newton run reproduces
+    that run after 2000 steps (flame front within one cell, temperature
+    within 20 K over fluid cells), with few fallback cells, and its
+    chemistry step is several times faster than the Newton step."""
+    p = I.config4(nx=1024, ny=256, precision="fp32")
+    f = I.config4_fields(p)
+    steps = 2000
+    ref = _domain(p, f, "fp32")
+    X, D = S.collect(ref, f["phi"], 400_000, 8, steps // 8, seed=1)
+    ref.step(steps - 7 * (steps // 8))
+    theta = S.theta_scale(p)
+    stats, Xn, Yn = S.normalisation(X, D, theta)
+    net, loss = S.train(Xn, Yn, epochs=40, batch=8192, seed=1)
+    assert loss < 1e-3
+    sur = _domain(dict(p, chem="surrogate"), f, "fp32")
+    sur.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], 1e-6))
+    sur.step(steps)
+    Ta, Tb = sur.get("T"), ref.get("T")
+    err = S.flame_errors(Ta, Tb, f["phi"], p)
+    assert err["rows_with_front"] > 200 and err["rows_front_mismatch"] == 0
+    assert err["front_max_diff_cells"] <= 1.0
+    assert err["T_max_abs_diff_K"] <= 20.0
+    fb, ev = sur.chem_stats()
+    assert fb / ev < 0.02
+    t_newton, t_sur = _ms_per_step(ref), _ms_per_step(sur)
+    assert t_sur * 3.0 < t_newton, (t_sur, t_newton)
+    sur.close()
+    ref.close()
+    net.close()

@@ -70,3 +70,35 @@ def test_surrogate_record_layout():
     assert s.lo[0] == 300.0 - 17.0 and s.hi[0] == 2000.0 + 17.0
     assert s.lo[7] < p["P0"] < s.hi[7] and s.hi[7] - s.lo[7] < 1e-5 * p["P0"]
     assert s.elem[1][0] == 4.0 and s.elem[3][5] == 2.0
+
+
+def test_adiabatic_temperature_closes_the_energy_balance():
+    """Complete combustion at constant c_p: sum_k hf_k (Yb - Yin) + cp_b
+    (T_ad - T_in) = 0, and the lean mixture has O2 left and no CH4."""
+    p = I.config4(nx=64, ny=32)
+    Tad = S.adiabatic_temperature(p)
+    Yin = np.array(p["Y_in"])
+    Yb = np.array(I.burnt_composition(list(Yin), p["species"], p["M"]))
+    assert Yb[0] == 0.0 and Yb[1] > 0.0
+    assert abs(np.sum(np.array(p["hf"]) * (Yb - Yin)) +
+               np.sum(np.array(p["cp"]) * Yb) * (Tad - p["T_in"])) < 1e-6
+    assert 1700.0 < Tad < 1950.0
+
+
+def test_front_positions_interpolate_a_linear_ramp_exactly():
+    nx = 50
+    x = np.arange(nx, dtype=float)
+    T = np.tile(np.clip(300.0 + 100.0 * (x - 10.0), 300.0, 2300.0), (3, 1))
+    T = np.minimum(T, np.tile(np.clip(300.0 + 100.0 * (40.0 - x), 300.0, 2300.0), (3, 1)))
+    f = S.front_positions(T, 1050.0)
+    assert np.allclose(f[:, 0], 17.5) and np.allclose(f[:, 1], 32.5)
+
+
+def test_flame_errors_see_a_shift_of_a_third_of_a_cell():
+    p = I.config4(nx=64, ny=4)
+    x = np.arange(64, dtype=float)
+    ref = np.tile(300.0 + 1500.0 / (1.0 + np.exp((x - 30.0) / 2.0)), (4, 1)).reshape(-1)
+    test = np.tile(300.0 + 1500.0 / (1.0 + np.exp((x - 30.0 - 1.0 / 3.0) / 2.0)), (4, 1)).reshape(-1)
+    e = S.flame_errors(test, ref, np.zeros(64 * 4), p)
+    assert abs(e["front_max_diff_cells"] - 1.0 / 3.0) < 0.02
+    assert e["rows_with_front"] == 4 and e["rows_front_mismatch"] == 0
