@@ -281,6 +281,41 @@ int pflb_chem_increments(pflb_domain* d, void* dst, size_t bytes, int dtype, int
  * the integrator and cells the network evaluated.  Synchronises. */
 int pflb_chem_stats(pflb_domain* d, double* fallback_cells, double* evaluated_cells);
 
+/* ------------------------------------------------------------------------
+ * Batched stepping.  Not in the paper: an added pattern for many independent
+ * particle assemblies (2-D, no species).  One persistent kernel per step
+ * walks the tiles of every domain of the batch; the steps are replayed from
+ * a captured CUDA graph (two steps per graph).  Domains keep their own
+ * arrays and stay usable through the single-domain calls; a batch step
+ * leaves every domain's scalars current (no deferred reduction).
+ * ------------------------------------------------------------------------ */
+typedef struct pflb_batch pflb_batch;
+#define PFLB_BATCH_TILE_32x8 0
+#define PFLB_BATCH_TILE_32x16 1 /* two rows per thread */
+#define PFLB_BATCH_TILE_64x4 2
+#define PFLB_BATCH_TILES 3
+
+/* A batch over n domains (all 2-D, K = 0, same precision and device, fields
+ * set).  The domains must outlive the batch.  PFLB_ERR_UNSUPPORTED when a
+ * domain cannot be batched. */
+int pflb_create_batch(pflb_domain** domains, int n, pflb_batch** out);
+/* Advance every domain of the batch by nsteps (asynchronous; ordered after
+ * the work already queued on the domains' streams, and their streams wait
+ * for it). */
+int pflb_batch_step(pflb_batch* b, int nsteps);
+/* Tile shape (PFLB_BATCH_TILE_*) and resident blocks per SM (0: the most
+ * the kernel allows) of the persistent grid. */
+int pflb_batch_set_config(pflb_batch* b, int tile, int blocks_per_sm);
+int pflb_batch_get_config(const pflb_batch* b, int* tile, int* blocks_per_sm, int* grid);
+/* Time every (tile shape, blocks per SM) pair over `steps` batch steps,
+ * keep the fastest, and put every domain back in its state before the
+ * call.  us_per_step (may be NULL) receives PFLB_BATCH_TILES x 8 values,
+ * [tile][blocks_per_sm - 1], 0 where not run.  Synchronises. */
+int pflb_batch_autotune(pflb_batch* b, int steps, int* tile, int* blocks_per_sm,
+                        double* us_per_step);
+int pflb_batch_destroy(pflb_batch* b);
+const char* pflb_batch_last_error(const pflb_batch* b);
+
 /* Largest lattice (cells) that pflb_step_noalloc accepts. */
 #define PFLB_NOALLOC_MAX_CELLS (1 << 22)
 

@@ -112,6 +112,15 @@ def lib():
         L.pflb_set_surrogate.argtypes = [vp, vp, C.POINTER(Surrogate)]
         L.pflb_chem_increments.argtypes = [vp, vp, C.c_size_t, C.c_int, C.c_int]
         L.pflb_chem_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.pflb_create_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+        L.pflb_batch_step.argtypes = [vp, C.c_int]
+        L.pflb_batch_set_config.argtypes = [vp, C.c_int, C.c_int]
+        L.pflb_batch_get_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                            C.POINTER(C.c_int)]
+        L.pflb_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
+        L.pflb_batch_destroy.argtypes = [vp]
+        L.pflb_batch_last_error.argtypes = [vp]
+        L.pflb_batch_last_error.restype = C.c_char_p
         L.pflb_last_error.argtypes = [vp]
         L.pflb_last_error.restype = C.c_char_p
         _lib = L
@@ -448,6 +457,61 @@ class Mlp:
     def close(self):
         if self._h:
             lib().pflb_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many 2-D domains without species advanced together: one persistent
+    kernel per step over all their tiles, replayed from a CUDA graph."""
+
+    TILES = {"32x8": 0, "32x16": 1, "64x4": 2}
+
+    def __init__(self, domains):
+        self.domains = list(domains)  # kept alive as long as the batch
+        arr = (C.c_void_p * len(self.domains))(*[d._h.value for d in self.domains])
+        self._h = C.c_void_p()
+        rc = lib().pflb_create_batch(arr, len(self.domains), C.byref(self._h))
+        if rc != 0:
+            msg = lib().pflb_batch_last_error(None)
+            raise PflbError(f"pflb_create_batch error {rc}: {msg.decode() if msg else ''}")
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = lib().pflb_batch_last_error(self._h)
+            raise PflbError(f"pflb batch error {rc}: {msg.decode() if msg else ''}")
+
+    def step(self, n: int = 1):
+        self._check(lib().pflb_batch_step(self._h, int(n)))
+
+    def set_config(self, tile: str = "32x8", blocks_per_sm: int = 0):
+        self._check(lib().pflb_batch_set_config(self._h, self.TILES[tile], int(blocks_per_sm)))
+
+    def config(self):
+        t, b, g = C.c_int(), C.c_int(), C.c_int()
+        self._check(lib().pflb_batch_get_config(self._h, C.byref(t), C.byref(b), C.byref(g)))
+        names = {v: k for k, v in self.TILES.items()}
+        return {"tile": names[t.value], "blocks_per_sm": b.value, "grid": g.value}
+
+    def autotune(self, steps: int = 5):
+        """Time every (tile shape, blocks per SM), keep the fastest; the
+        domains' states are put back.  Returns (config, {(tile, bps): us})."""
+        t, b = C.c_int(), C.c_int()
+        us = np.zeros(3 * 8)
+        self._check(lib().pflb_batch_autotune(self._h, int(steps), C.byref(t), C.byref(b),
+                                              us.ctypes.data))
+        names = {v: k for k, v in self.TILES.items()}
+        table = {(names[i // 8], i % 8 + 1): float(us[i]) for i in range(24) if us[i] > 0}
+        return self.config(), table
+
+    def close(self):
+        if self._h:
+            lib().pflb_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

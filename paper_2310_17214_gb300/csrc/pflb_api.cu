@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <utility>
+#include <vector>
 
 #include "../../include/pflb.h"
 #include "pflb_launch.cuh"
@@ -205,9 +206,13 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
     return fail(nullptr, PFLB_ERR_CUDA, "%s", cudaGetErrorString(e));
   }
   const size_t n = (size_t)N;
-  // partial sums: one slot per block of the 1-D init grid or the step's tile grid
-  const long long tiles = (long long)((D.nx + 31) / 32) * ((D.ny + 7) / 8) *
-                          (D.dim == 3 ? (D.nz + 15) / 16 : 1);
+  // partial sums: one slot per block of the 1-D init grid or of any tile grid
+  // (the step's 32 x 8 tiles and the batch's tile shapes)
+  long long tiles = 0;
+  for (int cfg = 0; cfg < BATCH_SHAPES; ++cfg)
+    tiles = std::max<long long>(tiles, (long long)((D.nx + batch_tx(cfg) - 1) / batch_tx(cfg)) *
+                                           ((D.ny + batch_ty(cfg) - 1) / batch_ty(cfg)) *
+                                           (D.dim == 3 ? (D.nz + 15) / 16 : 1));
   const long long blocks = std::max<long long>((N + BLOCK - 1) / BLOCK, tiles);
   bool ok = true;
   auto al = [&](void** p, size_t bytes) {
@@ -735,6 +740,316 @@ int pflb_destroy(pflb_domain* d) {
   delete d->L;
   delete d;
   return PFLB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct pflb_batch {
+  std::vector<pflb_domain*> doms;
+  std::vector<int> cur_expected;  // each domain's input buffer at the next batch step
+  Launcher* L0 = nullptr;
+  int device = 0;
+  cudaStream_t stream = nullptr;  // the batch's own (blocking) stream
+  cudaEvent_t ev = nullptr;
+  size_t entry_bytes = 0;
+  void* entries = nullptr;        // device work list [n][entry_bytes]
+  std::vector<unsigned char> host_entries;
+  int* tile_begin[BATCH_SHAPES] = {};  // device prefix sums per tile shape
+  int occ[BATCH_SHAPES] = {};
+  int sms = 0;
+  int cfg = 0, bps = 0, grid = 0;
+  int flip = 0;                   // parity of the next batch step
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps, starting at flip 0 / 1
+  std::string err;
+};
+
+namespace {
+
+int bfail(pflb_batch* b, int code, const char* msg) {
+  if (b) b->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+void drop_graphs(pflb_batch* b) {
+  for (auto& g : b->graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+int batch_grid(const pflb_batch* b, int cfg, int bps) {
+  const int occ = b->occ[cfg];
+  const int per = bps > 0 ? std::min(bps, occ) : occ;
+  return std::max(1, per * b->sms);
+}
+
+// Rebuild the work list when a domain was stepped on its own since the last
+// batch step (its input buffer moved); order the batch after the domains'
+// queued work and fold their deferred reductions.
+int batch_prepare(pflb_batch* b) {
+  bool stale = false;
+  for (size_t i = 0; i < b->doms.size(); ++i) {
+    pflb_domain* d = b->doms[i];
+    if (d->L->finalize(d->B, d->stream) != cudaSuccess)
+      return bfail(b, PFLB_ERR_CUDA, "finalize of a member domain failed");
+    if ((d->cur ^ b->flip) != b->cur_expected[i]) stale = true;
+  }
+  if (stale) {
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+      pflb_domain* d = b->doms[i];
+      b->doms[i]->L->batch_entry(b->host_entries.data() + i * b->entry_bytes, d->B,
+                                 d->cur ^ b->flip);
+      b->cur_expected[i] = d->cur ^ b->flip;
+    }
+  }
+  cudaStream_t last = reinterpret_cast<cudaStream_t>(-1);
+  for (pflb_domain* d : b->doms) {
+    if (d->stream == last) continue;
+    last = d->stream;
+    if (cudaEventRecord(b->ev, d->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev, 0) != cudaSuccess)
+      return bfail(b, PFLB_ERR_CUDA, "stream ordering failed");
+  }
+  if (stale &&
+      cudaMemcpyAsync(b->entries, b->host_entries.data(), b->host_entries.size(),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return bfail(b, PFLB_ERR_CUDA, "work list upload failed");
+  if (stale && cudaStreamSynchronize(b->stream) != cudaSuccess)  // host staging reused
+    return bfail(b, PFLB_ERR_CUDA, "work list upload failed");
+  return PFLB_OK;
+}
+
+int batch_finish(pflb_batch* b, int nsteps) {
+  if (cudaEventRecord(b->ev, b->stream) != cudaSuccess)
+    return bfail(b, PFLB_ERR_CUDA, "stream ordering failed");
+  cudaStream_t last = reinterpret_cast<cudaStream_t>(-1);
+  for (pflb_domain* d : b->doms) {
+    if ((nsteps & 1) != 0) d->cur ^= 1;
+    d->B.pending = 0;
+    if (d->stream == last) continue;
+    last = d->stream;
+    if (cudaStreamWaitEvent(d->stream, b->ev, 0) != cudaSuccess)
+      return bfail(b, PFLB_ERR_CUDA, "stream ordering failed");
+  }
+  return PFLB_OK;
+}
+
+cudaError_t batch_launch_one(pflb_batch* b, int flip) {
+  return b->L0->batch_launch(b->entries, b->tile_begin[b->cfg], (int)b->doms.size(), b->cfg,
+                             b->grid, flip, b->stream);
+}
+
+cudaError_t batch_capture(pflb_batch* b, int start) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = batch_launch_one(b, start);
+  cudaError_t e2 = batch_launch_one(b, start ^ 1);
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (e == cudaSuccess && e1 == cudaSuccess && e2 == cudaSuccess)
+    e = cudaGraphInstantiate(&b->graph[start], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+  if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+  return e;
+}
+
+// nsteps batch steps on the batch stream: graph replays of two steps, one
+// plain launch for an odd remainder.
+int batch_run(pflb_batch* b, int nsteps) {
+  int n = nsteps;
+  while (n >= 2) {
+    if (!b->graph[b->flip]) {
+      cudaError_t e = batch_capture(b, b->flip);
+      if (e != cudaSuccess) return bfail(b, PFLB_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (cudaGraphLaunch(b->graph[b->flip], b->stream) != cudaSuccess)
+      return bfail(b, PFLB_ERR_CUDA, "graph launch failed");
+    n -= 2;
+  }
+  if (n == 1) {
+    cudaError_t e = batch_launch_one(b, b->flip);
+    if (e != cudaSuccess) return bfail(b, PFLB_ERR_CUDA, cudaGetErrorString(e));
+    b->flip ^= 1;
+  }
+  return PFLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pflb_create_batch(pflb_domain** domains, int n, pflb_batch** out) {
+  if (!domains || !out || n < 1) return bfail(nullptr, PFLB_ERR_ARG, "NULL argument or n < 1");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    pflb_domain* d = domains[i];
+    if (!d) return bfail(nullptr, PFLB_ERR_ARG, "NULL domain");
+    if (!d->L || !d->has_fields) return bfail(nullptr, PFLB_ERR_STATE, "set_fields must come first");
+    if (d->L->batch_entry_bytes() == 0)
+      return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "only 2-D domains without species batch");
+    if (d->L->batch_key() != domains[0]->L->batch_key())
+      return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "domains of a batch share one precision");
+    if (d->desc.device != domains[0]->desc.device)
+      return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "domains of a batch share one device");
+    for (int j = 0; j < i; ++j)
+      if (domains[j] == d) return bfail(nullptr, PFLB_ERR_ARG, "a domain appears twice");
+  }
+  pflb_batch* b = new (std::nothrow) pflb_batch();
+  if (!b) return bfail(nullptr, PFLB_ERR_OOM, "host allocation failed");
+  b->doms.assign(domains, domains + n);
+  b->L0 = domains[0]->L;
+  b->device = domains[0]->desc.device;
+  b->entry_bytes = b->L0->batch_entry_bytes();
+  b->host_entries.resize(b->entry_bytes * n);
+  b->cur_expected.assign(n, -1);
+  auto bad = [&](int code, const char* msg) {
+    pflb_batch_destroy(b);
+    return bfail(nullptr, code, msg);
+  };
+  if (cudaSetDevice(b->device) != cudaSuccess) return bad(PFLB_ERR_CUDA, "cudaSetDevice failed");
+  if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+    return bad(PFLB_ERR_CUDA, "device query failed");
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
+    return bad(PFLB_ERR_CUDA, "stream creation failed");
+  if (cudaMalloc(&b->entries, b->host_entries.size()) != cudaSuccess)
+    return bad(PFLB_ERR_OOM, "device allocation failed");
+  for (int cfg = 0; cfg < BATCH_SHAPES; ++cfg) {
+    std::vector<int> tb(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      const pflb_domain_desc& D = domains[i]->desc;
+      const long long t = (long long)((D.nx + batch_tx(cfg) - 1) / batch_tx(cfg)) *
+                          ((D.ny + batch_ty(cfg) - 1) / batch_ty(cfg));
+      if (t > domains[i]->B.slots) return bad(PFLB_ERR_STATE, "reduction slots too few");
+      if ((long long)tb[i] + t > (1LL << 30)) return bad(PFLB_ERR_ARG, "batch too large");
+      tb[i + 1] = tb[i] + (int)t;
+    }
+    if (cudaMalloc((void**)&b->tile_begin[cfg], (n + 1) * sizeof(int)) != cudaSuccess)
+      return bad(PFLB_ERR_OOM, "device allocation failed");
+    if (cudaMemcpy(b->tile_begin[cfg], tb.data(), (n + 1) * sizeof(int),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return bad(PFLB_ERR_CUDA, "upload failed");
+    b->occ[cfg] = b->L0->batch_occupancy(cfg);
+    if (b->occ[cfg] < 1) return bad(PFLB_ERR_CUDA, "batch kernel has no occupancy");
+  }
+  b->cfg = 0;
+  b->bps = 0;
+  b->grid = batch_grid(b, 0, 0);
+  *out = b;
+  return PFLB_OK;
+}
+
+int pflb_batch_step(pflb_batch* b, int nsteps) {
+  if (!b) return bfail(b, PFLB_ERR_ARG, "NULL batch");
+  if (nsteps < 0) return bfail(b, PFLB_ERR_ARG, "nsteps < 0");
+  if (nsteps == 0) return PFLB_OK;
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, PFLB_ERR_CUDA, "cudaSetDevice");
+  int r = batch_prepare(b);
+  if (r) return r;
+  if ((r = batch_run(b, nsteps))) return r;
+  return batch_finish(b, nsteps);
+}
+
+int pflb_batch_set_config(pflb_batch* b, int tile, int blocks_per_sm) {
+  if (!b) return bfail(b, PFLB_ERR_ARG, "NULL batch");
+  if (tile < 0 || tile >= BATCH_SHAPES || blocks_per_sm < 0)
+    return bfail(b, PFLB_ERR_ARG, "bad tile shape or blocks per SM");
+  if (blocks_per_sm > b->occ[tile]) return bfail(b, PFLB_ERR_ARG, "blocks per SM above occupancy");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return bfail(b, PFLB_ERR_CUDA, "synchronise failed");
+  drop_graphs(b);
+  b->cfg = tile;
+  b->bps = blocks_per_sm;
+  b->grid = batch_grid(b, tile, blocks_per_sm);
+  return PFLB_OK;
+}
+
+int pflb_batch_get_config(const pflb_batch* b, int* tile, int* blocks_per_sm, int* grid) {
+  if (!b) return PFLB_ERR_ARG;
+  if (tile) *tile = b->cfg;
+  if (blocks_per_sm) *blocks_per_sm = b->bps > 0 ? std::min(b->bps, b->occ[b->cfg]) : b->occ[b->cfg];
+  if (grid) *grid = b->grid;
+  return PFLB_OK;
+}
+
+int pflb_batch_autotune(pflb_batch* b, int steps, int* tile, int* blocks_per_sm,
+                        double* us_per_step) {
+  if (!b || !tile || !blocks_per_sm) return bfail(b, PFLB_ERR_ARG, "NULL argument");
+  if (steps < 1) return bfail(b, PFLB_ERR_ARG, "steps < 1");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, PFLB_ERR_CUDA, "cudaSetDevice");
+  const size_t n = b->doms.size();
+  std::vector<void*> snap(n, nullptr);
+  std::vector<size_t> nbytes(n, 0);
+  int r = PFLB_OK;
+  for (size_t i = 0; i < n && !r; ++i) {
+    nbytes[i] = state_bytes(b->doms[i]);
+    if (cudaMalloc(&snap[i], nbytes[i]) != cudaSuccess) r = bfail(b, PFLB_ERR_OOM, "snapshot");
+    else r = pflb_get_state(b->doms[i], snap[i], nbytes[i], PFLB_DEVICE);
+  }
+  if (us_per_step)
+    for (int k = 0; k < BATCH_SHAPES * 8; ++k) us_per_step[k] = 0;
+  const int cfg0 = b->cfg, bps0 = b->bps;
+  int best_cfg = cfg0, best_bps = bps0;
+  double best = -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int cfg = 0; cfg < BATCH_SHAPES && !r; ++cfg) {
+    for (int bps = 1; bps <= std::min(b->occ[cfg], 8) && !r; ++bps) {
+      if ((r = pflb_batch_set_config(b, cfg, bps))) break;
+      if ((r = pflb_batch_step(b, 2))) break;  // warm-up and graph capture
+      if ((r = batch_prepare(b))) break;
+      cudaEventRecord(e0, b->stream);
+      if ((r = batch_run(b, 2 * steps))) break;
+      cudaEventRecord(e1, b->stream);
+      if ((r = batch_finish(b, 2 * steps))) break;
+      float ms = 0;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        r = bfail(b, PFLB_ERR_CUDA, "timing failed");
+        break;
+      }
+      const double us = 1e3 * ms / (2 * steps);
+      if (us_per_step) us_per_step[cfg * 8 + bps - 1] = us;
+      if (best < 0 || us < best) { best = us; best_cfg = cfg; best_bps = bps; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t i = 0; i < n; ++i) {
+    if (snap[i]) {
+      int r2 = pflb_set_state(b->doms[i], snap[i], nbytes[i], PFLB_DEVICE);
+      if (!r && r2) r = bfail(b, r2, "restoring a domain failed");
+      cudaStreamSynchronize(b->doms[i]->stream);
+      cudaFree(snap[i]);
+    }
+  }
+  if (r) {
+    pflb_batch_set_config(b, cfg0, bps0);
+    return r;
+  }
+  if ((r = pflb_batch_set_config(b, best_cfg, best_bps))) return r;
+  *tile = b->cfg;
+  pflb_batch_get_config(b, nullptr, blocks_per_sm, nullptr);
+  return PFLB_OK;
+}
+
+int pflb_batch_destroy(pflb_batch* b) {
+  if (!b) return PFLB_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  for (int* p : b->tile_begin)
+    if (p) cudaFree(p);
+  if (b->entries) cudaFree(b->entries);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return PFLB_OK;
+}
+
+const char* pflb_batch_last_error(const pflb_batch* b) {
+  return b ? b->err.c_str() : g_create_err.c_str();
 }
 
 }  // extern "C"

@@ -73,16 +73,17 @@ template <> struct Lattice<3> {
   }
 };
 
-// Tile shape: 32 x (8 RPT) cells per plane, 256 threads; in 2-D every thread
-// can own RPT rows and issues the population loads of its cells before the
-// staging barrier (PREFETCH), so the two load phases overlap.  Measured on
-// GB300: one row per thread is fastest (two rows spill at the 64-register
-// cap); the prefetch helps the FP16-stored path.  3-D blocks march over ZC
-// planes.
-template <int DIM> struct Tile {
-  static constexpr int RPT = 1;
+// Tile shape: TX x (256 / TX) RPT cells per plane, 256 threads; in 2-D every
+// thread can own RPT rows and issues the population loads of its cells before
+// the staging barrier (PREFETCH), so the two load phases overlap.  Measured
+// on GB300 for the single-domain step: 32 x 8 with one row per thread is
+// fastest (two rows spill at the 64-register cap); the prefetch helps the
+// FP16-stored path.  The batched step lets its autotuner pick among shapes.
+// 3-D blocks march over ZC planes.
+template <int DIM, int TXv = 32, int RPTv = 1> struct Tile {
+  static constexpr int RPT = RPTv;
   static constexpr bool PREFETCH = DIM == 2;
-  static constexpr int TX = 32, TY = 8 * RPT;
+  static constexpr int TX = TXv, TY = (256 / TXv) * RPT;
   static constexpr int ZC = DIM == 3 ? 16 : 1;
   static constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
   static constexpr int NPL = DIM == 3 ? 3 : 1;  // staged planes
@@ -588,6 +589,60 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // Block sum of one per-thread value into FP64 (result in thread 0).  FP32
 // values are summed within the warp with compensation (the pair s + e is
 // exact up to the final rounding), warps are combined in FP64.
+// Warp part of the sums below (result in lane 0).
+template <class Real>
+__device__ __forceinline__ double warp_sum(Real v) {
+  if constexpr (sizeof(Real) == 4) {
+    float s = v, e = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float so = __shfl_down_sync(0xffffffffu, s, o);
+      const float eo = __shfl_down_sync(0xffffffffu, e, o);
+      float t, err;
+      two_sum(s, so, t, err);
+      s = t;
+      e = e + eo + err;
+    }
+    return double(s) + double(e);
+  } else {
+    double w = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    return w;
+  }
+}
+
+// The three sums of a tile (I, and the two fluxes when `bc` holds) with one
+// barrier, grouped exactly as block_sum; results valid in thread 0.  `sh`
+// holds 96 doubles and is free again after the block's next barrier.
+template <class Real>
+__device__ __forceinline__ void block_sum3(Real a, Real b, Real c, bool bc, double* sh,
+                                           double& ra, double& rb, double& rc) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double wa = warp_sum(a);
+  const double wb = bc ? warp_sum(b) : 0.0, wc = bc ? warp_sum(c) : 0.0;
+  if (lane == 0) {
+    sh[wid] = wa;
+    sh[32 + wid] = wb;
+    sh[64 + wid] = wc;
+  }
+  __syncthreads();
+  ra = rb = rc = 0.0;
+  if (wid == 0) {
+    const bool in = lane < (int)(blockDim.x >> 5);
+    double x = in ? sh[lane] : 0.0, y = in ? sh[32 + lane] : 0.0, z = in ? sh[64 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+      z += __shfl_down_sync(0xffffffffu, z, o);
+    }
+    ra = x;
+    rb = bc ? y : 0.0;
+    rc = bc ? z : 0.0;
+  }
+}
+
 template <class Real>
 __device__ __forceinline__ double block_sum(Real v, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -690,16 +745,15 @@ __device__ __forceinline__ void combine_partials(const double* partials, unsigne
 // the ticket; the other warps retire).  With a fixed P0 the combine is
 // deferred: block 0 of the next launch, or the on-demand finalize kernel,
 // does it, and the step ends without a serial tail.
-__device__ __forceinline__ void publish_partials(double sI, double sIn, double sOut,
-                                                 double* partials, unsigned* counter,
-                                                 DevScalars* scal, int p0_closed, bool is_init,
-                                                 double init_P0, double eos_c,
-                                                 double inv_rho_ref) {
+// Publish into slot `bid` of `nb`; `now` combines at the last arrival.
+__device__ __forceinline__ void publish_partials_at(double sI, double sIn, double sOut,
+                                                    double* partials, unsigned* counter,
+                                                    DevScalars* scal, int p0_closed, bool is_init,
+                                                    double init_P0, double eos_c,
+                                                    double inv_rho_ref, unsigned bid,
+                                                    unsigned nb, bool now) {
   if (threadIdx.x >= 32) return;
-  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   const int lane = threadIdx.x;
-  const bool now = p0_closed || is_init;
   unsigned last = 0;
   if (lane == 0) {
     partials[4 * bid + 0] = sI;
@@ -716,6 +770,17 @@ __device__ __forceinline__ void publish_partials(double sI, double sIn, double s
   __threadfence();
   combine_partials(partials, nb, scal, p0_closed, is_init, init_P0, eos_c, inv_rho_ref);
   if (lane == 0) *counter = 0u;
+}
+
+__device__ __forceinline__ void publish_partials(double sI, double sIn, double sOut,
+                                                 double* partials, unsigned* counter,
+                                                 DevScalars* scal, int p0_closed, bool is_init,
+                                                 double init_P0, double eos_c,
+                                                 double inv_rho_ref) {
+  publish_partials_at(sI, sIn, sOut, partials, counter, scal, p0_closed, is_init, init_P0, eos_c,
+                      inv_rho_ref,
+                      blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                      gridDim.x * gridDim.y * gridDim.z, p0_closed || is_init);
 }
 
 // On-demand combine of the deferred partials of the last step (one warp).
@@ -738,11 +803,11 @@ struct Plane {
 // xy halo.  Out-of-domain halo cells follow the ghost rules: periodic faces
 // wrap; otherwise the adjacent cell's values, with the inlet state (T_in,
 // Y_in) on the inlet face and the wall temperature on a wall that has one.
-template <int DIM, class Real, class Store, int K, int HP>
+template <int DIM, class Real, class Store, int K, int HP, class T_ = Tile<DIM>>
 __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const State<Real, Store>& S,
                                             Plane<Real, K, HP>& pl, int x0, int y0, int z,
                                             Real P0) {
-  using T_ = Tile<DIM>;
+  static_assert(T_::HP == HP, "plane and tile shape disagree");
   for (int h = threadIdx.x; h < HP; h += blockDim.x) {
     const int hx = h % T_::HX, hy = h / T_::HX;
     int q[3] = {x0 - 1 + hx, y0 - 1 + hy, z};
@@ -803,9 +868,9 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
 
 // Staged-plane accessor: own and neighbour values of the staged fields and
 // properties (the populations come from global memory).
-template <int DIM, class Real, bool PRE = false>
+template <int DIM, class Real, bool PRE = false, class TL = Tile<DIM>>
 struct PlaneAcc {
-  static constexpr int HP = Tile<DIM>::HP;
+  static constexpr int HP = TL::HP;
   static constexpr bool has_pops = PRE;  // populations prefetched into registers
   const Real* __restrict__ cen;
   const Real* __restrict__ zm;
@@ -815,7 +880,7 @@ struct PlaneAcc {
   __device__ __forceinline__ Real c(int f) const { return cen[f * HP + h]; }
   __device__ __forceinline__ Real n(int f, int a, int s) const {
     if (a == 0) return cen[f * HP + h + s];
-    if (a == 1) return cen[f * HP + h + s * Tile<DIM>::HX];
+    if (a == 1) return cen[f * HP + h + s * TL::HX];
     return (s < 0 ? zm : zp)[f * HP + h];
   }
   template <class Store>
@@ -1036,37 +1101,28 @@ template <int DIM, class Real, class Store> struct MinBlocks {
                                : (DIM == 2 || sizeof(Store) == 2 ? 4 : 3);
 };
 
-template <int DIM, int K, class Real, class Store>
-__global__ void __launch_bounds__(BLOCK, MinBlocks<DIM, Real, Store>::value)
-step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
-            const double* __restrict__ prev_partials) {
-  using T_ = Tile<DIM>;
-  constexpr int HP = T_::HP;
-  using PL = Plane<Real, K, HP>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  PL* planes = reinterpret_cast<PL*>(smem_raw);
-  __shared__ double red_sh[32];
-
+// One tile of the fused step (tile (bx, by) of the xy grid, z-chunk bz in
+// 3-D): stages the tile's planes in `planes` (shared memory), updates its
+// cells and returns the block sums of the reduction in thread 0 (I, inlet
+// flux, outlet flux).  Every thread of the block calls it.
+template <int DIM, int K, class Real, class Store, class T_ = Tile<DIM>>
+__device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<Real, Store>& S,
+                                          int bx, int by, int bz,
+                                          Plane<Real, K, T_::HP>* planes, double* red_sh,
+                                          double& sI, double& sIn, double& sOut) {
   const Real P0 = scal_P0<Real>(S.scal);
   const Real dlnP0 = scal_dlnP0<Real>(S.scal);
   const Real dP0r = scal_dP0r<Real>(S.scal);
 
   const int tx = threadIdx.x % T_::TX, ty = threadIdx.x / T_::TX;
-  const int x0 = blockIdx.x * T_::TX, y0 = blockIdx.y * T_::TY;
+  const int x0 = bx * T_::TX, y0 = by * T_::TY;
   const int x = x0 + tx, y = y0 + ty;
   const int h = (ty + 1) * T_::HX + (tx + 1);
   const bool in_xy = x < P.nx && y < P.ny;
-  const int z_begin = blockIdx.z * T_::ZC;
+  const int z_begin = bz * T_::ZC;
   const int z_end = DIM == 3 ? min(z_begin + T_::ZC, P.nz) : 1;
   const bool flux_block = (x0 == 0 && P.bc[0] == BC_INLET) ||
                           (x0 + T_::TX >= P.nx && P.bc[1] == BC_OUTLET);
-
-  // deferred combine of the previous step's partials (fixed P0 only): block
-  // 0's first warp does it while the other blocks start on their cells
-  if (prev_partials && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
-      threadIdx.x < 32)
-    combine_partials(prev_partials, gridDim.x * gridDim.y * gridDim.z, S.scal, 0, false, 0.0,
-                     P.eos_c, P.inv_rho_ref);
 
   Real accI = 0, accIn = 0, accOut = 0;
   if constexpr (DIM == 2) {
@@ -1090,7 +1146,7 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
         }
       }
     }
-    stage_plane<DIM>(P, S, planes[0], x0, y0, 0, P0);
+    stage_plane<DIM, Real, Store, K, T_::HP, T_>(P, S, planes[0], x0, y0, 0, P0);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -1100,8 +1156,8 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
         const int xyz[3] = {x, yr, 0};
         const int hr = (ty + r * RS + 1) * T_::HX + (tx + 1);
         Real fi, fo;
-        const PlaneAcc<DIM, Real, T_::PREFETCH> A{&planes[0].f[0][0], nullptr, nullptr, hr,
-                                                  pre[r]};
+        const PlaneAcc<DIM, Real, T_::PREFETCH, T_> A{&planes[0].f[0][0], nullptr, nullptr, hr,
+                                                      pre[r]};
         accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
@@ -1109,17 +1165,19 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
     }
   } else {
     // ring of three staged planes: slot (z mod 3)
-    stage_plane<DIM>(P, S, planes[(z_begin + 2) % 3], x0, y0, z_begin - 1, P0);
-    stage_plane<DIM>(P, S, planes[z_begin % 3], x0, y0, z_begin, P0);
+    stage_plane<DIM, Real, Store, K, T_::HP, T_>(P, S, planes[(z_begin + 2) % 3], x0, y0,
+                                                 z_begin - 1, P0);
+    stage_plane<DIM, Real, Store, K, T_::HP, T_>(P, S, planes[z_begin % 3], x0, y0, z_begin, P0);
     for (int z = z_begin; z < z_end; ++z) {
-      stage_plane<DIM>(P, S, planes[(z + 1) % 3], x0, y0, z + 1, P0);
+      stage_plane<DIM, Real, Store, K, T_::HP, T_>(P, S, planes[(z + 1) % 3], x0, y0, z + 1, P0);
       __syncthreads();
       if (in_xy) {
         const int c = x + P.nx * (y + P.ny * z);
         const int xyz[3] = {x, y, z};
         Real fi, fo;
-        const PlaneAcc<DIM, Real> A{&planes[z % 3].f[0][0], &planes[(z + 2) % 3].f[0][0],
-                                    &planes[(z + 1) % 3].f[0][0], h, nullptr};
+        const PlaneAcc<DIM, Real, false, T_> A{&planes[z % 3].f[0][0],
+                                               &planes[(z + 2) % 3].f[0][0],
+                                               &planes[(z + 1) % 3].f[0][0], h, nullptr};
         accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
@@ -1128,20 +1186,38 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
     }
   }
 
-  // (d) block partials in FP64, deterministic finish by the last block
-  const double sI = block_sum<Real>(accI, red_sh);
-  double sIn = 0, sOut = 0;
-  if (flux_block) {
-    sIn = block_sum<Real>(accIn, red_sh);
-    sOut = block_sum<Real>(accOut, red_sh);
-  }
+  // (d) block partials in FP64 (one barrier)
+  block_sum3<Real>(accI, accIn, accOut, flux_block, red_sh, sI, sIn, sOut);
+}
+
+template <int DIM, int K, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK, MinBlocks<DIM, Real, Store>::value)
+step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
+            const double* __restrict__ prev_partials) {
+  using T_ = Tile<DIM>;
+  using PL = Plane<Real, K, T_::HP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PL* planes = reinterpret_cast<PL*>(smem_raw);
+  __shared__ double red_sh[96];
+
+  // deferred combine of the previous step's partials (fixed P0 only): block
+  // 0's first warp does it while the other blocks start on their cells
+  if (prev_partials && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
+      threadIdx.x < 32)
+    combine_partials(prev_partials, gridDim.x * gridDim.y * gridDim.z, S.scal, 0, false, 0.0,
+                     P.eos_c, P.inv_rho_ref);
+
+  double sI, sIn, sOut;
+  step_tile<DIM, K, Real, Store, T_>(P, S, blockIdx.x, blockIdx.y, blockIdx.z, planes, red_sh,
+                                     sI, sIn, sOut);
+  // deterministic finish by the last block (closed P0) or deferred
   publish_partials(sI, sIn, sOut, S.partials, S.counter, S.scal, p0_closed, false, 0.0, P.eos_c,
                    P.inv_rho_ref);
 }
 
-template <int DIM, int K, class Real>
+template <int DIM, int K, class Real, class T_ = Tile<DIM>>
 constexpr size_t step_smem_bytes() {
-  return sizeof(Plane<Real, K, Tile<DIM>::HP>) * Tile<DIM>::NPL;
+  return sizeof(Plane<Real, K, T_::HP>) * T_::NPL;
 }
 
 // ------------------------------------------- chemistry pre-pass (implicit)

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "../../include/pflb.h"
+#include "pflb_batch.cuh"
 #include "pflb_kernels.cuh"
 #include "pflb_surrogate.cuh"
 #include "pflb_tma.cuh"
@@ -96,6 +97,17 @@ struct Launcher {
   // into `out` ([K+1][N] doubles) when non-null
   virtual cudaError_t chem_pass(Buffers& B, int cur, double* out, cudaStream_t st) = 0;
   virtual float g_scale() const = 0;
+  // ---- batched stepping (2-D lattices without species) ----
+  // bytes of this domain's batch work-list entry (0: cannot be batched)
+  virtual size_t batch_entry_bytes() const = 0;
+  // the entry: parameters, both ping-pong states, P0 mode, current buffer
+  virtual void batch_entry(void* dst, const Buffers& B, int cur) const = 0;
+  // resident blocks per SM of the batch kernel for tile shape cfg
+  virtual int batch_occupancy(int cfg) const = 0;
+  virtual cudaError_t batch_launch(const void* entries, const int* tile_begin, int ndom, int cfg,
+                                   int grid, int flip, cudaStream_t st) const = 0;
+  // domains can share a batch when their keys are equal (same kernel)
+  virtual int batch_key() const = 0;
 };
 
 constexpr double R_GAS = 8.314;  // J/(mol K), value printed in Sec. 3.1
@@ -321,6 +333,63 @@ struct LauncherImpl final : Launcher {
     return false;
   }
   int kernel() const override { return kernel_sel; }
+
+  static constexpr bool kBatchable = DIM == 2 && K == 0;
+  size_t batch_entry_bytes() const override {
+    return kBatchable ? sizeof(BatchDom<K, Real, Store>) : 0;
+  }
+  void batch_entry(void* dst, const Buffers& B, int cur) const override {
+    if constexpr (kBatchable) {
+      BatchDom<K, Real, Store> e;
+      std::memset(&e, 0, sizeof(e));
+      e.P = P;
+      e.S[0] = state(B, 0);
+      e.S[1] = state(B, 1);
+      e.p0_closed = p0_closed;
+      e.cur0 = cur;
+      std::memcpy(dst, &e, sizeof(e));
+    }
+  }
+  template <int CFG>
+  static int batch_occ_of() {
+    using T_ = typename BatchShape<CFG>::T;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, batch_step_kernel<K, Real, Store, T_>, BLOCK,
+            batch_smem_bytes<K, Real, T_>()) != cudaSuccess)
+      return 0;
+    return nb;
+  }
+  int batch_occupancy(int cfg) const override {
+    if constexpr (kBatchable) {
+      return cfg == 0 ? batch_occ_of<0>() : cfg == 1 ? batch_occ_of<1>()
+                                                      : cfg == 2 ? batch_occ_of<2>() : 0;
+    } else {
+      return 0;
+    }
+  }
+  template <int CFG>
+  static cudaError_t batch_launch_cfg(const void* entries, const int* tile_begin, int ndom,
+                                      int grid, int flip, cudaStream_t st) {
+    using T_ = typename BatchShape<CFG>::T;
+    batch_step_kernel<K, Real, Store, T_><<<grid, BLOCK, batch_smem_bytes<K, Real, T_>(), st>>>(
+        static_cast<const BatchDom<K, Real, Store>*>(entries), tile_begin, ndom, flip);
+    return cudaGetLastError();
+  }
+  cudaError_t batch_launch(const void* entries, const int* tile_begin, int ndom, int cfg, int grid,
+                           int flip, cudaStream_t st) const override {
+    if constexpr (kBatchable) {
+      switch (cfg) {
+        case 0: return batch_launch_cfg<0>(entries, tile_begin, ndom, grid, flip, st);
+        case 1: return batch_launch_cfg<1>(entries, tile_begin, ndom, grid, flip, st);
+        case 2: return batch_launch_cfg<2>(entries, tile_begin, ndom, grid, flip, st);
+        default: return cudaErrorInvalidValue;
+      }
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+  int batch_key() const override { return kBatchable ? 100 + MODE : -1; }
 
   bool tma_usable(const Buffers& B, int cur) {
     if constexpr (!kTmaType) {

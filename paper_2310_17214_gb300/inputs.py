@@ -112,12 +112,14 @@ def _rot3(rng):
 
 
 def ellipse_assembly(nx, ny, count, amin, amax, porosity, eta, seed, x0, periodic_y=True,
-                     gap=None, max_attempts=200000):
+                     gap=None, max_attempts=200000, per_particle=None):
     """Seeded non-overlapping ellipses in a bed region starting at x0.
 
     The bed's length is chosen so that the solid area of the drawn particles
     gives the target porosity inside it; particles keep a gap of at least eta
-    (checked on the grid).  Returns (phi_s [ny, nx], info)."""
+    (checked on the grid).  With `per_particle`, a particle that finds no
+    place in that many draws makes the bed 10 % longer (dense targets jam
+    random sequential addition).  Returns (phi_s [ny, nx], info)."""
     rng = np.random.default_rng(seed)
     gap = eta if gap is None else gap
     axes = rng.uniform(amin, amax, size=(count, 2))
@@ -135,8 +137,15 @@ def ellipse_assembly(nx, ny, count, amin, amax, porosity, eta, seed, x0, periodi
         a, b = axes[idx]
         th = angles[idx]
         ok = False
+        tries = 0
         while attempts < max_attempts and not ok:
             attempts += 1
+            tries += 1
+            if per_particle and tries > per_particle:
+                grown = min(nx - x0 - 8, int(length * 1.1) + 1)
+                if grown == length:
+                    break
+                length, tries = grown, 0
             cx = rng.uniform(x0 + a, x0 + length - a)
             cy = rng.uniform(0, ny) if periodic_y else rng.uniform(b, ny - b)
             r = int(math.ceil(a + gap + eta)) + 1
@@ -312,6 +321,45 @@ def config1_fields(p):
     phi = disc_phi(p["nx"], p["ny"], 32.0, 32.0, 8.0, p["eta"]).reshape(-1)
     T = (1.0 - phi) * p["T_in"] + phi * p["Ts_uniform"]
     return {"phi": phi, "T": T, "Y": None, "Ts": None, "u": None}
+
+
+def config5(n=48, seed=5, precision="fp32", steps=2000, base=(256, 128)):
+    """n independent 2-D channel beds without species, advanced as a batch:
+    sizes log-uniform from 256x128 to 1024x512 (aspect 2:1, ragged), bed
+    porosity uniform in 0.4-0.8, parabolic inlet u_max uniform in 0.02-0.08,
+    lattice air (nu = 0.05) at 300 K over particles held at 600 K, ellipse
+    semi-axes growing with the domain, bed from x = nx/8 over about half
+    the channel.  Sizes, porosities and speeds come from one seeded PCG64;
+    `base` is the smallest size (tests use smaller beds)."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(n):
+        s = 2.0 ** rng.uniform(0.0, 2.0)
+        por = float(rng.uniform(0.4, 0.8))
+        umax = float(rng.uniform(0.02, 0.08))
+        nx, ny = int(round(base[0] * s)), int(round(base[1] * s))
+        g = s * base[0] / 256.0  # particle size scale
+        p = _base(2, nx, ny)
+        p["bc"] = ["inlet", "outlet", "wall", "wall", "periodic", "periodic"]
+        lattice_air(p, 0.05)
+        p.update({"A_u": 145.0, "A_T": 70.0, "eta": 4.0, "inlet_parabolic": 1, "u_in": umax,
+                  "T_in": 300.0, "Ts_uniform": 600.0, "p0_mode": "fixed",
+                  "precision": precision, "steps": steps, "seed": seed * 1000 + i,
+                  "bed": {"count": max(4, int(round(65.5 * (1.0 - por)))), "amin": 6.0 * g,
+                          "amax": 14.0 * g, "porosity": por, "x0": nx // 8},
+                  "name": f"cfg5_bed_{i}_{nx}x{ny}_d2q9_{precision}"})
+        probs.append(p)
+    return probs
+
+
+def config5_fields(p):
+    b = p["bed"]
+    phi, info = ellipse_assembly(p["nx"], p["ny"], b["count"], b["amin"], b["amax"],
+                                 b["porosity"], p["eta"], p["seed"], b["x0"], periodic_y=False,
+                                 per_particle=200)
+    phi = phi.reshape(-1)
+    T = (1.0 - phi) * p["T_in"] + phi * p["Ts_uniform"]
+    return {"phi": phi, "T": T, "Y": None, "Ts": None, "u": None, "info": info}
 
 
 def _reactive_gas(p, species, M, cp, hf_mol, dref):
