@@ -754,6 +754,7 @@ struct pflb_batch {
   cudaEvent_t ev = nullptr;
   size_t entry_bytes = 0;
   void* entries = nullptr;        // device work list [n][entry_bytes]
+  unsigned* tile_ctr = nullptr;   // tile counters, one per launch parity
   std::vector<unsigned char> host_entries;
   int* tile_begin[BATCH_SHAPES] = {};  // device prefix sums per tile shape
   int occ[BATCH_SHAPES] = {};
@@ -836,7 +837,7 @@ int batch_finish(pflb_batch* b, int nsteps) {
 
 cudaError_t batch_launch_one(pflb_batch* b, int flip) {
   return b->L0->batch_launch(b->entries, b->tile_begin[b->cfg], (int)b->doms.size(), b->cfg,
-                             b->grid, flip, b->stream);
+                             b->grid, flip, b->tile_ctr, b->stream);
 }
 
 cudaError_t batch_capture(pflb_batch* b, int start) {
@@ -913,7 +914,9 @@ int pflb_create_batch(pflb_domain** domains, int n, pflb_batch** out) {
   if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess)
     return bad(PFLB_ERR_CUDA, "stream creation failed");
-  if (cudaMalloc(&b->entries, b->host_entries.size()) != cudaSuccess)
+  if (cudaMalloc(&b->entries, b->host_entries.size()) != cudaSuccess ||
+      cudaMalloc((void**)&b->tile_ctr, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(b->tile_ctr, 0, 2 * sizeof(unsigned)) != cudaSuccess)
     return bad(PFLB_ERR_OOM, "device allocation failed");
   for (int cfg = 0; cfg < BATCH_SHAPES; ++cfg) {
     std::vector<int> tb(n + 1, 0);
@@ -1042,6 +1045,7 @@ int pflb_batch_destroy(pflb_batch* b) {
   for (int* p : b->tile_begin)
     if (p) cudaFree(p);
   if (b->entries) cudaFree(b->entries);
+  if (b->tile_ctr) cudaFree(b->tile_ctr);
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;

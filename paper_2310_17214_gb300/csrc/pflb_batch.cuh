@@ -6,7 +6,10 @@
 // domains' tile counts.  A launch is a grid-stride loop over the global tile
 // index: a block finds the tile's domain by binary search, copies that
 // domain's parameters into shared memory when it changes domain, and runs the
-// same per-tile code as the single-domain step.  Each domain's reduction
+// same per-tile code as the single-domain step.  Tiles are handed out by an
+// atomic counter (one per launch parity; each launch clears the other one
+// for the next launch), so blocks that draw cheap tiles take more of them
+// and no SM idles at the end.  Each domain's reduction
 // slots are its tile indices, and the last tile of a domain to finish
 // combines them at once, so a batch step leaves no deferred work behind and
 // every domain's P0 is current for the next launch.
@@ -42,7 +45,8 @@ template <class Real, class Store, class T_> struct BatchMinBlocks {
 template <int K, class Real, class Store, class T_>
 __global__ void __launch_bounds__(BLOCK, (BatchMinBlocks<Real, Store, T_>::value))
 batch_step_kernel(const BatchDom<K, Real, Store>* __restrict__ doms,
-                  const int* __restrict__ tile_begin, int ndom, int flip) {
+                  const int* __restrict__ tile_begin, int ndom, int flip,
+                  unsigned* __restrict__ tile_ctr) {
   using PL = Plane<Real, K, T_::HP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PL* planes = reinterpret_cast<PL*>(smem_raw);
@@ -50,10 +54,17 @@ batch_step_kernel(const BatchDom<K, Real, Store>* __restrict__ doms,
   __shared__ Params<Real, K> Psh;
   __shared__ State<Real, Store> Ssh;
   __shared__ int p0c_sh;
+  __shared__ int next_sh[2];
 
   const int total = tile_begin[ndom];
-  int cur_dom = -1;
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+  unsigned* ctr = tile_ctr + flip;
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) tile_ctr[flip ^ 1] = 0u;  // the next launch's counter
+    next_sh[0] = (int)atomicAdd(ctr, 1u);
+  }
+  __syncthreads();
+  int cur_dom = -1, par = 0;
+  for (int t = next_sh[0]; t < total; t = next_sh[par]) {
     // domain of tile t: the last d with tile_begin[d] <= t
     int lo = 0, hi = ndom - 1;
     while (lo < hi) {
@@ -75,6 +86,9 @@ batch_step_kernel(const BatchDom<K, Real, Store>* __restrict__ doms,
       __syncthreads();
       cur_dom = lo;
     }
+    // draw the next tile now; the tile's staging barrier publishes it
+    par ^= 1;
+    if (threadIdx.x == 0) next_sh[par] = (int)atomicAdd(ctr, 1u);
     const int lt = t - tile_begin[lo];
     const int nbx = (Psh.nx + T_::TX - 1) / T_::TX;
     double sI, sIn, sOut;

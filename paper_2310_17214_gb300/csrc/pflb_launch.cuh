@@ -105,7 +105,8 @@ struct Launcher {
   // resident blocks per SM of the batch kernel for tile shape cfg
   virtual int batch_occupancy(int cfg) const = 0;
   virtual cudaError_t batch_launch(const void* entries, const int* tile_begin, int ndom, int cfg,
-                                   int grid, int flip, cudaStream_t st) const = 0;
+                                   int grid, int flip, unsigned* tile_ctr,
+                                   cudaStream_t st) const = 0;
   // domains can share a batch when their keys are equal (same kernel)
   virtual int batch_key() const = 0;
 };
@@ -370,19 +371,19 @@ struct LauncherImpl final : Launcher {
   }
   template <int CFG>
   static cudaError_t batch_launch_cfg(const void* entries, const int* tile_begin, int ndom,
-                                      int grid, int flip, cudaStream_t st) {
+                                      int grid, int flip, unsigned* ctr, cudaStream_t st) {
     using T_ = typename BatchShape<CFG>::T;
     batch_step_kernel<K, Real, Store, T_><<<grid, BLOCK, batch_smem_bytes<K, Real, T_>(), st>>>(
-        static_cast<const BatchDom<K, Real, Store>*>(entries), tile_begin, ndom, flip);
+        static_cast<const BatchDom<K, Real, Store>*>(entries), tile_begin, ndom, flip, ctr);
     return cudaGetLastError();
   }
   cudaError_t batch_launch(const void* entries, const int* tile_begin, int ndom, int cfg, int grid,
-                           int flip, cudaStream_t st) const override {
+                           int flip, unsigned* ctr, cudaStream_t st) const override {
     if constexpr (kBatchable) {
       switch (cfg) {
-        case 0: return batch_launch_cfg<0>(entries, tile_begin, ndom, grid, flip, st);
-        case 1: return batch_launch_cfg<1>(entries, tile_begin, ndom, grid, flip, st);
-        case 2: return batch_launch_cfg<2>(entries, tile_begin, ndom, grid, flip, st);
+        case 0: return batch_launch_cfg<0>(entries, tile_begin, ndom, grid, flip, ctr, st);
+        case 1: return batch_launch_cfg<1>(entries, tile_begin, ndom, grid, flip, ctr, st);
+        case 2: return batch_launch_cfg<2>(entries, tile_begin, ndom, grid, flip, ctr, st);
         default: return cudaErrorInvalidValue;
       }
     } else {
