@@ -208,6 +208,12 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
  * stage (2-D, FP32 compute, nx a multiple of 4 -- 8 with FP16 storage). */
 #define PFLB_KERNEL_TILED 0
 #define PFLB_KERNEL_TMA 1
+/* PFLB_KERNEL_PERSISTENT(_32x16): 2-D only; one grid of resident blocks walks
+ * the 32 x 8 (or 32 x 16, two rows per thread) tiles, handed out by an
+ * atomic counter, so no second wave and no idle SMs at the end. */
+#define PFLB_KERNEL_PERSISTENT 2
+#define PFLB_KERNEL_PERSISTENT_32x16 3
+#define PFLB_KERNELS 4
 
 /* Select the step kernel of a domain (after pflb_set_fields).  Returns
  * PFLB_ERR_UNSUPPORTED if the kernel cannot run this domain. */
@@ -216,8 +222,9 @@ int pflb_select_kernel(pflb_domain* d, int kernel);
 /* Time every step kernel that can run this domain over `steps` steps each
  * and keep the fastest (the domain's state is restored afterwards, so the
  * physics is unchanged).  *chosen receives the kernel, *us_per_step (may be
- * NULL) the time per step of each candidate in kernel order (2 values, a
- * negative value for a kernel that cannot run).  Synchronises the stream. */
+ * NULL) the time per step of each candidate in kernel order (PFLB_KERNELS
+ * values, a negative value for a kernel that cannot run).  Synchronises the
+ * stream. */
 int pflb_autotune(pflb_domain* d, int steps, int* chosen, double* us_per_step);
 
 /* ------------------------------------------------------------------------

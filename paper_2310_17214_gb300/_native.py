@@ -294,7 +294,7 @@ class Domain:
         _check(lib().pflb_get_scalars(self._h, C.byref(s)), self._h)
         return {f: getattr(s, f) for f, _ in Scalars._fields_}
 
-    KERNELS = {"tiled": 0, "tma": 1}
+    KERNELS = {"tiled": 0, "tma": 1, "persistent": 2, "persistent_32x16": 3}
 
     def select_kernel(self, name: str):
         _check(lib().pflb_select_kernel(self._h, self.KERNELS[name]), self._h)
@@ -303,11 +303,11 @@ class Domain:
         """Time each step kernel (state restored afterwards), keep the fastest.
         Returns (chosen name, {name: us per step or None})."""
         ch = C.c_int()
-        us = np.zeros(2)
+        us = np.zeros(len(self.KERNELS))
         _check(lib().pflb_autotune(self._h, int(steps), C.byref(ch), us.ctypes.data), self._h)
         names = {v: k for k, v in self.KERNELS.items()}
         return names[ch.value], {names[i]: (float(us[i]) if us[i] > 0 else None)
-                                 for i in range(2)}
+                                 for i in range(len(self.KERNELS))}
 
     def set_surrogate(self, net: "Mlp", surr: Surrogate):
         """Attach a trained network (chem mode "surrogate", six species)."""

@@ -126,7 +126,7 @@ Launcher* make_launcher(const pflb_domain* d) {
 void free_buffers(pflb_domain* d) {
   void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
                   d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
-                  d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats};
+                  d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats, d->B.tile_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::memset(&d->B, 0, sizeof(d->B));
@@ -230,6 +230,7 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   d->B.slots = blocks;
   al((void**)&d->B.partials, (size_t)blocks * 2 * 4 * sizeof(double));
   al((void**)&d->B.counter, sizeof(unsigned));
+  al((void**)&d->B.tile_ctr, 2 * sizeof(unsigned));
   if (!ok) {
     cudaGetLastError();
     free_buffers(d);
@@ -584,7 +585,7 @@ int pflb_autotune(pflb_domain* d, int steps, int* chosen, double* us_per_step) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < PFLB_KERNELS; ++k) {
     double us = -1;
     if (d->L->select_kernel(k, d->B, d->cur)) {
       cudaError_t e = d->L->step(d->B, d->cur, 1, d->stream);  // warm-up

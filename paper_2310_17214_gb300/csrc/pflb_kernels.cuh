@@ -1193,7 +1193,7 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
 template <int DIM, int K, class Real, class Store>
 __global__ void __launch_bounds__(BLOCK, MinBlocks<DIM, Real, Store>::value)
 step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
-            const double* __restrict__ prev_partials) {
+            const double* __restrict__ prev_partials, unsigned prev_nb) {
   using T_ = Tile<DIM>;
   using PL = Plane<Real, K, T_::HP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1204,8 +1204,7 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
   // 0's first warp does it while the other blocks start on their cells
   if (prev_partials && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 &&
       threadIdx.x < 32)
-    combine_partials(prev_partials, gridDim.x * gridDim.y * gridDim.z, S.scal, 0, false, 0.0,
-                     P.eos_c, P.inv_rho_ref);
+    combine_partials(prev_partials, prev_nb, S.scal, 0, false, 0.0, P.eos_c, P.inv_rho_ref);
 
   double sI, sIn, sOut;
   step_tile<DIM, K, Real, Store, T_>(P, S, blockIdx.x, blockIdx.y, blockIdx.z, planes, red_sh,
@@ -1213,6 +1212,47 @@ step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
   // deterministic finish by the last block (closed P0) or deferred
   publish_partials(sI, sIn, sOut, S.partials, S.counter, S.scal, p0_closed, false, 0.0, P.eos_c,
                    P.inv_rho_ref);
+}
+
+// Persistent variant of the 2-D step: one grid of resident blocks walks the
+// tiles, handed out by an atomic counter (one per step parity; each launch
+// clears the other one for the next step), so no block waits for a second
+// wave and cheap tiles do not leave SMs idle.  Reduction slots are the tile
+// indices, as in step_kernel.
+template <int DIM, int K, class Real, class Store, class T_>
+__global__ void __launch_bounds__(BLOCK, (sizeof(Real) == 8 ? 2 : (T_::RPT > 1 ? 3 : 4)))
+step_persistent_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
+                       const double* __restrict__ prev_partials, unsigned prev_nb,
+                       unsigned* __restrict__ tile_ctr, int parity) {
+  static_assert(DIM == 2, "the persistent step walks 2-D tiles");
+  using PL = Plane<Real, K, T_::HP>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PL* planes = reinterpret_cast<PL*>(smem_raw);
+  __shared__ double red_sh[96];
+  __shared__ int next_sh[2];
+
+  if (prev_partials && blockIdx.x == 0 && threadIdx.x < 32)
+    combine_partials(prev_partials, prev_nb, S.scal, 0, false, 0.0, P.eos_c, P.inv_rho_ref);
+
+  const int nbx = (P.nx + T_::TX - 1) / T_::TX;
+  const int total = nbx * ((P.ny + T_::TY - 1) / T_::TY);
+  unsigned* ctr = tile_ctr + parity;
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) tile_ctr[parity ^ 1] = 0u;  // the next step's counter
+    next_sh[0] = (int)atomicAdd(ctr, 1u);
+  }
+  __syncthreads();
+  int par = 0;
+  for (int t = next_sh[0]; t < total; t = next_sh[par]) {
+    // draw the next tile now; the tile's staging barrier publishes it
+    par ^= 1;
+    if (threadIdx.x == 0) next_sh[par] = (int)atomicAdd(ctr, 1u);
+    double sI, sIn, sOut;
+    step_tile<DIM, K, Real, Store, T_>(P, S, t % nbx, t / nbx, 0, planes, red_sh, sI, sIn,
+                                       sOut);
+    publish_partials_at(sI, sIn, sOut, S.partials, S.counter, S.scal, p0_closed, false, 0.0,
+                        P.eos_c, P.inv_rho_ref, (unsigned)t, (unsigned)total, p0_closed != 0);
+  }
 }
 
 template <int DIM, int K, class Real, class T_ = Tile<DIM>>

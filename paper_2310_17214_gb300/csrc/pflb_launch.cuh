@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -31,6 +32,7 @@ struct Buffers {
   DevScalars* scal;
   double* partials;        // two buffers of `slots` x 4 doubles (step parity)
   unsigned* counter;
+  unsigned* tile_ctr;      // tile counters of the persistent step, one per parity
   int N;
   long long slots;         // partial slots per buffer (>= blocks of any launch)
   int pending;             // the last step's partials are not combined yet
@@ -88,7 +90,8 @@ struct Launcher {
   // combine deferred partials of the last step into the scalar state
   virtual cudaError_t finalize(Buffers& B, cudaStream_t st) = 0;
   // step kernel: 0 = staged tiles, 1 = TMA-pipelined persistent tiles (2-D
-  // FP32 compute with 16-byte rows); returns false if not available here
+  // FP32 compute with 16-byte rows), 2 / 3 = persistent staged tiles 32 x 8 /
+  // 32 x 16 (2-D); returns false if not available here
   virtual bool select_kernel(int k, const Buffers& B, int cur) = 0;
   virtual int kernel() const = 0;
   // learned chemistry (six-species mechanism only)
@@ -331,7 +334,38 @@ struct LauncherImpl final : Launcher {
   bool select_kernel(int k, const Buffers& B, int cur) override {
     if (k == 0) { kernel_sel = 0; return true; }
     if (k == 1 && tma_usable(B, cur) && tma_usable(B, 1 - cur)) { kernel_sel = 1; return true; }
+    if ((k == 2 || k == 3) && DIM == 2 && B.tile_ctr) { kernel_sel = k; return true; }
     return false;
+  }
+
+  // persistent 2-D step with tile shape T_ (kernels 2: 32 x 8, 3: 32 x 16)
+  int pgrid[2] = {0, 0};
+  template <class T_>
+  cudaError_t step_persistent(Buffers& B, int cur, cudaStream_t st, const double* prev,
+                              int& grid_cache) {
+    if constexpr (DIM == 2) {
+      constexpr size_t smem = step_smem_bytes<DIM, K, Real, T_>();
+      auto kern = step_persistent_kernel<DIM, K, Real, Store, T_>;
+      if (grid_cache == 0) {
+        int dev = 0, sms = 0, occ = 0;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BLOCK, smem);
+        if (e != cudaSuccess) return e;
+        grid_cache = std::max(1, occ) * sms;
+      }
+      const int tiles = ((P.nx + T_::TX - 1) / T_::TX) * ((P.ny + T_::TY - 1) / T_::TY);
+      if (tiles > B.slots) return cudaErrorInvalidValue;
+      kern<<<std::min(grid_cache, tiles), BLOCK, smem, st>>>(
+          P, state(B, cur), p0_closed, prev, (unsigned)B.last_nb, B.tile_ctr, cur);
+      B.last_nb = tiles;
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
   }
   int kernel() const override { return kernel_sel; }
 
@@ -355,9 +389,12 @@ struct LauncherImpl final : Launcher {
   static int batch_occ_of() {
     using T_ = typename BatchShape<CFG>::T;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, batch_step_kernel<K, Real, Store, T_>, BLOCK,
-            batch_smem_bytes<K, Real, T_>()) != cudaSuccess)
+    auto kern = batch_step_kernel<K, Real, Store, T_>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem_bytes<K, Real, T_>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BLOCK,
+                                                      batch_smem_bytes<K, Real, T_>()) !=
+            cudaSuccess)
       return 0;
     return nb;
   }
@@ -462,7 +499,8 @@ struct LauncherImpl final : Launcher {
       const int n_tiles = tiles_x * ((P.ny + LY::TY - 1) / LY::TY);
       const TmaMaps& m = maps[cur];
       step_tma_kernel<K, Store><<<tma_grid, BLOCK, LY::smem_bytes, st>>>(
-          P, state(B, cur), p0_closed, prev, m.T, m.phi, m.Ts, m.Y, m.g, tiles_x, n_tiles);
+          P, state(B, cur), p0_closed, prev, (unsigned)B.last_nb, m.T, m.phi, m.Ts, m.Y, m.g,
+          tiles_x, n_tiles);
       B.last_nb = tma_grid;
       return cudaGetLastError();
     } else {
@@ -476,6 +514,11 @@ struct LauncherImpl final : Launcher {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid = step_grid();
+    if (kernel_sel >= 2 && nsteps > 0) {
+      // both counters start at zero; consecutive steps then clear each other's
+      e = cudaMemsetAsync(B.tile_ctr, 0, 2 * sizeof(unsigned), st);
+      if (e != cudaSuccess) return e;
+    }
     for (int n = 0; n < nsteps; ++n) {
       if constexpr (K > 0) {
         if (P.chem >= 2) {
@@ -488,9 +531,15 @@ struct LauncherImpl final : Launcher {
       if (kernel_sel == 1 && tma_usable(B, cur)) {
         e = step_tma(B, cur, st, prev);
         if (e != cudaSuccess) return e;
+      } else if (kernel_sel == 2) {
+        e = step_persistent<Tile<DIM, 32, 1>>(B, cur, st, prev, pgrid[0]);
+        if (e != cudaSuccess) return e;
+      } else if (kernel_sel == 3) {
+        e = step_persistent<Tile<DIM, 32, 2>>(B, cur, st, prev, pgrid[1]);
+        if (e != cudaSuccess) return e;
       } else {
         step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
-                                                                     prev);
+                                                                     prev, (unsigned)B.last_nb);
         B.last_nb = step_blocks();
       }
       B.pending = p0_closed ? 0 : 1;

@@ -264,7 +264,7 @@ __device__ __forceinline__ void issue_tile(const TmaMapRefs& M, const Params<flo
 template <int K, class Store>
 __global__ void __launch_bounds__(BLOCK, 2)
 step_tma_kernel(const Params<float, K> P, const State<float, Store> S, int p0_closed,
-                const double* __restrict__ prev_partials,
+                const double* __restrict__ prev_partials, unsigned prev_nb,
                 const __grid_constant__ CUtensorMap mT, const __grid_constant__ CUtensorMap mPhi,
                 const __grid_constant__ CUtensorMap mTs, const __grid_constant__ CUtensorMap mY,
                 const __grid_constant__ CUtensorMap mG, int tiles_x, int n_tiles) {
@@ -285,7 +285,7 @@ step_tma_kernel(const Params<float, K> P, const State<float, Store> S, int p0_cl
   const float dP0r = scal_dP0r<float>(S.scal);
 
   if (prev_partials && blockIdx.x == 0 && threadIdx.x < 32)
-    combine_partials(prev_partials, gridDim.x, S.scal, 0, false, 0.0, P.eos_c, P.inv_rho_ref);
+    combine_partials(prev_partials, prev_nb, S.scal, 0, false, 0.0, P.eos_c, P.inv_rho_ref);
 
   // self-check of the alignment every TMA issue relies on (the same answer
   // in every thread): record it and skip all copies rather than fault

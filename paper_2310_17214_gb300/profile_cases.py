@@ -1,0 +1,89 @@
+"""Small, self-contained workloads for profiler captures.
+
+    python -m paper_2310_17214_gb300.profile_cases surrogate [nx ny]
+    python -m paper_2310_17214_gb300.profile_cases batch [n_domains tile]
+
+Each case sets up its workload, warms up, and brackets a few steps with
+cudaProfilerStart / cudaProfilerStop (torch.cuda.profiler), so that a capture
+with `ncu --profile-from-start off` sees only those steps.
+
+surrogate: the two-step six-species bed (FP32 transport); samples the Newton
+run (200k rows), trains the network for 30 epochs, copies the Newton run's
+state into a surrogate-mode domain, then profiles three surrogate steps and
+two Newton steps.
+batch: the first n of the 48 batched beds (FP32, K = 0) with one tile shape
+at the most resident blocks; profiles two batch steps.
+"""
+from __future__ import annotations
+
+import sys
+
+from . import inputs as I
+from . import surrogate as S
+from ._native import Batch, Domain
+
+
+def surrogate_case(nx=2048, ny=512, precision="fp32"):
+    import torch
+    p = I.config4(nx=nx, ny=ny, precision=precision)
+    f = I.config4_fields(p)
+
+    def dom_of(chem):
+        d = Domain(dict(p, chem=chem), precision)
+        d.set_phase_field(f["phi"], f["Ts"])
+        d.set_fields(f["T"], f["Y"])
+        return d
+
+    d = dom_of("implicit")
+    X, D = S.collect(d, f["phi"], 200_000, 4, 500, seed=0)
+    theta = S.theta_scale(p)
+    stats, Xn, Yn = S.normalisation(X, D, theta)
+    net, _ = S.train(Xn, Yn, epochs=30, batch=8192)
+    sd = dom_of("surrogate")
+    sd.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], 1e-6))
+    sd.set_state(d.get_state())
+    sd.step(5)
+    d.step(5)
+    sd.scalars()
+    d.scalars()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    sd.step(3)
+    d.step(2)
+    sd.scalars()
+    d.scalars()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("fallback/evaluated", sd.chem_stats())
+
+
+def batch_case(n=48, tile="32x16"):
+    import torch
+    doms = []
+    for p in I.config5(n=n):
+        f = I.config5_fields(p)
+        d = Domain(p, "fp32")
+        d.set_phase_field(f["phi"], f["Ts"])
+        d.set_fields(f["T"])
+        doms.append(d)
+    b = Batch(doms)
+    b.set_config(tile, 0)
+    b.step(4)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    b.step(2)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(b.config(), sum(p["nx"] * p["ny"] for p in I.config5(n=n)))
+
+
+if __name__ == "__main__":
+    case = sys.argv[1] if len(sys.argv) > 1 else "surrogate"
+    if case == "surrogate":
+        args = [int(a) for a in sys.argv[2:4]]
+        surrogate_case(*args)
+    elif case == "batch":
+        batch_case(int(sys.argv[2]) if len(sys.argv) > 2 else 48,
+                   sys.argv[3] if len(sys.argv) > 3 else "32x16")
+    else:
+        raise SystemExit(f"unknown case {case}")

@@ -259,7 +259,8 @@ def test_autotune_keeps_the_physics():
     dom.set_phase_field(f["phi"], f["Ts"])
     dom.set_fields(f["T"], f["Y"])
     chosen, times = dom.autotune(10)
-    assert chosen in ("tiled", "tma") and times["tiled"] is not None
+    assert chosen in Domain.KERNELS and times["tiled"] is not None
+    assert times["persistent"] is not None and times["persistent_32x16"] is not None
     assert dom.scalars()["step"] == 0
     dom.select_kernel("tiled")
     dom.step(50)
@@ -274,8 +275,38 @@ def test_autotune_keeps_the_physics():
     d2.set_phase_field(g["phi"], g["Ts"])
     d2.set_fields(g["T"], g["Y"])
     chosen, times = d2.autotune(5)
-    assert chosen == "tiled" and times["tma"] is None
+    assert chosen != "tma" and times["tma"] is None
     d2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_fp16"])
+def test_persistent_kernels_equal_the_tiled_kernel(precision):
+    """The persistent kernels run the same per-tile code over the same tiles
+    (32 x 8) or taller ones (32 x 16): every field bit for bit, and kernels
+    may be switched between steps (the deferred reduction of the last step
+    is combined over the block count of the launch that wrote it)."""
+    p = I.config2(nx=200, ny=72, precision=precision)
+    p["bed"] = {"count": 6, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 50}
+    f = I.config2_fields(p)
+    runs = {}
+    for plan in (["tiled"], ["persistent"], ["persistent_32x16"],
+                 ["tiled", "persistent_32x16", "persistent", "tiled"]):
+        dom = Domain(p, precision)
+        dom.set_phase_field(f["phi"], f["Ts"])
+        dom.set_fields(f["T"], f["Y"])
+        for kern in plan * (4 // len(plan)):
+            dom.select_kernel(kern)
+            dom.step(15)
+        runs["/".join(plan)] = (dom.get("T", "g", "Y"), dom.scalars())
+        dom.close()
+    ref, sref = runs["tiled"]
+    for name, (got, sc) in runs.items():
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), (name, k)
+        assert sc["step"] == sref["step"] == 60
+        tol = 1e-12 if precision == "fp64" else 1e-6
+        for k in ("I", "mass", "flux_in", "flux_out"):
+            assert abs(sc[k] - sref[k]) <= tol * max(abs(sref[k]), 1e-300), (name, k)
 
 
 # ------------------------------------------------------ implicit chemistry
