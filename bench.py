@@ -61,6 +61,20 @@ def kernel_hash():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def recorded_fp64_flops(workload):
+    """FP64 flops per cell of the FP64 step from the committed ncu count, if
+    it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_fp64_flops.txt")
+    if not os.path.exists(path):
+        return None
+    h = kernel_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == workload and parts[1] == "fp64" and parts[2] == h:
+            return float(parts[3])
+    return None
+
+
 def recorded_traffic(workload, precision):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
@@ -502,6 +516,16 @@ def main():
                               "ms_per_step": t64 * 1e3, "steps": len(ms64),
                               "alg_bytes_per_cell": alg_bytes_per_cell(prob, "fp64"),
                               "achieved_gbs": alg_bytes_per_cell(prob, "fp64") * N / t64 / 1e9}
+        # the FP64 step is bound by the FP64 pipe: its roofline is the probed FMA rate
+        from paper_2310_17214_gb300._native import probe_fp64_tflops
+        peak64 = probe_fp64_tflops(dev.index)
+        fpc = recorded_fp64_flops(workload)
+        ach64 = fpc * N / t64 / 1e12 if fpc else None
+        extra["fp64_step"]["roofline"] = {
+            "bound": "alu", "unit": "TFLOP/s", "peak": peak64,
+            "peak_kind": "measured FP64 FMA rate (pflb_probe_fp64_fma)",
+            "flops_per_cell": fpc, "achieved": ach64,
+            "frac": ach64 / peak64 if ach64 else None}
         extra["speedup_vs_fp64"] = t64 / per_launch
         extra["error_vs_fp64"] = error_vs_fp64(prob, fields, 500, dev)
         extra["surrogate"] = surrogate_leg(dev, flush)

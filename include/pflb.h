@@ -323,6 +323,11 @@ int pflb_batch_autotune(pflb_batch* b, int steps, int* tile, int* blocks_per_sm,
 int pflb_batch_destroy(pflb_batch* b);
 const char* pflb_batch_last_error(const pflb_batch* b);
 
+/* Device diagnostic (not in the paper): the measured FP64 FMA rate of
+ * `device` in TFLOP/s (2 flops per FMA), the ceiling of the FP64 step and of
+ * the Newton chemistry.  Allocates 8 bytes, synchronises the device. */
+int pflb_probe_fp64_fma(int device, double* tflops);
+
 /* Largest lattice (cells) that pflb_step_noalloc accepts. */
 #define PFLB_NOALLOC_MAX_CELLS (1 << 22)
 

@@ -121,6 +121,7 @@ def lib():
         L.pflb_batch_destroy.argtypes = [vp]
         L.pflb_batch_last_error.argtypes = [vp]
         L.pflb_batch_last_error.restype = C.c_char_p
+        L.pflb_probe_fp64_fma.argtypes = [C.c_int, C.POINTER(C.c_double)]
         L.pflb_last_error.argtypes = [vp]
         L.pflb_last_error.restype = C.c_char_p
         _lib = L
@@ -519,3 +520,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def probe_fp64_tflops(device: int = 0) -> float:
+    """Measured FP64 FMA rate of the GPU (TFLOP/s), the FP64 paths' ceiling."""
+    t = C.c_double()
+    rc = lib().pflb_probe_fp64_fma(int(device), C.byref(t))
+    if rc != 0:
+        raise PflbError(f"pflb_probe_fp64_fma error {rc}")
+    return t.value

@@ -125,6 +125,7 @@ struct Params {
   Real Y_in[KK];
   Real M0, cp0;
   Real invM[KK], cp[KK], hf[KK], Dlat[KK];
+  Real cpD[KK];            // cp_k Dlat_k (enthalpy-flux cross term)
   int D_Tdep;
   Real inv_DTref, D_exp;
   int Ts_field;
@@ -808,6 +809,9 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
                                             Plane<Real, K, HP>& pl, int x0, int y0, int z,
                                             Real P0) {
   static_assert(T_::HP == HP, "plane and tile shape disagree");
+  // tiles whose halo lies inside the lattice need no ghost rules
+  const bool inner = x0 >= 1 && y0 >= 1 && x0 + T_::TX < P.nx && y0 + T_::TY < P.ny &&
+                     (DIM == 2 || (z >= 0 && z < P.nz));
   for (int h = threadIdx.x; h < HP; h += blockDim.x) {
     const int hx = h % T_::HX, hy = h / T_::HX;
     int q[3] = {x0 - 1 + hx, y0 - 1 + hy, z};
@@ -815,6 +819,7 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
     int nout = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
+      if (inner) break;
       const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
       if (q[a] < 0 || q[a] >= n) {
         const int face = 2 * a + (q[a] >= n ? 1 : 0);
@@ -973,20 +978,31 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const Real iphr = fluid_on ? fdiv(Real(1), phif * rho) : Real(0);
   const Real rf0 = A.c(F_RF);
 
-  // (b) species
+  // (b) species; the face factors (phi_f rho f_D averaged over the face) are
+  // shared by every species, and the central differences of Y_k feed the
+  // enthalpy-flux cross term of the temperature equation
   Real Yn[KK];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    Real adv = 0, dif = 0;
+  Real sx[3] = {0, 0, 0};  // sum_k cp_k D_k (Y_k(+) - Y_k(-)) per axis
+  {
+    Real fm[DIM], fp[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      const Real ym = at(F_Y0 + k, a, -1), yp = at(F_Y0 + k, a, +1);
-      adv += u[a] > Real(0) ? u[a] * (Y0[k] - ym) : u[a] * (yp - Y0[k]);
-      const Real km = Real(0.5) * P.Dlat[k] * (rf0 + at(F_RF, a, -1));
-      const Real kp = Real(0.5) * P.Dlat[k] * (rf0 + at(F_RF, a, +1));
-      dif += kp * (yp - Y0[k]) - km * (Y0[k] - ym);
+      fm[a] = Real(0.5) * (rf0 + at(F_RF, a, -1));
+      fp[a] = Real(0.5) * (rf0 + at(F_RF, a, +1));
     }
-    Yn[k] = fluid_on ? Y0[k] + (-phif * rho * adv + dif + phif * om[k]) * iphr : Y0[k];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      Real adv = 0, dif = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const Real dm = Y0[k] - at(F_Y0 + k, a, -1), dp = at(F_Y0 + k, a, +1) - Y0[k];
+        adv += u[a] * (u[a] > Real(0) ? dm : dp);
+        dif += fp[a] * dp - fm[a] * dm;
+        sx[a] += P.cpD[k] * (dp + dm);
+      }
+      Yn[k] = fluid_on ? Y0[k] + (-phif * rho * adv + P.Dlat[k] * dif + phif * om[k]) * iphr
+                       : Y0[k];
+    }
   }
 
   // (b) temperature
@@ -1001,14 +1017,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
       const Real km = Real(0.5) * (kc + at(F_KT, a, -1));
       const Real kp = Real(0.5) * (kc + at(F_KT, a, +1));
       dif += kp * (tp - T0) - km * (T0 - tm);
-      if constexpr (K > 0) {
-        const Real gT = Real(0.5) * (tp - tm);
-        Real s = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          s += P.cp[k] * P.Dlat[k] * (at(F_Y0 + k, a, +1) - at(F_Y0 + k, a, -1));
-        cross += Real(0.5) * fD * s * gT;
-      }
+      if constexpr (K > 0) cross += Real(0.25) * fD * sx[a] * (tp - tm);
     }
     const Real rhs = -phif * rho * cp * adv + dif + phif * (rho * cross + dP0r + omT + SI);
     Tn = T0 + rhs * iphr * fdiv(Real(1), cp);

@@ -153,6 +153,7 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
     P.cp[k] = Real(m.cp[k]);
     P.hf[k] = Real(m.hf[k]);
     P.Dlat[k] = Real(m.Dref[k] * h2);
+    P.cpD[k] = Real(m.cp[k] * m.Dref[k] * h2);
     P.rho_ref_M[k] = Real(d.rho_ref / m.M[k]);
   }
   P.D_Tdep = (K > 0 && m.D_exp != 0.0) ? 1 : 0;
