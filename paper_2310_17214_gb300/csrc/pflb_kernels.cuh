@@ -1062,32 +1062,37 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const Real Ph = sg + Real(0.5) * rho * CS2 * D;
   const Real omega = fdiv(Real(2) * rho, rho + Real(6) * mu);
   const Real src_w = Real(1) - Real(0.5) * omega;
-  Real uu = 0, uG = 0, uF = 0;
+  // f_eq / rho - w = w e with e = 3 cu + 9/2 cu^2 - 3/2 uu;
+  // g_eq = cs2 f_eq + w (P_h - rho cs2) = w (P_h + rho e / 3);
+  // Xi = w [(c - u).(G e + F (1 + e)) + rho cs2 D] = w [(c.H - u.H) e + c.F - u.F + rho cs2 D]
+  // with H = G + F.  Collected per cell: g* = (1 - omega) g + w [A0 + B e + src_w x],
+  // A0 = omega P_h + src_w rho cs2 D, B = omega rho cs2, x = (c.H - u.H) e + c.F - u.F.
+  Real H[3] = {0, 0, 0};
+  Real uu = 0, uH = 0, uF = 0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
+    H[a] = G[a] + F[a];
     uu += u[a] * u[a];
-    uG += u[a] * G[a];
+    uH += u[a] * H[a];
     uF += u[a] * F[a];
   }
-  const Real rD = rho * CS2 * D;
   const Real rho3 = rho * CS2;
+  const Real A0 = omega * Ph + src_w * (rho3 * D);
+  const Real B = omega * rho3;
+  const Real uu15 = Real(1.5) * uu;
+  const Real keep = Real(1) - omega;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const Real w = Real(L::w(i));
-    Real cu = 0, cG = 0, cF = 0;
+    Real cu = 0, cH = 0, cF = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      if (L::c(i, a) > 0) { cu += u[a]; cG += G[a]; cF += F[a]; }
-      if (L::c(i, a) < 0) { cu -= u[a]; cG -= G[a]; cF -= F[a]; }
+      if (L::c(i, a) > 0) { cu += u[a]; cH += H[a]; cF += F[a]; }
+      if (L::c(i, a) < 0) { cu -= u[a]; cH -= H[a]; cF -= F[a]; }
     }
-    // f_eq / rho - w = w e with e = 3 cu + 9/2 cu^2 - 3/2 uu;
-    // g_eq = cs2 f_eq + w (P_h - rho cs2) = w (P_h + rho e / 3);
-    // Xi = w [(c - u).(G e + F (1 + e)) + rho cs2 D]
-    const Real e = cu * (Real(3) + Real(4.5) * cu) - Real(1.5) * uu;
-    const Real geq = w * (Ph + rho3 * e);
-    const Real xs = (cG - uG) * e + (cF - uF) * (Real(1) + e);
-    const Real xi = w * (xs + rD);
-    const Real g = gin[i] + omega * (geq - gin[i]) + src_w * xi;
+    const Real e = cu * (Real(3) + Real(4.5) * cu) - uu15;
+    const Real x = (cH - uH) * e + (cF - uF);
+    const Real g = keep * gin[i] + w * (A0 + B * e + src_w * x);
     Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g, P.g_scale * Real(1.0 / L::w(i)));
   }
 
@@ -1106,8 +1111,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
 // GB300: FP32/FP16 2-D and FP16 3-D run best at <= 64 registers, FP32 3-D at
 // <= 85; FP64 is FP64-pipe bound and keeps the registers it needs).
 template <int DIM, class Real, class Store> struct MinBlocks {
-  static constexpr int value = sizeof(Real) == 8 ? (DIM == 3 ? 1 : 2)
-                               : (DIM == 2 || sizeof(Store) == 2 ? 4 : 3);
+  static constexpr int value = sizeof(Real) == 8 ? (DIM == 3 ? 1 : 2) : (DIM == 2 ? 4 : 3);
 };
 
 // One tile of the fused step (tile (bx, by) of the xy grid, z-chunk bz in
