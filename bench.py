@@ -57,8 +57,13 @@ def measured_peaks():
 
 
 def kernel_hash():
+    """Identity of the step kernel's build: its source and the compiler flags."""
+    from paper_2310_17214_gb300 import build as B
+    h = hashlib.sha256()
     with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        h.update(f.read())
+    h.update(" ".join(B.ARCH + B.FLAGS[:-2]).encode())  # the include path is machine-specific
+    return h.hexdigest()[:16]
 
 
 def recorded_fp64_flops(workload):
