@@ -61,3 +61,25 @@ def test_create_rejects_bad_descriptions_without_touching_the_gpu():
     d = nat.make_desc(p)
     d.dim = 4
     assert nat.lib().pflb_create_domain(ctypes.byref(d), ctypes.byref(h)) == -7
+
+
+def test_added_entry_points_reject_null_arguments_without_touching_the_gpu():
+    """The surrogate, batch and probe calls check their arguments before any
+    CUDA call: NULL handles and outputs give PFLB_ERR_ARG (-1)."""
+    L = nat.lib()
+    h = ctypes.c_void_p()
+    assert L.pflb_create_batch(None, 0, ctypes.byref(h)) == -1 and not h.value
+    assert L.pflb_create_batch(None, 3, None) == -1
+    assert L.pflb_batch_step(None, 1) == -1
+    assert L.pflb_batch_set_config(None, 0, 0) == -1
+    assert L.pflb_batch_get_config(None, None, None, None) == -1
+    assert L.pflb_batch_autotune(None, 1, None, None, None) == -1
+    assert L.pflb_batch_destroy(None) == 0
+    assert L.pflb_mlp_create(0, None, None) == -1
+    assert L.pflb_mlp_set_params(None, None) == -1
+    assert L.pflb_mlp_get_params(None, None) == -1
+    assert L.pflb_mlp_forward(None, None, None, 0) == -1
+    assert L.pflb_mlp_destroy(None) == 0
+    assert L.pflb_set_surrogate(None, None, None) == -1
+    assert L.pflb_chem_stats(None, None, None) == -1
+    assert L.pflb_probe_fp64_fma(0, None) == -1
