@@ -114,6 +114,9 @@ typedef struct pflb_domain_desc {
   double Ts_uniform;       /* K */
   double rhocp_s, lambda_s;/* solid volumetric heat capacity (J/m^3/K), conductivity (W/m/K) */
   double phi_min;          /* phase fraction below which a phase is frozen (e.g. 1e-6) */
+  double T_max;            /* hottest temperature the run may reach (K), e.g. the adiabatic
+                              flame temperature; 0 = none beyond T_in, Ts_uniform and the
+                              wall temperatures.  Only the stability checks read it. */
   void* stream;            /* cudaStream_t (NULL = legacy default stream) */
   int device;              /* CUDA device ordinal */
 } pflb_domain_desc;
@@ -151,11 +154,32 @@ typedef struct pflb_scalars {
   int status;              /* latched device status (PFLB_OK or PFLB_ERR_UNSTABLE) */
 } pflb_scalars;
 
-/* Create a domain: validates the description (tau > 1/2 at T_in, bc pairing),
- * allocates every device array (populations double-buffered for the pull
- * scheme).  Errors: PFLB_ERR_ARG, PFLB_ERR_UNSUPPORTED, PFLB_ERR_OOM,
- * PFLB_ERR_CUDA.  On error *out is NULL. */
+/* Create a domain: validates the description, then allocates every device
+ * array (populations double-buffered for the pull scheme).
+ *
+ * Checks before any CUDA call (so they run without a GPU):
+ *   PFLB_ERR_ARG / PFLB_ERR_UNSUPPORTED -- lattice extent, precision, boundary
+ *     kinds (periodic faces in pairs, inlet only at x-lo, outlet only at
+ *     x-hi), positive and finite dx, dt, rho_ref, Pr, eta, P0, mu_ref, M0, cp0;
+ *   PFLB_ERR_UNSTABLE -- the explicit scheme of Sec. 3.3 (BGK collision,
+ *     forward-Euler FD) is outside its stability range at one of T_in,
+ *     Ts_uniform, the wall temperatures or T_max, with the single gas of the
+ *     description (M0): relaxation time tau = 1/2 + nu/cs^2 not above 1/2,
+ *     thermal diffusion number lambda dt / (rho cp dx^2) above 1/(2 dim)
+ *     (1/4 in 2-D, 1/6 in 3-D), solid diffusion number above the same
+ *     limit, interface exchange number A_T lambda dt / (rho cp (eta dx)^2)
+ *     above 1, or |u_in| at or above the lattice sound speed 1/sqrt(3).
+ *     pflb_set_mechanism repeats the check with the inlet mixture and the
+ *     species diffusion numbers D_k(T) dt / dx^2.
+ * Other errors: PFLB_ERR_OOM, PFLB_ERR_CUDA.  On error *out is NULL and
+ * pflb_last_error(NULL) names the failed check. */
 int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out);
+
+/* The checks pflb_create_domain makes (and, when mech is not NULL, those of
+ * pflb_set_mechanism with that mechanism), without any CUDA call: PFLB_OK or
+ * the code create / set_mechanism would return, the reason in
+ * pflb_last_error(NULL). */
+int pflb_validate(const pflb_domain_desc* desc, const pflb_mechanism* mech);
 
 /* Static solid fraction phi_s in [0, 1] (N values, sum of phase fractions
  * is one, Sec. 2 eq. sum-varphialpha) and, when Ts_field, the initial solid
@@ -163,7 +187,9 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out);
 int pflb_set_phase_field(pflb_domain* d, const void* phi_s, const void* Ts, int dtype, int where);
 
 /* Species data and reactions; must precede pflb_set_fields when K > 0.
- * K must be one of the compiled species counts (0, 5, 6). */
+ * K must be one of the compiled species counts (0, 5, 6).  Returns
+ * PFLB_ERR_UNSTABLE when the inlet mixture breaks one of the stability limits
+ * listed under pflb_create_domain (gas and species diffusion numbers, tau). */
 int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m);
 
 /* Initial T (and Y when K > 0; optional velocity u, dim*N values, NULL = rest).
@@ -173,8 +199,11 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m);
 int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, int where);
 
 /* Advance nsteps time steps asynchronously on the domain's stream.  A NaN
- * or an instability latches PFLB_ERR_UNSTABLE in the device status word;
- * it is returned by the next synchronising call (get_fields/get_scalars). */
+ * or an instability latches PFLB_ERR_UNSTABLE in the device status word (a
+ * NaN in T, Y, the populations' sum or the velocity of any cell makes the
+ * step's FP64 reduction NaN); a bounded device wait that ran out latches
+ * PFLB_ERR_TIMEOUT.  The latched code is returned by the next synchronising
+ * call (get_fields / get_scalars); the fields are then not to be trusted. */
 int pflb_step(pflb_domain* d, int nsteps);
 
 /* Copy fields out, packed in the order T, Y, Ts, U, RHO, PH, G of the mask
@@ -218,6 +247,16 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
 /* Select the step kernel of a domain (after pflb_set_fields).  Returns
  * PFLB_ERR_UNSUPPORTED if the kernel cannot run this domain. */
 int pflb_select_kernel(pflb_domain* d, int kernel);
+
+/* Bound, in SM clock cycles, of the device-side waits of this domain's
+ * kernels (the TMA kernel's wait for each staged tile).  Default 2^31, about
+ * a second at 2 GHz; 0 makes each wait a single non-blocking probe.  A wait
+ * that runs out latches PFLB_ERR_TIMEOUT and the block stops working on
+ * tiles; before it exits it still waits (with the default bound) for the
+ * copies it has issued, so no copy lands in a finished block's shared
+ * memory.  A small bound is how the timeout path is exercised without a
+ * hung GPU.  Errors: PFLB_ERR_ARG (cycles < 0 or > 2^40). */
+int pflb_set_wait_limit(pflb_domain* d, long long cycles);
 
 /* Time every step kernel that can run this domain over `steps` steps each
  * and keep the fastest (the domain's state is restored afterwards, so the
@@ -333,17 +372,23 @@ int pflb_probe_fp64_fma(int device, double* tflops);
 
 /* One time step on caller-owned device arrays, allocating nothing.
  *
- * For callers that cannot allocate device memory: code that runs while
- * someone else captures a CUDA graph, plug-ins whose host framework owns all
- * device memory through its own pool, loops that forbid allocator calls after
- * start-up.  The paper has no counterpart; it is the same fused step as
- * pflb_step.  The caller owns and passes every state array (layout as in
- * pflb_get_fields, in the compute precision: double for PFLB_FP64, float for
- * PFLB_FP32): phi (N), g_in/g_out (Q*N), T_in/T_out (N), Y_in/Y_out (K*N, or
- * NULL when K = 0), Ts_in/Ts_out (N, or NULL unless desc->Ts_field).  `mech`
- * may be NULL for K = 0.  `scalars` (host) carries P0, P0_prev, mass, step
- * and status in, and returns the updated values (P0 of the next step, I,
- * fluxes) after the step; the call synchronises desc->stream.
+ * For callers that cannot allocate device memory: plug-ins whose host
+ * framework owns all device memory through its own pool, and loops that
+ * forbid allocator calls after start-up (cudaMalloc / cudaFree can
+ * synchronise the whole device and take unbounded time).  The paper has no
+ * counterpart; it is the same fused step as pflb_step.  The caller owns and
+ * passes every state array (layout as in pflb_get_fields, in the compute
+ * precision: double for PFLB_FP64, float for PFLB_FP32): phi (N),
+ * g_in/g_out (Q*N), T_in/T_out (N), Y_in/Y_out (K*N, or NULL when K = 0),
+ * Ts_in/Ts_out (N, or NULL unless desc->Ts_field).  `mech` may be NULL for
+ * K = 0.  `scalars` (host) carries P0 (> 0), P0_prev, mass, step and status
+ * in, and returns the updated values (P0 of the next step, I, fluxes) after
+ * the step; the call copies the scalars through host memory and
+ * synchronises desc->stream before it returns.
+ *
+ * The description and mechanism pass the same checks as pflb_create_domain
+ * and pflb_set_mechanism (PFLB_ERR_ARG, PFLB_ERR_UNSUPPORTED,
+ * PFLB_ERR_UNSTABLE); on any error pflb_last_error(NULL) names the reason.
  *
  * The reduction scratch (per-block partials, arrival counter, scalar block)
  * is a fixed device array inside the library, sized for at most

@@ -58,13 +58,14 @@ class OrcParams(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with plain IEEE double arithmetic (no contraction)."""
+    """Compile the oracle with plain IEEE double arithmetic (no contraction);
+    its independent per-cell loops run on OpenMP host threads."""
     with _lock:
         os.makedirs(os.path.dirname(LIB), exist_ok=True)
         if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
             tmp = LIB + f".{os.getpid()}.tmp"
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                                   "-shared", "-fPIC", SRC, "-o", tmp, "-lm"])
+                                   "-fopenmp", "-shared", "-fPIC", SRC, "-o", tmp, "-lm"])
             os.replace(tmp, LIB)
     return LIB
 
@@ -92,8 +93,16 @@ def lib():
         L.orc_moments.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_step.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_void_p]
         L.orc_run.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_int]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's per-cell loops (0: all cores); returns
+    the number in effect.  Results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _ptr(a):

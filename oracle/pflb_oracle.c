@@ -32,11 +32,20 @@
  * Layout: cell = x + nx*(y + ny*z); populations g[i*N + cell]; species
  * Y[k*N + cell]; velocity u[a*N + cell].
  *
+ * Host threads: within each phase of a step the per-cell updates are
+ * independent (every cell reads the previous phase's arrays and writes only
+ * its own entries), so those loops carry an OpenMP "parallel for".  No sum is
+ * split across threads: the global reductions (I, the boundary fluxes) stay
+ * serial in cell order, and the results do not depend on the thread count.
+ *
  * Parity pins: tests/test_oracle_pins.py (closed forms, invariants, brute force).
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_KMAX 8
 #define ORC_JMAX 4
@@ -475,6 +484,7 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
   double eta2 = p->eta * p->eta;
   double Cs = p->rhocp_s / p->rho_ref;
   double Lams = p->lambda_s * p->dt / (p->rho_ref * p->dx * p->dx);
+  #pragma omp parallel for schedule(static)
   for (int c = 0; c < N; ++c) {
     int xyz[3];
     coords(p, c, xyz);
@@ -616,6 +626,7 @@ static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, 
   int N = ncell(p), dim = p->dim;
   double eta2 = p->eta * p->eta;
   double rho_in = eos_rho(p, P0, mixture_Mw(p, p->Y_in), p->T_in);
+  #pragma omp parallel for schedule(static)
   for (int c = 0; c < N; ++c) {
     int xyz[3];
     coords(p, c, xyz);
@@ -666,6 +677,7 @@ int orc_init(const orc_params* p, const double* phi, double* g, const double* T,
              const double* u, const double* Ph, double P0, double* scal) {
   lat_t L = lattice_of(p->dim);
   int N = ncell(p);
+  #pragma omp parallel for schedule(static)
   for (int c = 0; c < N; ++c) {
     double Yc[ORC_KMAX], uc[3] = {0, 0, 0}, geq[ORC_QMAX];
     for (int k = 0; k < p->K; ++k) Yc[k] = Y[(size_t)k * N + c];
@@ -727,6 +739,7 @@ int orc_step(const orc_params* p, const double* phi, double* g, double* T, doubl
   orc_fd_phase(p, phi, T, Y, p->Ts_field ? Ts : NULL, u, P0, P0prev, Tn, Yn, Tsn);
 
   /* 4-5: divergence from the low-Mach constraint, source, collision */
+  #pragma omp parallel for schedule(static)
   for (int c = 0; c < N; ++c) {
     int xyz[3];
     coords(p, c, xyz);
@@ -806,3 +819,16 @@ int orc_run(const orc_params* p, const double* phi, double* g, double* T, double
 }
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* Host threads used by the per-cell loops (n <= 0: all cores); returns the
+ * number in effect (1 without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n <= 0) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return n;
+#else
+  (void)n;
+  return 1;
+#endif
+}

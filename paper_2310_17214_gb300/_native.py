@@ -37,7 +37,7 @@ class Desc(C.Structure):
         ("p0_mode", C.c_int), ("P0", C.c_double),
         ("Ts_field", C.c_int), ("Ts_uniform", C.c_double),
         ("rhocp_s", C.c_double), ("lambda_s", C.c_double), ("phi_min", C.c_double),
-        ("stream", C.c_void_p), ("device", C.c_int),
+        ("T_max", C.c_double), ("stream", C.c_void_p), ("device", C.c_int),
     ]
 
 
@@ -86,6 +86,7 @@ def lib():
         L = C.CDLL(path)
         vp = C.c_void_p
         L.pflb_create_domain.argtypes = [C.POINTER(Desc), C.POINTER(vp)]
+        L.pflb_validate.argtypes = [C.POINTER(Desc), C.POINTER(Mechanism)]
         L.pflb_set_phase_field.argtypes = [vp, vp, vp, C.c_int, C.c_int]
         L.pflb_set_mechanism.argtypes = [vp, C.POINTER(Mechanism)]
         L.pflb_set_fields.argtypes = [vp, C.c_uint, vp, C.c_int, C.c_int]
@@ -99,6 +100,7 @@ def lib():
         L.pflb_step_noalloc.argtypes = [C.POINTER(Desc), C.POINTER(Mechanism), vp, vp, vp,
                                         vp, vp, vp, vp, vp, vp, C.POINTER(Scalars)]
         L.pflb_select_kernel.argtypes = [vp, C.c_int]
+        L.pflb_set_wait_limit.argtypes = [vp, C.c_longlong]
         L.pflb_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), vp]
         L.pflb_destroy.argtypes = [vp]
         L.pflb_mlp_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
@@ -129,13 +131,17 @@ def lib():
 
 
 class PflbError(RuntimeError):
-    pass
+    """A failed library call; `code` is the PFLB_ERR_* status."""
+
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 def _check(rc, handle=None):
     if rc != 0:
         msg = lib().pflb_last_error(handle)
-        raise PflbError(f"pflb error {rc}: {msg.decode() if msg else ''}")
+        raise PflbError(f"pflb error {rc}: {msg.decode() if msg else ''}", rc)
 
 
 def make_desc(prob: dict, precision: str = "fp64", stream: int = 0, device: int = 0) -> Desc:
@@ -165,6 +171,7 @@ def make_desc(prob: dict, precision: str = "fp64", stream: int = 0, device: int 
     d.Ts_uniform = prob.get("Ts_uniform", 300.0)
     d.rhocp_s, d.lambda_s = prob.get("rhocp_s", 1.0), prob.get("lambda_s", 0.0)
     d.phi_min = prob.get("phi_min", 1e-6)
+    d.T_max = prob.get("T_max", 0.0)
     d.stream = stream
     d.device = device
     return d
@@ -193,6 +200,16 @@ def make_mechanism(prob: dict) -> Mechanism:
                 m.rorder[j][k] = r["reverse"]["order"][k]
     m.p_ref = prob.get("p_ref", 101325.0)
     return m
+
+
+def validate(prob: dict, precision: str = "fp64"):
+    """(status, message) of the description and mechanism checks that
+    pflb_create_domain and pflb_set_mechanism make; no CUDA call."""
+    d = make_desc(prob, precision)
+    m = make_mechanism(prob) if prob.get("K", 0) else None
+    rc = lib().pflb_validate(C.byref(d), C.byref(m) if m is not None else None)
+    msg = lib().pflb_last_error(None)
+    return rc, (msg.decode() if msg else "")
 
 
 def lattice(dim):
@@ -300,6 +317,10 @@ class Domain:
     def select_kernel(self, name: str):
         _check(lib().pflb_select_kernel(self._h, self.KERNELS[name]), self._h)
 
+    def set_wait_limit(self, cycles: int):
+        """Bound of the device-side waits in SM clock cycles (0: one probe)."""
+        _check(lib().pflb_set_wait_limit(self._h, int(cycles)), self._h)
+
     def autotune(self, steps: int = 20):
         """Time each step kernel (state restored afterwards), keep the fastest.
         Returns (chosen name, {name: us per step or None})."""
@@ -373,9 +394,10 @@ class Domain:
 def step_noalloc(prob, precision, arrays, scalars, stream=0, device=0):
     """One step through pflb_step_noalloc on caller-owned CUDA tensors.
 
-    For callers that cannot allocate device memory (graph capture owned by
-    someone else, host frameworks with their own memory pool): the library
-    allocates nothing here; its reduction scratch is a fixed device array.
+    For callers that cannot allocate device memory (host frameworks that own
+    all device memory through their own pool, loops that forbid allocator
+    calls after start-up): the library allocates nothing here; its reduction
+    scratch is a fixed device array.
     `arrays` maps phi, g_in, g_out, T_in, T_out, Y_in, Y_out, Ts_in, Ts_out to
     contiguous CUDA tensors in the compute precision (Y/Ts may be absent);
     `scalars` is a dict with P0, P0_prev, mass, step, status and is returned
@@ -392,7 +414,8 @@ def step_noalloc(prob, precision, arrays, scalars, stream=0, device=0):
                                  ptr("T_out"), ptr("Y_in"), ptr("Y_out"), ptr("Ts_in"),
                                  ptr("Ts_out"), C.byref(sc))
     if rc != 0:
-        raise PflbError(f"pflb_step_noalloc error {rc}")
+        msg = lib().pflb_last_error(None)
+        raise PflbError(f"pflb_step_noalloc error {rc}: {msg.decode() if msg else ''}", rc)
     return {f: getattr(sc, f) for f, _ in Scalars._fields_}
 
 

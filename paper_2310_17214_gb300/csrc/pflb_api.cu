@@ -14,6 +14,7 @@
 
 #include "../../include/pflb.h"
 #include "pflb_launch.cuh"
+#include "pflb_validate.cuh"
 
 using namespace pflb;
 
@@ -27,6 +28,7 @@ struct pflb_domain {
   int cur = 0;
   bool has_mech = false, has_phase = false, has_fields = false;
   Launcher* L = nullptr;
+  long long wait_limit = kDefaultWaitCycles;
   std::string err;
 };
 
@@ -134,6 +136,143 @@ void free_buffers(pflb_domain* d) {
 
 }  // namespace
 
+namespace pflb {
+
+void set_global_error(const std::string& msg) { g_create_err = msg; }
+
+const char* status_message(int status) {
+  switch (status) {
+    case PFLB_ERR_UNSTABLE: return "instability (NaN or non-positive temperature sum)";
+    case PFLB_ERR_TIMEOUT: return "a bounded device wait ran out";
+    case PFLB_ERR_UNSUPPORTED: return "a kernel's self-check failed (shared-memory alignment)";
+    default: return "device status set";
+  }
+}
+
+int validate_desc(const pflb_domain_desc& D, std::string& msg) {
+  auto bad = [&](int code, const char* why) { msg = why; return code; };
+  if (D.dim != 2 && D.dim != 3) return bad(PFLB_ERR_UNSUPPORTED, "dim must be 2 or 3");
+  if (D.nx < 2 || D.ny < 1 || (D.dim == 3 && D.nz < 1)) return bad(PFLB_ERR_ARG, "bad lattice extent");
+  const long long N = (long long)D.nx * D.ny * (D.dim == 3 ? D.nz : 1);
+  if (N > (1LL << 31) / 32) return bad(PFLB_ERR_ARG, "lattice too large for int indexing");
+  if (D.precision < PFLB_FP64 || D.precision > PFLB_FP32_FP16STORE)
+    return bad(PFLB_ERR_ARG, "bad precision");
+  for (int a = 0; a < D.dim; ++a) {
+    const int lo = D.bc[2 * a], hi = D.bc[2 * a + 1];
+    if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return bad(PFLB_ERR_ARG, "bad bc kind");
+    if ((lo == PFLB_BC_PERIODIC) != (hi == PFLB_BC_PERIODIC))
+      return bad(PFLB_ERR_ARG, "periodic faces must come in pairs");
+    if ((lo == PFLB_BC_INLET && a != 0) || (hi == PFLB_BC_OUTLET && a != 0) ||
+        lo == PFLB_BC_OUTLET || hi == PFLB_BC_INLET)
+      return bad(PFLB_ERR_ARG, "inlet only at x-lo, outlet only at x-hi");
+  }
+  const double pos[] = {D.dx, D.dt, D.rho_ref, D.Pr, D.eta, D.P0, D.mu_ref};
+  for (double v : pos)
+    if (!(v > 0 && std::isfinite(v)))
+      return bad(PFLB_ERR_ARG, "dx, dt, rho_ref, Pr, eta, P0, mu_ref must be positive and finite");
+  if (D.sutherland && !(D.suth_T > 0 && D.suth_S >= 0))
+    return bad(PFLB_ERR_ARG, "Sutherland constants must be positive");
+  if (!(D.T_in > 0) || !(D.Ts_uniform > 0)) return bad(PFLB_ERR_ARG, "T_in, Ts_uniform must be > 0");
+  if (!(D.M0 > 0 && D.cp0 > 0)) return bad(PFLB_ERR_ARG, "M0, cp0 must be > 0");
+  if (D.p0_mode != PFLB_P0_FIXED && D.p0_mode != PFLB_P0_CLOSED) return bad(PFLB_ERR_ARG, "bad p0_mode");
+  if (D.Ts_field && !(D.rhocp_s > 0)) return bad(PFLB_ERR_ARG, "rhocp_s must be > 0");
+  if (!(D.A_u >= 0 && D.A_T >= 0 && D.lambda_s >= 0 && D.phi_min >= 0 && D.T_max >= 0))
+    return bad(PFLB_ERR_ARG, "A_u, A_T, lambda_s, phi_min, T_max must be >= 0");
+  return PFLB_OK;
+}
+
+int validate_mech(const pflb_mechanism& m, std::string& msg) {
+  auto bad = [&](int code, const char* why) { msg = why; return code; };
+  if (m.K != 0 && m.K != 5 && m.K != 6) return bad(PFLB_ERR_UNSUPPORTED, "species count must be 0, 5 or 6");
+  if (m.J < 0 || m.J > PFLB_JMAX) return bad(PFLB_ERR_ARG, "bad reaction count");
+  if (m.chem_mode != PFLB_CHEM_NONE && m.chem_mode != PFLB_CHEM_EXPLICIT &&
+      m.chem_mode != PFLB_CHEM_IMPLICIT && m.chem_mode != PFLB_CHEM_SURROGATE)
+    return bad(PFLB_ERR_UNSUPPORTED, "chem_mode");
+  if (m.chem_mode == PFLB_CHEM_SURROGATE && m.K != 6)
+    return bad(PFLB_ERR_UNSUPPORTED, "the surrogate needs the six-species mechanism");
+  for (int j = 0; j < m.J; ++j)
+    if (m.rev[j] && !(m.p_ref > 0)) return bad(PFLB_ERR_ARG, "p_ref must be > 0");
+  for (int k = 0; k < m.K; ++k)
+    if (!(m.M[k] > 0 && m.cp[k] > 0 && m.Dref[k] >= 0))
+      return bad(PFLB_ERR_ARG, "species data must be positive");
+  if (m.K > 0 && m.D_exp != 0.0 && !(m.D_Tref > 0)) return bad(PFLB_ERR_ARG, "D_Tref must be > 0");
+  return PFLB_OK;
+}
+
+int check_stability(const pflb_domain_desc& D, const pflb_mechanism* m, std::string& msg) {
+  const bool mix = m && m->K > 0;
+  double invMw = 1.0 / D.M0;
+  if (mix) {
+    invMw = 0.0;
+    for (int k = 0; k < m->K; ++k) invMw += m->Y_in[k] / m->M[k];
+    if (!(invMw > 0)) { msg = "inlet composition has no mass"; return PFLB_ERR_ARG; }
+  }
+  const double h2 = D.dt / (D.dx * D.dx);
+  const double lim = 1.0 / (2.0 * D.dim);
+  double temps[9];
+  int nt = 0;
+  temps[nt++] = D.T_in;
+  temps[nt++] = D.Ts_uniform;
+  if (D.T_max > 0) temps[nt++] = D.T_max;
+  for (int f = 0; f < 2 * D.dim; ++f)
+    if (D.bc[f] == PFLB_BC_WALL && D.wall_T[f] > 0) temps[nt++] = D.wall_T[f];
+  char buf[256];
+  for (int i = 0; i < nt; ++i) {
+    const double T = temps[i];
+    double mu = D.mu_ref;
+    if (D.sutherland) mu *= std::pow(T / D.suth_T, 1.5) * (D.suth_T + D.suth_S) / (T + D.suth_S);
+    const double mu_lat = mu * h2 / D.rho_ref;
+    const double rho_lat = D.P0 / (8.314 * T * invMw * D.rho_ref);
+    const double tau = 0.5 + 3.0 * mu_lat / rho_lat;  // tau = 1/2 + nu / cs^2
+    const double a = mu_lat / (rho_lat * D.Pr);       // lambda / (rho cp), lattice units
+    if (!(tau > 0.5) || !std::isfinite(tau)) {
+      std::snprintf(buf, sizeof(buf), "relaxation time tau = %.6g <= 1/2 at T = %g K", tau, T);
+      msg = buf;
+      return PFLB_ERR_UNSTABLE;
+    }
+    if (!(a <= lim)) {
+      std::snprintf(buf, sizeof(buf),
+                    "thermal diffusion number %.4g above %.4g at T = %g K (reduce dt)", a, lim, T);
+      msg = buf;
+      return PFLB_ERR_UNSTABLE;
+    }
+    if (!(D.A_T * a / (D.eta * D.eta) <= 1.0)) {
+      std::snprintf(buf, sizeof(buf), "interface exchange number A_T a / eta^2 = %.4g above 1 at T = %g K",
+                    D.A_T * a / (D.eta * D.eta), T);
+      msg = buf;
+      return PFLB_ERR_UNSTABLE;
+    }
+    if (mix) {
+      for (int k = 0; k < m->K; ++k) {
+        double Dk = m->Dref[k] * h2;
+        if (m->D_exp != 0.0) Dk *= std::pow(T / m->D_Tref, m->D_exp);
+        if (!(Dk <= lim)) {
+          std::snprintf(buf, sizeof(buf),
+                        "species %d diffusion number %.4g above %.4g at T = %g K (reduce dt)", k,
+                        Dk, lim, T);
+          msg = buf;
+          return PFLB_ERR_UNSTABLE;
+        }
+      }
+    }
+  }
+  if (D.Ts_field) {
+    const double as = D.lambda_s * D.dt / (D.rhocp_s * D.dx * D.dx);
+    if (!(as <= lim)) {
+      std::snprintf(buf, sizeof(buf), "solid diffusion number %.4g above %.4g", as, lim);
+      msg = buf;
+      return PFLB_ERR_UNSTABLE;
+    }
+  }
+  if (!(std::fabs(D.u_in) < std::sqrt(1.0 / 3.0))) {
+    msg = "inlet speed at or above the lattice sound speed";
+    return PFLB_ERR_UNSTABLE;
+  }
+  return PFLB_OK;
+}
+
+}  // namespace pflb
+
 extern "C" {
 
 int pflb_lattice(int dim, int* c_out, double* w_out) {
@@ -158,33 +297,27 @@ const char* pflb_last_error(const pflb_domain* d) {
   return d ? d->err.c_str() : g_create_err.c_str();
 }
 
+int pflb_validate(const pflb_domain_desc* desc, const pflb_mechanism* mech) {
+  if (!desc) return fail(nullptr, PFLB_ERR_ARG, "desc is NULL");
+  std::string why;
+  int rc = validate_desc(*desc, why);
+  if (rc == PFLB_OK && mech) rc = validate_mech(*mech, why);
+  if (rc == PFLB_OK) rc = check_stability(*desc, mech, why);
+  if (rc != PFLB_OK) return fail(nullptr, rc, "%s", why.c_str());
+  g_create_err.clear();
+  return PFLB_OK;
+}
+
 int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   if (!out) return fail(nullptr, PFLB_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!desc) return fail(nullptr, PFLB_ERR_ARG, "desc is NULL");
   const pflb_domain_desc& D = *desc;
-  if (D.dim != 2 && D.dim != 3) return fail(nullptr, PFLB_ERR_UNSUPPORTED, "dim must be 2 or 3");
-  if (D.nx < 2 || D.ny < 1 || (D.dim == 3 && D.nz < 1))
-    return fail(nullptr, PFLB_ERR_ARG, "bad lattice extent");
+  std::string why;
+  int rc = validate_desc(D, why);
+  if (rc == PFLB_OK) rc = check_stability(D, nullptr, why);
+  if (rc != PFLB_OK) return fail(nullptr, rc, "%s", why.c_str());
   const long long N = (long long)D.nx * D.ny * (D.dim == 3 ? D.nz : 1);
-  if (N > (1LL << 31) / 32) return fail(nullptr, PFLB_ERR_ARG, "lattice too large for int indexing");
-  if (D.precision < PFLB_FP64 || D.precision > PFLB_FP32_FP16STORE)
-    return fail(nullptr, PFLB_ERR_ARG, "bad precision");
-  for (int a = 0; a < D.dim; ++a) {
-    int lo = D.bc[2 * a], hi = D.bc[2 * a + 1];
-    if ((lo == PFLB_BC_PERIODIC) != (hi == PFLB_BC_PERIODIC))
-      return fail(nullptr, PFLB_ERR_ARG, "periodic faces must come in pairs");
-    if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return fail(nullptr, PFLB_ERR_ARG, "bad bc kind");
-    if ((lo == PFLB_BC_INLET && a != 0) || (hi == PFLB_BC_OUTLET && a != 0) ||
-        lo == PFLB_BC_OUTLET || hi == PFLB_BC_INLET)
-      return fail(nullptr, PFLB_ERR_ARG, "inlet only at x-lo, outlet only at x-hi");
-  }
-  if (!(D.dx > 0 && D.dt > 0 && D.rho_ref > 0 && D.Pr > 0 && D.eta > 0 && D.P0 > 0 &&
-        D.mu_ref > 0))
-    return fail(nullptr, PFLB_ERR_ARG, "dx, dt, rho_ref, Pr, eta, P0, mu_ref must be positive");
-  if (D.p0_mode != PFLB_P0_FIXED && D.p0_mode != PFLB_P0_CLOSED)
-    return fail(nullptr, PFLB_ERR_ARG, "bad p0_mode");
-  if (D.Ts_field && !(D.rhocp_s > 0)) return fail(nullptr, PFLB_ERR_ARG, "rhocp_s must be > 0");
 
   pflb_domain* d = new (std::nothrow) pflb_domain();
   if (!d) return fail(nullptr, PFLB_ERR_OOM, "host allocation failed");
@@ -243,19 +376,12 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
 
 int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
   if (!d || !m) return fail(d, PFLB_ERR_ARG, "NULL argument");
-  if (m->K != 0 && m->K != 5 && m->K != 6)
-    return fail(d, PFLB_ERR_UNSUPPORTED, "species count must be 0, 5 or 6");
-  if (m->J < 0 || m->J > PFLB_JMAX) return fail(d, PFLB_ERR_ARG, "bad reaction count");
-  if (m->chem_mode != PFLB_CHEM_NONE && m->chem_mode != PFLB_CHEM_EXPLICIT &&
-      m->chem_mode != PFLB_CHEM_IMPLICIT && m->chem_mode != PFLB_CHEM_SURROGATE)
-    return fail(d, PFLB_ERR_UNSUPPORTED, "chem_mode");
-  if (m->chem_mode == PFLB_CHEM_SURROGATE && m->K != 6)
-    return fail(d, PFLB_ERR_UNSUPPORTED, "the surrogate needs the six-species mechanism");
-  for (int j = 0; j < m->J; ++j)
-    if (m->rev[j] && !(m->p_ref > 0)) return fail(d, PFLB_ERR_ARG, "p_ref must be > 0");
-  for (int k = 0; k < m->K; ++k)
-    if (!(m->M[k] > 0 && m->cp[k] > 0 && m->Dref[k] >= 0))
-      return fail(d, PFLB_ERR_ARG, "species data must be positive");
+  {
+    std::string why;
+    int rc = validate_mech(*m, why);
+    if (rc == PFLB_OK) rc = check_stability(d->desc, m, why);
+    if (rc != PFLB_OK) return fail(d, rc, "%s", why.c_str());
+  }
   if (d->has_fields) return fail(d, PFLB_ERR_STATE, "set_mechanism must precede set_fields");
   cudaSetDevice(d->desc.device);
   const size_t n = (size_t)d->N;
@@ -339,6 +465,7 @@ int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, i
   delete d->L;
   d->L = make_launcher(d);
   if (!d->L) return fail(d, PFLB_ERR_UNSUPPORTED, "no kernel compiled for this combination");
+  d->L->set_wait_limit(d->wait_limit);
   d->B.pending = 0;
   cudaError_t e = d->L->init(d->B, d->cur, u, d->desc.P0, d->stream);
   if (u) cudaFreeAsync(u, d->stream);
@@ -371,7 +498,7 @@ int pflb_get_scalars(pflb_domain* d, pflb_scalars* out) {
   out->flux_out = h.flux_out;
   out->step = h.step;
   out->status = h.status;
-  if (h.status != 0) return fail(d, h.status, "instability (NaN or non-positive temperature sum)");
+  if (h.status != 0) return fail(d, h.status, "%s", status_message(h.status));
   return PFLB_OK;
 }
 
@@ -460,7 +587,7 @@ int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int 
   CK(d, cudaStreamSynchronize(d->stream));
   DevScalars h;
   CK(d, cudaMemcpy(&h, d->B.scal, sizeof(h), cudaMemcpyDeviceToHost));
-  if (h.status != 0) return fail(d, h.status, "instability (NaN or non-positive temperature sum)");
+  if (h.status != 0) return fail(d, h.status, "%s", status_message(h.status));
   return PFLB_OK;
 }
 
@@ -557,6 +684,14 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
     CK(d, cudaMemcpyAsync(p, in + off, b, k, d->stream));
     return PFLB_OK;
   });
+}
+
+int pflb_set_wait_limit(pflb_domain* d, long long cycles) {
+  if (!d) return fail(d, PFLB_ERR_ARG, "NULL domain");
+  if (cycles < 0 || cycles > (1LL << 40)) return fail(d, PFLB_ERR_ARG, "cycles out of range");
+  d->wait_limit = cycles;
+  if (d->L) d->L->set_wait_limit(cycles);
+  return PFLB_OK;
 }
 
 int pflb_select_kernel(pflb_domain* d, int kernel) {

@@ -1,0 +1,45 @@
+// pflb_chem_impl.cuh -- definition of chem_pass_launch (see pflb_chem.cuh);
+// included by the two translation units that instantiate it.
+#pragma once
+
+#include <algorithm>
+
+#include "pflb_chem.cuh"
+
+namespace pflb {
+
+template <int K, class Real>
+cudaError_t chem_pass_launch(const Params<Real, K>& P, const State<Real, Real>& S, Real* src,
+                             const SurrArgs* surr, int* fb_idx, unsigned* fb_count,
+                             double* stats, double* out, cudaStream_t st) {
+  const int blocks = (P.N + BLOCK - 1) / BLOCK;
+  if (P.chem == 2) {
+    chem_implicit_kernel<K, Real, Real><<<blocks, BLOCK, 0, st>>>(P, S, src);
+  } else if (P.chem == 3) {
+    if constexpr (K == 6) {
+      if (!surr || !fb_idx) return cudaErrorInvalidValue;
+      SurrArgs a = *surr;
+      a.fb_idx = fb_idx;
+      a.fb_count = fb_count;
+      a.stats = stats;
+      cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(unsigned), st);
+      if (e != cudaSuccess) return e;
+      // persistent grid: each block loads the network once
+      const int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, 152 * 4);
+      chem_surrogate_kernel<K, Real, Real><<<nb, 256, 0, st>>>(P, S, src, a);
+      const int fb_blocks = (int)std::min<long long>(
+          ((long long)P.N + FALLBACK_BLOCK - 1) / FALLBACK_BLOCK, 152 * 16);
+      chem_fallback_kernel<K, Real, Real><<<fb_blocks, FALLBACK_BLOCK, 0, st>>>(P, S, src,
+                                                                                fb_idx, fb_count);
+    } else {
+      return cudaErrorNotSupported;
+    }
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  if (out)
+    src_to_increments_kernel<K, Real, Real><<<blocks, BLOCK, 0, st>>>(P, S, src, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pflb

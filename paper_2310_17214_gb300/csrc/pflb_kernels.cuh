@@ -30,6 +30,8 @@ namespace pflb {
 constexpr int KMAX = 8;
 constexpr int JMAX = 4;
 constexpr int BLOCK = 256;  // threads per block (one cell each per plane)
+// default bound of a device-side wait: 2^31 SM clock cycles, about a second
+constexpr long long kDefaultWaitCycles = 1LL << 31;
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTLET = 3 };
 enum { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP16 = 2 };
@@ -445,16 +447,21 @@ __device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
   for (int k = 0; k < K; ++k) y0[k] = Y0[k];
   y0[K] = T0;
   int ok = -1;
+  // the sub-step and Newton loops stay rolled: unrolled, they multiply the
+  // fully unrolled Jacobian and elimination by up to 7 x 30 copies
+#pragma unroll 1
   for (int nsub = 1; nsub <= 64 && ok != 0; nsub *= 2) {
 #pragma unroll
     for (int m = 0; m < n; ++m) zs[m] = y0[m];
     ok = 0;
     const double h = c.dt / nsub, hr = h * inv_rho;
+#pragma unroll 1
     for (int sub = 0; sub < nsub && ok == 0; ++sub) {
 #pragma unroll
       for (int m = 0; m < n; ++m) z[m] = zs[m];
       const double inv_Ts = 1.0 / zs[K];  // temperature scale of the update test
       ok = -1;
+#pragma unroll 1
       for (int it = 0; it < 30; ++it) {
         double w[K + 1], dw[K + 1][K + 1];
         rates_jacobian64<K>(c, z, rho, w, dw);
@@ -1104,7 +1111,9 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const Real fx = phif * rho * u[0];
   fin = (xyz[0] == 0 && P.bc[0] == BC_INLET) ? fx : Real(0);
   fout = outlet_cell ? fx : Real(0);
-  return phif * fdiv(Real(1), Tn * mixture_invMw(P, Yn));
+  // 0 * P_h is NaN when any pulled population is: a NaN confined to the
+  // populations reaches the FP64 reduction (and the status word) this step
+  return phif * fdiv(Real(1), Tn * mixture_invMw(P, Yn)) + Real(0) * Ph;
 }
 
 // Resident blocks per SM requested from the register allocator (measured on

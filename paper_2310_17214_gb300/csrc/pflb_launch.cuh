@@ -13,6 +13,7 @@
 
 #include "../../include/pflb.h"
 #include "pflb_batch.cuh"
+#include "pflb_chem.cuh"
 #include "pflb_kernels.cuh"
 #include "pflb_surrogate.cuh"
 #include "pflb_tma.cuh"
@@ -112,6 +113,8 @@ struct Launcher {
                                    cudaStream_t st) const = 0;
   // domains can share a batch when their keys are equal (same kernel)
   virtual int batch_key() const = 0;
+  // bound of the kernels' device waits (SM clock cycles)
+  virtual void set_wait_limit(long long cycles) = 0;
 };
 
 constexpr double R_GAS = 8.314;  // J/(mol K), value printed in Sec. 3.1
@@ -282,6 +285,8 @@ struct LauncherImpl final : Launcher {
   int tma_state = 0;  // 0 unknown, 1 usable, -1 not usable
   int tma_grid = 0;
   int kernel_sel = 0;
+  long long wait_limit = kDefaultWaitCycles;
+  void set_wait_limit(long long cycles) override { wait_limit = cycles; }
   SurrArgs surr;
   bool has_surr = false;
 
@@ -300,35 +305,17 @@ struct LauncherImpl final : Launcher {
       return cudaErrorNotSupported;
     } else {
       if (!B.src) return cudaErrorInvalidValue;
-      if (P.chem == 2) {
-        chem_implicit_kernel<K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
-            P, state(B, cur), static_cast<Real*>(B.src));
-      } else if (P.chem == 3) {
-        if constexpr (K == 6) {
-          if (!has_surr || !B.fb_idx) return cudaErrorInvalidValue;
-          SurrArgs a = surr;
-          a.fb_idx = B.fb_idx;
-          a.fb_count = B.fb_count;
-          a.stats = B.chem_stats;
-          cudaMemsetAsync(B.fb_count, 0, sizeof(unsigned), st);
-          // persistent grid: each block loads the network once
-          int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, 152 * 4);
-          chem_surrogate_kernel<K, Real, Store><<<nb, 256, 0, st>>>(
-              P, state(B, cur), static_cast<Real*>(B.src), a);
-          const int fb_blocks = (int)std::min<long long>(
-              ((long long)P.N + FALLBACK_BLOCK - 1) / FALLBACK_BLOCK, 152 * 16);
-          chem_fallback_kernel<K, Real, Store><<<fb_blocks, FALLBACK_BLOCK, 0, st>>>(
-              P, state(B, cur), static_cast<Real*>(B.src), B.fb_idx, B.fb_count);
-        } else {
-          return cudaErrorNotSupported;
-        }
-      } else {
-        return cudaErrorInvalidValue;
-      }
-      if (out)
-        src_to_increments_kernel<K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
-            P, state(B, cur), static_cast<const Real*>(B.src), out);
-      return cudaGetLastError();
+      // the chemistry reads T, Y, phi and P0 only: one instantiation per
+      // (K, compute type), shared by 2-D and 3-D and by both storage types
+      const State<Real, Store> S = state(B, cur);
+      State<Real, Real> C;
+      std::memset(&C, 0, sizeof(C));
+      C.T_in = S.T_in;
+      C.Y_in = S.Y_in;
+      C.phi = S.phi;
+      C.scal = S.scal;
+      return chem_pass_launch<K, Real>(P, C, static_cast<Real*>(B.src), has_surr ? &surr : nullptr,
+                                       B.fb_idx, B.fb_count, B.chem_stats, out, st);
     }
   }
 
@@ -501,7 +488,7 @@ struct LauncherImpl final : Launcher {
       const TmaMaps& m = maps[cur];
       step_tma_kernel<K, Store><<<tma_grid, BLOCK, LY::smem_bytes, st>>>(
           P, state(B, cur), p0_closed, prev, (unsigned)B.last_nb, m.T, m.phi, m.Ts, m.Y, m.g,
-          tiles_x, n_tiles);
+          tiles_x, n_tiles, wait_limit);
       B.last_nb = tma_grid;
       return cudaGetLastError();
     } else {

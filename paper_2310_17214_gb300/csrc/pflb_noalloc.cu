@@ -1,21 +1,24 @@
 // pflb_noalloc.cu -- pflb_step_noalloc: one time step on caller-owned device
 // arrays without any device allocation.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph that is being captured by someone else, plug-ins living under a host
-// framework that owns every device allocation through its own pool, or
-// real-time loops that forbid allocator calls after start-up.  They own the
-// state arrays and pass them in; the only memory this entry point needs
+// Some callers cannot call cudaMalloc at all: plug-ins living under a host
+// framework that owns every device allocation through its own pool, or loops
+// that forbid allocator calls after start-up (an allocation or free can
+// synchronise the device and take unbounded time).  They own the state
+// arrays and pass them in; the only memory this entry point needs
 // besides them -- the per-block partial sums of the P0 reduction, the
 // arrival counter of the finishing block and the scalar block -- lives in the
 // fixed file-scope device array below, sized for at most
 // PFLB_NOALLOC_MAX_CELLS cells.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
+#include <string>
 
 #include "../../include/pflb.h"
 #include "pflb_launch.cuh"
+#include "pflb_validate.cuh"
 
 using namespace pflb;
 
@@ -33,8 +36,11 @@ static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 void* scratch_ptr[kMaxDevices] = {nullptr};
 
-// status code only: this entry point keeps no per-call message state
-int err(int code, const char*) { return code; }
+// the reason goes where pflb_last_error(NULL) reads it (this host thread)
+int err(int code, const std::string& msg) {
+  set_global_error(msg);
+  return code;
+}
 
 }  // namespace
 
@@ -46,6 +52,13 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
     return err(PFLB_ERR_ARG, "NULL argument");
   const pflb_domain_desc& D = *desc;
   const int K = mech ? mech->K : 0;
+  {
+    std::string why;
+    int rc = validate_desc(D, why);
+    if (rc == PFLB_OK && mech) rc = validate_mech(*mech, why);
+    if (rc == PFLB_OK) rc = check_stability(D, mech, why);
+    if (rc != PFLB_OK) return err(rc, why);
+  }
   if (D.dim != 2) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports D2Q9 only");
   if (K != 0 && K != 5) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports K = 0 or 5");
   if (D.precision != PFLB_FP64 && D.precision != PFLB_FP32)
@@ -54,7 +67,8 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
   if (mech && mech->chem_mode > PFLB_CHEM_EXPLICIT)
     return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports explicit chemistry only");
   if (D.Ts_field && (!Ts_in || !Ts_out)) return err(PFLB_ERR_ARG, "Ts arrays are required");
-  if (D.nx < 2 || D.ny < 1) return err(PFLB_ERR_ARG, "bad lattice extent");
+  if (!(scalars->P0 > 0) || !std::isfinite(scalars->P0) || !std::isfinite(scalars->P0_prev))
+    return err(PFLB_ERR_ARG, "scalars->P0 must be positive and P0, P0_prev finite");
   const long long N = (long long)D.nx * D.ny;
   if (N > PFLB_NOALLOC_MAX_CELLS)
     return err(PFLB_ERR_ARG, "lattice larger than PFLB_NOALLOC_MAX_CELLS cells");
@@ -140,6 +154,6 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
   scalars->flux_out = h.flux_out;
   scalars->step = h.step;
   scalars->status = h.status;
-  if (h.status != 0) return err(PFLB_ERR_UNSTABLE, "instability (NaN or non-positive sum)");
+  if (h.status != 0) return err(h.status, status_message(h.status));
   return PFLB_OK;
 }

@@ -14,8 +14,10 @@
 // crosses the domain edge is zero-filled and still counts in full).  Cells on
 // the domain edge use the boundary rules of the global-memory pull, and the
 // staged halo of edge tiles is overwritten with the ghost / periodic values.
-// Waits are bounded: a wait that runs out latches PFLB_ERR_TIMEOUT in the
-// status word, waits (bounded) once more for the copies in flight and exits.
+// Waits are bounded (pflb_set_wait_limit): a wait that runs out latches
+// PFLB_ERR_TIMEOUT in the status word, waits (with the default bound) for the
+// copies the block has in flight, and stops working on tiles; the block still
+// publishes its partial sums so that the step's reduction completes.
 #pragma once
 
 #include <cuda.h>
@@ -47,11 +49,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait (about a second of SM clock): false when it ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait of at most `limit` SM clock cycles (a limit of 0 is one
+// non-blocking probe): false when it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  long long limit = kDefaultWaitCycles) {
+  if (limit <= 0) return mbar_test_wait(bar, parity);
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > (2LL << 30)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void fence_proxy_async() {
@@ -267,7 +282,8 @@ step_tma_kernel(const Params<float, K> P, const State<float, Store> S, int p0_cl
                 const double* __restrict__ prev_partials, unsigned prev_nb,
                 const __grid_constant__ CUtensorMap mT, const __grid_constant__ CUtensorMap mPhi,
                 const __grid_constant__ CUtensorMap mTs, const __grid_constant__ CUtensorMap mY,
-                const __grid_constant__ CUtensorMap mG, int tiles_x, int n_tiles) {
+                const __grid_constant__ CUtensorMap mG, int tiles_x, int n_tiles,
+                long long wait_limit) {
   const TmaMapRefs M{&mT, &mPhi, &mTs, &mY, &mG};
   using LY = TmaLayout<K, Store>;
   // All shared memory of this kernel is the dynamic buffer, its base rounded up
@@ -324,17 +340,18 @@ step_tma_kernel(const Params<float, K> P, const State<float, Store> S, int p0_cl
         issue_tile<K, Store>(M, P, stage[s ^ 1], &bar[s ^ 1], (tn % tiles_x) * LY::TX,
                              (tn / tiles_x) * LY::TY);
       }
-      s_ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!s_ok) {
-      // latch the timeout, give the copy in flight (if any) a bounded wait, exit
-      if (threadIdx.x == 0) {
+      s_ok = mbar_wait_bounded(&bar[s], (it >> 1) & 1, wait_limit) ? 1 : 0;
+      if (!s_ok) {
+        // latch the timeout; then drain: every copy this block issued (the
+        // current tile's and the next one's) completes before the block
+        // leaves the loop, so none lands in a finished block's shared memory
         atomicExch(&S.scal->status, -6);
+        mbar_wait_bounded(&bar[s], (it >> 1) & 1);
         if (tn < n_tiles) mbar_wait_bounded(&bar[s ^ 1], ((it + 1) >> 1) & 1);
       }
-      return;
     }
+    __syncthreads();
+    if (!s_ok) break;  // uniform: the block still publishes its (partial) sums
     float* raw = reinterpret_cast<float*>(stage[s]);
     const bool edge_tile = x0 == 0 || y0 == 0 || x0 + LY::TX >= P.nx || y0 + LY::TY >= P.ny;
     if (edge_tile) {

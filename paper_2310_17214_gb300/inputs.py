@@ -405,6 +405,9 @@ def config2(nx=1024, ny=256, precision="fp64", steps=20000, seed=2):
               "precision": precision, "steps": steps, "seed": seed,
               "ignite": [16, 64, 1500.0], "bed": {"count": 40, "amin": 8, "amax": 20,
                                                  "porosity": 0.6, "x0": 96},
+              # hottest temperature for the create-time stability check: above
+              # the adiabatic flame temperature of the inlet mixture (1822 K)
+              "T_max": 1900.0,
               "name": f"cfg2_reactive_bed_{nx}x{ny}_d2q9_{precision}"})
     return p
 
@@ -507,6 +510,21 @@ def config3(nx=256, ny=128, nz=128, precision="fp32_fp16", steps=2000, seed=3):
     p["bed"] = {"count": 150, "amin": 6, "amax": 16, "porosity": 0.5, "x0": 52}
     p["ignite"] = [8, 44, 1500.0]
     p["name"] = f"cfg3_reactive_bed_{nx}x{ny}x{nz}_d3q19_{precision}"
+    return p
+
+
+def config3_crop(n=64, precision="fp32_fp16", seed=3):
+    """The 3-D bed recipe on an n^3 lattice, for comparisons with the oracle:
+    same physics, mechanism, time step and inlet, the particle count scaled
+    with the volume (150 ellipsoids in 256 x 128 x 128 -> about 10 in 64^3),
+    semi-axes 6-16 cells, the bed from x = 3n/8 and an ignition slab over
+    [n/8, 5n/8) at 1500 K."""
+    p = config3(nx=n, ny=n, nz=n, precision=precision, seed=seed)
+    vol = n ** 3 / (256 * 128 * 128)
+    p["bed"] = {"count": max(1, int(round(150 * vol))), "amin": 6, "amax": 16,
+                "porosity": 0.5, "x0": 3 * n // 8}
+    p["ignite"] = [n // 8, 5 * n // 8, 1500.0]
+    p["name"] = f"cfg3_crop_reactive_bed_{n}^3_d3q19_{precision}"
     return p
 
 

@@ -13,6 +13,9 @@ state into a surrogate-mode domain, then profiles three surrogate steps and
 two Newton steps.
 batch: the first n of the 48 batched beds (FP32, K = 0) with one tile shape
 at the most resident blocks; profiles two batch steps.
+step3d: the 3-D D3Q19 reactive bed (256 x 128 x 128, or its first ncols
+columns) in one precision; times 20 steps with CUDA events, then profiles
+two steps.
 """
 from __future__ import annotations
 
@@ -77,6 +80,42 @@ def batch_case(n=48, tile="32x16"):
     print(b.config(), sum(p["nx"] * p["ny"] for p in I.config5(n=n)))
 
 
+def step3d_case(precision="fp32_fp16", ncols=256, kernel="tiled"):
+    import time
+
+    import numpy as np
+    import torch
+    p = I.config3(precision=precision)
+    f = I.config3_fields(p)
+    if ncols < p["nx"]:
+        nx, ny, nz = p["nx"], p["ny"], p["nz"]
+        cut = lambda a, k=1: np.ascontiguousarray(
+            np.asarray(a).reshape(k, nz, ny, nx)[..., :ncols]).reshape(-1)
+        f = {"phi": cut(f["phi"]), "T": cut(f["T"]), "Ts": cut(f["Ts"]),
+             "Y": cut(f["Y"], p["K"])}
+        p = dict(p, nx=ncols)
+    d = Domain(p, precision)
+    d.set_phase_field(f["phi"], f["Ts"])
+    d.set_fields(f["T"], f["Y"])
+    d.select_kernel(kernel)
+    d.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    d.step(20)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    N = f["phi"].size
+    print(f"step3d {precision} {p['nx']}x{p['ny']}x{p['nz']} kernel {kernel}: "
+          f"{ms * 1e3:.1f} us/step, {N / ms / 1e3:.0f} MLUPS", flush=True)
+    torch.cuda.profiler.start()
+    d.step(2)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("scalars", d.scalars())
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "surrogate"
     if case == "surrogate":
@@ -85,5 +124,9 @@ if __name__ == "__main__":
     elif case == "batch":
         batch_case(int(sys.argv[2]) if len(sys.argv) > 2 else 48,
                    sys.argv[3] if len(sys.argv) > 3 else "32x16")
+    elif case == "step3d":
+        step3d_case(sys.argv[2] if len(sys.argv) > 2 else "fp32_fp16",
+                    int(sys.argv[3]) if len(sys.argv) > 3 else 256,
+                    sys.argv[4] if len(sys.argv) > 4 else "tiled")
     else:
         raise SystemExit(f"unknown case {case}")

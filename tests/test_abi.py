@@ -83,3 +83,58 @@ def test_added_entry_points_reject_null_arguments_without_touching_the_gpu():
     assert L.pflb_set_surrogate(None, None, None) == -1
     assert L.pflb_chem_stats(None, None, None) == -1
     assert L.pflb_probe_fp64_fma(0, None) == -1
+
+
+def test_every_workload_passes_the_stability_checks():
+    """The descriptions of the five workloads (and the 3-D comparison crop)
+    pass the create / set_mechanism checks, including T_max."""
+    from paper_2310_17214_gb300 import inputs as I
+    probs = [I.config1(), I.config2(), I.config2(precision="fp32"), I.config3(),
+             I.config3_crop(64), I.config4(), I.config4(chem="surrogate")] + I.config5()
+    for p in probs:
+        rc, msg = nat.validate(p, p.get("precision", "fp64"))
+        assert rc == 0, (p.get("name"), rc, msg)
+
+
+def test_create_rejects_unstable_descriptions_without_touching_the_gpu():
+    """PFLB_ERR_UNSTABLE (-5) before any allocation: tau not above 1/2, a
+    thermal diffusion number above 1/6 in 3-D (the 3-D bed at the 2-D time
+    step, at its hottest temperature), a species diffusion number above the
+    limit (checked with the mechanism), a solid diffusion number above the
+    limit, the interface exchange number above 1, a sonic inlet."""
+    from paper_2310_17214_gb300 import inputs as I
+    L = nat.lib()
+    h = ctypes.c_void_p()
+
+    def create(p):
+        d = nat.make_desc(p, p.get("precision", "fp64"))
+        rc = L.pflb_create_domain(ctypes.byref(d), ctypes.byref(h))
+        assert not h.value
+        return rc, L.pflb_last_error(None).decode()
+
+    p = I.config1()
+    p["mu_ref"] = 1e-300
+    rc, msg = create(p)
+    assert rc == -5 and "relaxation time" in msg
+    p = I.config3()
+    p["dt"] = 2.5e-7
+    rc, msg = create(p)
+    assert rc == -5 and "thermal diffusion number" in msg, msg
+    p["T_max"] = 0.0  # at T_in and the solid temperature the 2-D step is still stable
+    assert nat.validate(p)[0] == 0
+    p = I.config2()
+    p["Dref"] = [d * 20 for d in p["Dref"]]
+    rc, msg = nat.validate(p)
+    assert rc == -5 and "species" in msg, msg
+    p = I.config2()
+    p["lambda_s"] *= 1e4
+    rc, msg = create(p)
+    assert rc == -5 and "solid diffusion" in msg, msg
+    p = I.config1()
+    p["A_T"] = 1e4
+    rc, msg = create(p)
+    assert rc == -5 and "exchange" in msg, msg
+    p = I.config1()
+    p["u_in"] = 0.6
+    rc, msg = create(p)
+    assert rc == -5 and "sound speed" in msg, msg

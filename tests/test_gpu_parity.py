@@ -185,14 +185,25 @@ def test_fp16_storage_config1_error_after_2000_steps():
     assert eu <= 5e-3 and eT <= 5e-3
 
 
-def test_fp32_reactive_small():
-    p = I.config2(nx=160, ny=48, precision="fp32")
+@pytest.mark.parametrize("precision,bar", [("fp32", 1e-4), ("fp32_fp16", 5e-3)])
+def test_fp32_reactive_bed_2000_steps(precision, bar):
+    """The reduced reactive bed (160 x 48, one-step chemistry through
+    ignition, transported solid temperature) after 2000 steps against the
+    oracle: L2 relative error of u, T - T_in and Y.  FP32 meets the 1e-4 bar;
+    the FP16-stored bar is the regression guard of the storage format in use
+    (the measured errors are printed)."""
+    p = I.config2(nx=160, ny=48, precision=precision)
     p["bed"] = {"count": 6, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 40}
     p["reactions"] = I.one_step_mechanism(3.3e8)
     f = I.config2_fields(p)
-    got, ref, sc, ora = run_pair(p, f, 200, precision="fp32")
-    assert l2rel(got["T"], ref["T"]) <= 1e-5
-    assert l2rel(got["u"], ref["u"]) <= 1e-3
+    O.set_threads(0)
+    got, ref, sc, ora = run_pair(p, f, 2000, precision=precision, chunks=2)
+    err = {"u": l2rel(got["u"], ref["u"]), "T": l2rel(got["T"] - 300.0, ref["T"] - 300.0),
+           "Y": l2rel(got["Y"], ref["Y"])}
+    print(f"{precision} 160x48 reactive, 2000 steps: " +
+          ", ".join(f"{k} {v:.2e}" for k, v in err.items()))
+    for k, v in err.items():
+        assert v <= bar, (k, v)
 
 
 # ------------------------------------------------------- kernel variants

@@ -93,6 +93,34 @@ def test_first_adam_step_moves_by_signed_learning_rate():
     net.close()
 
 
+def test_adam_steps_match_reference():
+    """Four library Adam steps on one fixed batch against the FP64 reference
+    Adam fed, at each step, the FP64 gradient at the BF16-rounded parameters:
+    this checks the second moment and the bias corrections of steps 2-4, not
+    only the first step.  Parameters whose gradient is clearly non-zero move
+    as the reference says to 1e-2; every tensor's displacement within 5e-2."""
+    theta, X, Y = case(2048, 8)
+    lr = 1e-3
+    net = Mlp()
+    net.set_params(theta)
+    net.train(dev(X), dev(Y), batch=2048, steps=4, lr=lr)
+    got = net.get_params().astype(np.float64) - theta.astype(np.float64)
+    net.close()
+    th = theta.astype(np.float64)
+    m, v = np.zeros_like(th), np.zeros_like(th)
+    g0 = None
+    for t in range(1, 5):
+        _, g = M.gradient(bf16_round(th.astype(np.float32)), bf16_round(X), Y.astype(np.float64))
+        g0 = g if g0 is None else g0
+        th, m, v = M.adam(th, g, m, v, t, lr)
+    ref = th - theta.astype(np.float64)
+    for t, (a, b, gg) in enumerate(zip(tensors(got), tensors(ref), tensors(g0))):
+        clear = np.abs(gg) > 0.2 * np.max(np.abs(gg))
+        assert clear.sum() > 0
+        assert np.allclose(a[clear], b[clear], rtol=1e-2, atol=0), t
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b), t
+
+
 def test_training_reduces_the_loss():
     theta, X, Y = case(65536, 4)
     net = Mlp()

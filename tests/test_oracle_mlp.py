@@ -49,3 +49,35 @@ def test_adam_reduces_the_loss():
         _, g = M.gradient(theta, X, Y)
         theta, m, v = M.adam(theta, g, m, v, t, 3e-3)
     assert M.loss(theta, X, Y) < 0.2 * L0
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g the bias-corrected moments are exactly g and
+    g^2 at every step (Kingma & Ba, Sec. 3), so each step moves theta by
+    -lr g / (|g| + eps): after t steps theta_t = theta_0 - t lr g / (|g| + eps).
+    A missing or wrong bias correction changes every step but the limit."""
+    rng = np.random.default_rng(6)
+    theta0 = rng.normal(0, 1, 50)
+    g = rng.normal(0, 1, 50) * np.logspace(-6, 2, 50)
+    lr, eps = 1e-2, 1e-8
+    theta, m, v = theta0.copy(), np.zeros(50), np.zeros(50)
+    for t in range(1, 8):
+        theta, m, v = M.adam(theta, g, m, v, t, lr, eps=eps)
+        ref = theta0 - t * lr * g / (np.abs(g) + eps)
+        assert np.allclose(theta, ref, rtol=0, atol=1e-13), t
+
+
+def test_adam_second_step_with_new_gradient():
+    """Two steps with gradients g1 then g2 (b1, b2 as in the library): the
+    bias-corrected moments are (b1 g1 + g2)/(1 + b1) and
+    (b2 g1^2 + g2^2)/(1 + b2), written out from the recursions by hand."""
+    rng = np.random.default_rng(7)
+    theta0 = rng.normal(0, 1, 20)
+    g1, g2 = rng.normal(0, 1, 20), rng.normal(0, 1, 20)
+    b1, b2, lr, eps = 0.9, 0.999, 1e-3, 1e-8
+    th, m, v = M.adam(theta0, g1, np.zeros(20), np.zeros(20), 1, lr)
+    th, m, v = M.adam(th, g2, m, v, 2, lr)
+    mh = (b1 * g1 + g2) / (1 + b1)
+    vh = (b2 * g1 ** 2 + g2 ** 2) / (1 + b2)
+    ref = theta0 - lr * g1 / (np.abs(g1) + eps) - lr * mh / (np.sqrt(vh) + eps)
+    assert np.allclose(th, ref, rtol=0, atol=1e-14)

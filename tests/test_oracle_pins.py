@@ -445,3 +445,83 @@ def test_channel_inlet_outlet_flux():
     ref = 4 * y * (ny - y) / ny ** 2
     assert np.max(np.abs(prof - ref / ref.max())) < 3e-2
     assert np.max(np.abs(ph.reshape(ny, nx)[:, -1])) < 2e-3
+
+
+# ------------------------------------------- temperature-dependent transport
+# Dynamic viscosity of air at 1 atm from standard property tables (Pa s).
+AIR_MU_TABLE = {300.0: 1.846e-5, 600.0: 3.058e-5}
+
+
+def _conduction_mode_mu(T0, nx=16, k=2, amp=1e-3, steps=4):
+    """Viscosity the oracle uses at T0, read back from the decay of a small
+    conduction mode (u = 0, one gas, physical units of the 2-D reactive bed).
+    Forward Euler with central differences maps a mode by
+    G = 1 - 2 a dt/dx^2 (1 - cos th), a = lambda / (rho cp) = mu / (rho Pr);
+    the O(amp^2) terms of the T-dependent coefficients do not project onto
+    the mode, so mu = a rho Pr follows to round-off."""
+    p = I._base(2, nx, 1)
+    p["bc"] = ["periodic"] * 6
+    p.update(dx=2.5e-5, dt=2.5e-7, rho_ref=1.2, sutherland=1, mu_ref=1.68e-5,
+             suth_T=273.0, suth_S=110.5, Pr=0.71)
+    x = np.arange(nx)
+    th = 2 * math.pi * k / nx
+    T = T0 + amp * np.cos(th * x)
+    for _ in range(steps):
+        T, _, _ = O.fd_phase(p, np.zeros(nx), T, None, None, np.zeros((2, nx)), p["P0"],
+                             p["P0"])
+    A = 2.0 / nx * np.sum((T - T.mean()) * np.cos(th * x))
+    G = (A / amp) ** (1.0 / steps)
+    a = (1.0 - G) * p["dx"] ** 2 / (2.0 * p["dt"] * (1.0 - math.cos(th)))
+    rho = p["P0"] * p["M0"] / (8.314 * T0)
+    return a * rho * p["Pr"]
+
+
+def test_sutherland_viscosity_against_air_tables():
+    """Sec. 4, eq. muT (Sutherland law, T* = 273 K, S = 110.5 K,
+    mu* = 1.68e-5 Pa s): the viscosity the oracle's conduction step uses at
+    300 K and 600 K matches tabulated air viscosity within 4 % (the paper's
+    mu* lies 2 % under the usual 1.716e-5), and the 600 K / 300 K ratio
+    within 2 %.  A wrong exponent (0.5 for 1.5) or swapped (T* + S)/(T + S)
+    moves the ratio by a factor 2.2 or 1.3."""
+    mu = {T: _conduction_mode_mu(T) for T in AIR_MU_TABLE}
+    for T, ref in AIR_MU_TABLE.items():
+        assert abs(mu[T] / ref - 1) < 0.04, (T, mu[T], ref)
+    r_tab = AIR_MU_TABLE[600.0] / AIR_MU_TABLE[300.0]
+    assert abs((mu[600.0] / mu[300.0]) / r_tab - 1) < 0.02
+    # and the read-back is the printed law itself, to round-off
+    for T in AIR_MU_TABLE:
+        law = 1.68e-5 * (T / 273.0) ** 1.5 * (273.0 + 110.5) / (T + 110.5)
+        assert abs(mu[T] / law - 1) < 1e-8
+
+
+def _species_mode_D(T0, nx=20, k=2, steps=5):
+    """Lattice diffusivity of the oracle's species step at uniform T0 (equal
+    molar masses and equal D_ref, so rho is uniform and the update linear):
+    the mode factor is G = 1 - 2 D (1 - cos th) exactly."""
+    p = _equal_mass_gas(small(2, nx, 1, bc=["periodic"] * 6, nu=0.05),
+                        D=(0.02, 0.02, 0.02))
+    p["D_Tref"], p["D_exp"] = 300.0, 1.7
+    x = np.arange(nx)
+    th = 2 * math.pi * k / nx
+    base = np.array([0.2, 0.3, 0.5])
+    amp = np.array([0.01, -0.004, -0.006])
+    Y = (base[:, None] + amp[:, None] * np.cos(th * x)[None, :]).reshape(-1)
+    T = np.full(nx, T0)
+    for _ in range(steps):
+        T, Y, _ = O.fd_phase(p, np.zeros(nx), T, Y, None, np.zeros((2, nx)), p["P0"], p["P0"])
+    Yk = Y.reshape(3, nx)
+    D = []
+    for kk in range(3):
+        A = 2.0 / nx * np.sum((Yk[kk] - base[kk]) * np.cos(th * x))
+        G = (A / amp[kk]) ** (1.0 / steps)
+        D.append((1.0 - G) / (2.0 * (1.0 - math.cos(th))))
+    return np.array(D)
+
+
+def test_species_diffusivity_power_law():
+    """D_k = D_ref (T / 300 K)^1.7 (the transport law of the reactive-bed
+    workload): the diffusivity read back from species modes at 300, 450 and
+    600 K is D_ref, D_ref 1.5^1.7 and D_ref 2^1.7."""
+    for T0 in (300.0, 450.0, 600.0):
+        D = _species_mode_D(T0)
+        assert np.allclose(D, 0.02 * (T0 / 300.0) ** 1.7, rtol=1e-11, atol=0), (T0, D)

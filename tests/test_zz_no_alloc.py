@@ -1,11 +1,11 @@
 """pflb_step_noalloc, the allocation-free variant of the fused step, against
 pflb_step on the same inputs, two calls in a row.
 
-It exists for callers that cannot allocate device memory -- code running
-while another component captures a CUDA graph, plug-ins whose host framework
-owns every device allocation, real-time loops that forbid allocator calls
-after start-up.  They pass their own state arrays; the library's reduction
-scratch is a fixed device array.  This file is collected last on purpose."""
+It exists for callers that cannot allocate device memory -- plug-ins whose
+host framework owns every device allocation through its own pool, loops that
+forbid allocator calls after start-up.  They pass their own state arrays; the
+library's reduction scratch is a fixed device array.  This file is collected
+last on purpose."""
 import numpy as np
 import pytest
 
@@ -86,3 +86,30 @@ def test_noalloc_rejects_oversized_and_unsupported():
     q["dim"], q["nz"] = 3, 4
     with pytest.raises(PflbError):
         step_noalloc(q, "fp64", arr, {"P0": p["P0"], "P0_prev": p["P0"]})
+
+
+def test_noalloc_validates_the_description_like_create():
+    """The description checks of pflb_create_domain run here too, before any
+    launch (the arrays are full-size, so nothing could go out of bounds
+    regardless): a bad boundary pairing, a P0 that is not positive and an
+    unstable description are refused with the reason in pflb_last_error."""
+    import torch
+    p, f = inert_case()
+    N = p["nx"] * p["ny"]
+    t = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda")
+    arr = {"phi": t(N), "g_in": t(9 * N), "g_out": t(9 * N), "T_in": t(N) + 300.0,
+           "T_out": t(N)}
+    sc = {"P0": p["P0"], "P0_prev": p["P0"]}
+    q = dict(p)
+    q["bc"] = ["inlet", "outlet", "periodic", "wall", "periodic", "periodic"]
+    with pytest.raises(PflbError) as e:
+        step_noalloc(q, "fp64", arr, sc)
+    assert e.value.code == -1 and "pairs" in str(e.value)
+    with pytest.raises(PflbError) as e:
+        step_noalloc(p, "fp64", arr, {"P0": 0.0, "P0_prev": 0.0})
+    assert e.value.code == -1 and "P0" in str(e.value)
+    q = dict(p)
+    q["A_T"] = 1e4
+    with pytest.raises(PflbError) as e:
+        step_noalloc(q, "fp64", arr, sc)
+    assert e.value.code == -5 and "exchange" in str(e.value)
