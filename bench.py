@@ -1,27 +1,33 @@
 """Benchmark of the fused PF-LB-FD time step on GB300.
 
-Workload: the 2-D reactive particle bed, 1024 x 256 D2Q9, 5 species with the
-one-step CH4 chemistry, transported solid temperature, 40 seeded ellipses
-(synthetic stand-in for the paper's packed beds).  A step is one pass of the
-whole hot path: pull collide-stream with drag, FD transport of T / Y / Ts,
-Arrhenius source, FP64 P0 / mass reduction; one fused kernel launch.
+Headline workload: the 3-D reactive particle bed, 256 x 128 x 128 D3Q19,
+5 species with the one-step CH4 chemistry, transported solid temperature,
+138 seeded ellipsoids (synthetic stand-in for the paper's packed beds), FP32
+compute with the populations stored as selected by --precision.  A step is one
+pass of the whole hot path: pull collide-stream with drag, FD transport of
+T / Y / Ts, Arrhenius source, FP64 P0 / mass reduction -- one fused kernel
+launch.  The working set (>= 0.5 GB) is larger than the 129 MB L2, so no flush
+is needed between steps.
 
-Prints ONE JSON line (rank 0).  `value` is MLUPS of the FP32 path (the
-configuration's mixed-precision leg) with inputs resident in HBM and L2
-flushed between steps; the plain FP64 GPU step is timed alongside and the
-error of FP32 against it is reported.  `--impl reference` times the FP64 CPU
-oracle instead (the reference arm of this project).
+Prints ONE JSON line (rank 0).  `value` is MLUPS with inputs resident in HBM;
+legs beside it: the plain FP64 GPU step of the same bed, the other FP32
+storage mode, the error of FP32 and FP16-stored runs against the FP64 run per
+field after 2000 steps, the 2-D reactive bed (1024 x 256), the learned
+chemistry surrogate, the batch of 48 beds, the end-to-end call with host
+buffers and the oracle on the host cores.  `--impl reference` times the FP64
+CPU oracle on the same workload (the reference arm of this project).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precision fp32|fp32_fp16|fp64] [--quick]
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -35,17 +41,23 @@ from paper_2310_17214_gb300 import inputs as I  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
 KERNEL_SRC = os.path.join(ROOT, "paper_2310_17214_gb300", "csrc", "pflb_kernels.cuh")
+DEFAULT_PRECISION = "fp32_fp16"
+METRIC = "MLUPS of the fused PF-LB-FD step (3-D D3Q19 reactive bed 256x128x128)"
 
 
 def alg_bytes_per_cell(prob, precision):
-    """Algorithmic bytes per cell update: populations read + write, T r/w,
+    """Algorithmic bytes per cell update: populations read + write (with the
+    FP16-stored mode, the FP16 residuals plus the cell's FP32 moments), T r/w,
     Y r/w, phi read, Ts r/w (derived fields excluded)."""
     Q = 9 if prob["dim"] == 2 else 19
-    b_g = {"fp64": 8, "fp32": 4, "fp32_fp16": 2}[precision]
     b = 8 if precision == "fp64" else 4
+    if precision == "fp32_fp16":
+        pops = 2 * Q * 2 + 2 * 4 * (prob["dim"] + 1)
+    else:
+        pops = 2 * Q * b
     K = prob.get("K", 0)
     ts = 2 * b if prob.get("Ts_field") else 0
-    return 2 * Q * b_g + 2 * b + 2 * K * b + b + ts
+    return pops + 2 * b + 2 * K * b + b + ts
 
 
 def measured_peaks():
@@ -66,24 +78,8 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_fp64_flops(workload):
-    """FP64 flops per cell of the FP64 step from the committed ncu count, if
-    it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_fp64_flops.txt")
-    if not os.path.exists(path):
-        return None
-    h = kernel_hash()
-    for line in open(path):
-        parts = line.split()
-        if len(parts) >= 4 and parts[0] == workload and parts[1] == "fp64" and parts[2] == h:
-            return float(parts[3])
-    return None
-
-
-def recorded_traffic(workload, precision):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.txt")
+def _recorded(fname, workload, precision):
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     h = kernel_hash()
@@ -94,62 +90,89 @@ def recorded_traffic(workload, precision):
     return None
 
 
-class ClockSampler:
-    """nvidia-smi samples (every 50 ms) during the timed region."""
+def recorded_fp64_flops(workload):
+    """FP64 flops per cell of the FP64 step from the committed ncu count, if it
+    was taken on the current kernel source (else None)."""
+    return _recorded("step_kernel_fp64_flops.txt", workload, "fp64")
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+def recorded_traffic(workload, precision):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    return _recorded("step_kernel_traffic.txt", workload, precision)
+
+
+class ClockSampler:
+    """SM clock and clock-event reasons sampled through NVML (ctypes, read
+    only) every millisecond while the timed region runs."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, device_index):
         self.dev = device_index
-        self.proc = None
-        self.lines = []
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._nvml = None
+        self._h = None
+
+    def _open(self):
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return False
+        if nv.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.dev)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok and nv.nvmlDeviceGetHandleByIndex_v2(self.dev, ctypes.byref(h)) != 0:
+            return False
+        self._nvml, self._h = nv, h
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.max_mhz = mx.value
+        return True
+
+    def _run(self):
+        nv, h = self._nvml, self._h
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0:
+                r = rs.value if nv.nvmlDeviceGetCurrentClocksEventReasons(
+                    h, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((mhz.value, r))
+            time.sleep(0.001)
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
+        if self._open():
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-            self.t.join(timeout=2)
+        self._stop.set()
+        if self._nvml is not None:
+            self._t.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+        if not self.samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples),
+                "sm_max_mhz": self.max_mhz, "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "NVML, 1 ms period, timed region"}
 
 
 def dist_setup(n_gpus):
@@ -183,52 +206,71 @@ def max_over_ranks(pg, x):
     return float(t.item())
 
 
+def workload_name(prob):
+    if prob["dim"] == 3:
+        return f"reactive_bed_{prob['nx']}x{prob['ny']}x{prob['nz']}_d3q19_k{prob['K']}"
+    return f"reactive_bed_{prob['nx']}x{prob['ny']}_d2q9_k{prob['K']}"
+
+
+def config_of(prob, fields, precision):
+    return {"workload": workload_name(prob), "nx": prob["nx"], "ny": prob["ny"],
+            "nz": prob.get("nz", 1), "lattice": "D3Q19" if prob["dim"] == 3 else "D2Q9",
+            "species": prob["K"], "particles": fields["info"]["placed"],
+            "porosity_bed": round(fields["info"]["porosity_bed"], 3),
+            "precision": precision,
+            "l2": "not flushed: the working set is larger than the 129 MB L2"}
+
+
 # ------------------------------------------------------------------ oracle arm
-def time_oracle(prob, fields, budget_s=12.0, max_steps=None, min_steps=2):
-    """Time the FP64 CPU oracle on the full grid (single thread) for about
-    budget_s seconds.  Returns (MLUPS, steps, seconds)."""
+def oracle_mlups(prob, fields, steps, threads):
+    """FP64 CPU oracle on the given grid: (MLUPS, seconds, threads used)."""
     from oracle import oracle as O
+    used = O.set_threads(threads)
     s = O.OracleState(prob, fields["phi"], fields["T"], fields["Y"], fields["Ts"])
-    N = fields["phi"].size
-    n, t0 = 0, time.perf_counter()
-    while True:
-        s.step(1)
-        n += 1
-        el = time.perf_counter() - t0
-        if (el >= budget_s and n >= min_steps) or (max_steps and n >= max_steps):
-            break
-    return N * n / el / 1e6, n, el
+    t0 = time.perf_counter()
+    s.step(steps)
+    el = time.perf_counter() - t0
+    return fields["phi"].size * steps / el / 1e6, el, used
 
 
-def crop_problem(prob, fields, ncols):
-    """The first `ncols` columns of the workload (same physics, inlet and
-    outlet kept), for bounded CPU samples."""
-    q = dict(prob)
-    q["nx"] = ncols
-    nx, ny = prob["nx"], prob["ny"]
-    cut = lambda a, k=1: None if a is None else \
-        np.ascontiguousarray(np.asarray(a).reshape(k, ny, nx)[:, :, :ncols]).reshape(-1)
-    f = {"phi": cut(fields["phi"]), "T": cut(fields["T"]), "Ts": cut(fields["Ts"]),
-         "Y": cut(fields["Y"], prob.get("K", 1)) if fields["Y"] is not None else None}
-    return q, f
+def cpu_baseline():
+    """The oracle on the 64^3 crop of the headline bed: all host cores, and
+    one core, each a sample of about 6-10 s."""
+    p = I.config3_crop(64)
+    f = I.config3_fields(p)
+    v_all, el_all, cores = oracle_mlups(p, f, 40, 0)
+    v_one, el_one, _ = oracle_mlups(p, f, 8, 1)
+    try:
+        model = next(ln.split(":", 1)[1].strip() for ln in open("/proc/cpuinfo")
+                     if ln.lower().startswith(("model name", "cpu part")))
+    except Exception:
+        model = None
+    return {"value": v_all, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"64^3 crop of the 3-D bed recipe (one-step chemistry, solid field), "
+                      f"40 steps on {cores} threads ({el_all:.1f} s); FP64 C with OpenMP "
+                      f"over the independent per-cell loops",
+            "single_thread": {"value": v_one, "sample": f"8 steps ({el_one:.1f} s)"},
+            "host_cpu": model, "nproc": os.cpu_count()}
 
 
 def run_reference(args, prob, fields, world, rank, pg):
-    """Reference arm: the FP64 CPU oracle on the host, each step a bounded
-    sample (a column crop of the workload) so that warm-up plus timed steps
-    take about two and a half minutes in total."""
+    """Reference arm: the FP64 CPU oracle on the host cores on the headline
+    workload, each step a bounded sample (a column crop when the whole grid
+    would not fit about two and a half minutes in all)."""
     if rank != 0:
         return
     from oracle import oracle as O
     O.build()
-    ny = prob["ny"]
-    q, f = crop_problem(prob, fields, 64)
+    cores = O.set_threads(0)
+    nx, ny, nz = prob["nx"], prob["ny"], prob.get("nz", 1)
+    plane = ny * nz
+    q, f = crop_problem(prob, fields, 16)
     s = O.OracleState(q, f["phi"], f["T"], f["Y"], f["Ts"])
     t0 = time.perf_counter()
     s.step(2)
-    rate = 2 * 64 * ny / (time.perf_counter() - t0)  # cells per second
+    rate = 2 * 16 * plane / (time.perf_counter() - t0)  # cells per second
     budget = 150.0 / (args.steps + args.warmup)
-    ncols = int(max(8, min(prob["nx"], budget * rate / ny)))
+    ncols = int(max(8, min(nx, budget * rate / plane)))
     q, f = crop_problem(prob, fields, ncols)
     s = O.OracleState(q, f["phi"], f["T"], f["Y"], f["Ts"])
     for _ in range(args.warmup):
@@ -237,36 +279,54 @@ def run_reference(args, prob, fields, world, rank, pg):
     for _ in range(args.steps):
         s.step(1)
     el = time.perf_counter() - t0
-    N = ncols * ny
+    N = ncols * plane
     mlups = N * args.steps / el / 1e6
-    sample = (f"first {ncols} of {prob['nx']} columns x {ny} rows of the workload, "
-              f"{args.steps} steps after {args.warmup} warm-up steps, single-threaded FP64 C")
+    sample = (f"first {ncols} of {nx} columns of the workload ({N} cells), {args.steps} steps "
+              f"after {args.warmup} warm-up steps, FP64 C on {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"reactive_bed_{prob['nx']}x{ny}_d2q9_k5", "nx": prob["nx"],
-                       "ny": ny, "lattice": "D2Q9", "species": prob["K"]},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "config": config_of(prob, fields, args.precision),
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-METRIC = "MLUPS of the fused PF-LB-FD step (2-D reactive bed 1024x256 D2Q9)"
+def crop_problem(prob, fields, ncols):
+    """The first `ncols` x-columns of the workload (same physics, inlet and
+    outlet kept), for bounded CPU samples."""
+    q = dict(prob)
+    q["nx"] = ncols
+    shape = (prob.get("nz", 1), prob["ny"], prob["nx"]) if prob["dim"] == 3 else \
+        (prob["ny"], prob["nx"])
+
+    def cut(a, k=1):
+        if a is None:
+            return None
+        return np.ascontiguousarray(np.asarray(a).reshape((k,) + shape)[..., :ncols]).reshape(-1)
+    f = {"phi": cut(fields["phi"]), "T": cut(fields["T"]), "Ts": cut(fields["Ts"]),
+         "Y": cut(fields["Y"], prob.get("K", 1)) if fields["Y"] is not None else None}
+    return q, f
 
 
 # --------------------------------------------------------------------- GPU arm
-def time_gpu(prob, fields, precision, steps, warmup, dev, flush, pg=None, clocks=False):
-    import torch
+def make_domain(prob, fields, precision, dev, stream):
     from paper_2310_17214_gb300._native import Domain
-    st = torch.cuda.current_stream(dev)
-    dom = Domain(prob, precision, stream=st.cuda_stream, device=dev.index)
+    dom = Domain(prob, precision, stream=stream, device=dev.index)
     dom.set_phase_field(fields["phi"], fields["Ts"])
     dom.set_fields(fields["T"], fields["Y"])
+    return dom
+
+
+def time_steps(dom, steps, warmup, dev, st, flush=None, pg=None, clocks=False):
+    """CUDA-event time of each of `steps` single steps (after `warmup`)."""
+    import torch
     for _ in range(warmup):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         dom.step(1)
     torch.cuda.synchronize(dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -278,7 +338,8 @@ def time_gpu(prob, fields, precision, steps, warmup, dev, flush, pg=None, clocks
         sampler.__enter__()
     w0 = time.perf_counter()
     for e0, e1 in evs:
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         e0.record(st)
         dom.step(1)
         e1.record(st)
@@ -287,9 +348,7 @@ def time_gpu(prob, fields, precision, steps, warmup, dev, flush, pg=None, clocks
     barrier(pg)
     if sampler:
         sampler.__exit__()
-    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    sc = dom.scalars()
-    return dom, ms, wall, (sampler.summary() if sampler else None), sc
+    return [e0.elapsed_time(e1) for e0, e1 in evs], wall, (sampler.summary() if sampler else None)
 
 
 def e2e_measure(prob, fields, precision, steps, dev):
@@ -297,11 +356,8 @@ def e2e_measure(prob, fields, precision, steps, dev):
     input state from pinned host memory (pflb_set_state), one step, read the
     result state back into pinned host memory (pflb_get_state)."""
     import torch
-    from paper_2310_17214_gb300._native import Domain
     st = torch.cuda.current_stream(dev)
-    dom = Domain(prob, precision, stream=st.cuda_stream, device=dev.index)
-    dom.set_phase_field(fields["phi"], fields["Ts"])
-    dom.set_fields(fields["T"], fields["Y"])
+    dom = make_domain(prob, fields, precision, dev, st.cuda_stream)
     nb = dom.state_bytes()
     h_in = torch.empty(nb, dtype=torch.uint8).pin_memory()
     h_out = torch.empty(nb, dtype=torch.uint8).pin_memory()
@@ -323,24 +379,26 @@ def e2e_measure(prob, fields, precision, steps, dev):
     return fields["phi"].size * steps / el / 1e6, nb
 
 
-def error_vs_fp64(prob, fields, steps, dev):
-    """L2 relative error of the FP32 path against the FP64 GPU path after
-    `steps` steps (u and T - T_in over the whole grid)."""
+def errors_vs_fp64(prob, fields, steps, dev, precisions):
+    """L2 relative error per field (u, T - T_in, Y, Ts - T_in over the whole
+    grid) of each FP32 mode against the FP64 GPU run after `steps` steps."""
     import torch
-    from paper_2310_17214_gb300._native import Domain
     st = torch.cuda.current_stream(dev)
     out = {}
-    for prec in ("fp64", "fp32"):
-        dom = Domain(prob, prec, stream=st.cuda_stream, device=dev.index)
-        dom.set_phase_field(fields["phi"], fields["Ts"])
-        dom.set_fields(fields["T"], fields["Y"])
+    for prec in ("fp64",) + tuple(precisions):
+        dom = make_domain(prob, fields, prec, dev, st.cuda_stream)
         dom.step(steps)
-        out[prec] = dom.get("T", "u")
+        out[prec] = dom.get("T", "Y", "Ts", "u")
         dom.close()
     l2 = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    return {"steps": steps,
-            "u_l2_rel": l2(out["fp32"]["u"], out["fp64"]["u"]),
-            "T_l2_rel": l2(out["fp32"]["T"] - prob["T_in"], out["fp64"]["T"] - prob["T_in"])}
+    T_in = prob["T_in"]
+    ref = out["fp64"]
+    res = {"steps": steps, "against": "FP64 GPU run of the same bed"}
+    for prec in precisions:
+        g = out[prec]
+        res[prec] = {"u": l2(g["u"], ref["u"]), "T": l2(g["T"] - T_in, ref["T"] - T_in),
+                     "Y": l2(g["Y"], ref["Y"]), "Ts": l2(g["Ts"] - T_in, ref["Ts"] - T_in)}
+    return res
 
 
 def _ms_per_step(dom, steps, flush, st):
@@ -361,24 +419,41 @@ def _ms_per_step(dom, steps, flush, st):
     return tot / steps
 
 
+def bed2d_leg(dev, flush, peaks, steps=50):
+    """The 2-D reactive bed (1024 x 256 D2Q9, 35 MB in FP32: L2-resident, so
+    the L2 is flushed between steps) in FP32."""
+    import torch
+    st = torch.cuda.current_stream(dev)
+    p = I.config2(precision="fp32")
+    f = I.config2_fields(p)
+    dom = make_domain(p, f, "fp32", dev, st.cuda_stream)
+    ms = _ms_per_step(dom, steps, flush, st)
+    dom.close()
+    N = f["phi"].size
+    bpc = alg_bytes_per_cell(p, "fp32")
+    ach = bpc * N / (ms * 1e-3) / 1e9
+    return {"workload": workload_name(p), "precision": "fp32", "ms_per_step": ms,
+            "mlups": N / ms / 1e3, "l2": "flushed between steps (256 MiB write)",
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                         "alg_bytes_per_cell": bpc}}
+
+
 def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6):
     """The learned chemistry on the two-step bed (2048 x 512, six species):
     sample the Newton run (FP32 transport), train on the GPU, run the
     surrogate from the same initial state, and compare it with the Newton
-    run after `steps` steps; then time the plain FP64 step (FP64 transport
-    and Newton), the FP32 + Newton step and the FP32 + surrogate step."""
+    run and with the plain FP64 run after `steps` steps; then time the plain
+    FP64 step (FP64 transport and Newton), the FP32 + Newton step and the
+    FP32 + surrogate step."""
     import torch
     from paper_2310_17214_gb300 import surrogate as S
-    from paper_2310_17214_gb300._native import Domain
     st = torch.cuda.current_stream(dev)
     p = I.config4(precision="fp32")
     f = I.config4_fields(p)
 
     def dom_of(chem, prec):
-        d = Domain(dict(p, chem=chem), prec, stream=st.cuda_stream, device=dev.index)
-        d.set_phase_field(f["phi"], f["Ts"])
-        d.set_fields(f["T"], f["Y"])
-        return d
+        return make_domain(dict(p, chem=chem), f, prec, dev, st.cuda_stream)
 
     ref = dom_of("implicit", "fp32")
     t0 = time.perf_counter()
@@ -394,7 +469,12 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
     sur = dom_of("surrogate", "fp32")
     sur.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], tol))
     sur.step(steps)
-    err = S.flame_errors(sur.get("T"), ref.get("T"), f["phi"], p)
+    T_sur = sur.get("T")
+    err = S.flame_errors(T_sur, ref.get("T"), f["phi"], p)
+    d64 = dom_of("implicit", "fp64")
+    d64.step(steps)
+    err64 = S.flame_errors(T_sur, d64.get("T"), f["phi"], p)
+    d64.close()
     fb, ev = sur.chem_stats()
     t_newton32 = _ms_per_step(ref, 30, flush, st)
     t_sur = _ms_per_step(sur, 100, flush, st)
@@ -410,28 +490,25 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
             "surrogate_mlups": N / t_sur / 1e3, "plain_fp64_mlups": N / t_plain64 / 1e3,
             "speedup_vs_plain_fp64": t_plain64 / t_sur,
             "speedup_vs_fp32_newton": t_newton32 / t_sur,
-            "error_after_steps": steps, "error_vs": "FP32 + Newton run from the same state",
-            **err, "fallback_frac": fb / ev if ev else None, "residual_tol": tol,
+            "error_after_steps": steps,
+            "error_vs_fp32_newton": err, "error_vs_plain_fp64": err64,
+            "fallback_frac": fb / ev if ev else None, "residual_tol": tol,
             "samples": int(len(X)), "sample_s": t_collect, "train_epochs": epochs,
             "train_s": t_train, "train_loss": loss}
 
 
-def batch_leg(dev, steps=200):
+def batch_leg(dev, peaks, steps=200):
     """48 uneven 2-D beds without species (8.5 M cells, FP32): aggregate
     MLUPS of the batched persistent kernel (tile shape and grid from the
     autotuner, graph replay) against the same domains advanced by 48
     separate launches per step.  Inputs exceed L2 (no flush needed)."""
     import torch
-    from paper_2310_17214_gb300._native import Batch, Domain
+    from paper_2310_17214_gb300._native import Batch
     st = torch.cuda.current_stream(dev)
-    probs = I.config5()
     doms, N = [], 0
-    for p in probs:
+    for p in I.config5():
         f = I.config5_fields(p)
-        d = Domain(p, "fp32", stream=st.cuda_stream, device=dev.index)
-        d.set_phase_field(f["phi"], f["Ts"])
-        d.set_fields(f["T"])
-        doms.append(d)
+        doms.append(make_domain(p, f, "fp32", dev, st.cuda_stream))
         N += f["phi"].size
 
     def timed(fn, k):
@@ -453,7 +530,6 @@ def batch_leg(dev, steps=200):
     b = Batch(doms)
     cfg, table = b.autotune(steps=5)
     ms_batch = timed(b.step, steps)
-    peaks, kind = measured_peaks()
     bpc = 2 * 9 * 4 + 2 * 4 + 4
     achieved = bpc * N / (ms_batch * 1e-3) / 1e9
     out = {"workload": f"batched_beds_48_domains_{N}_cells_d2q9_k0", "cells": N,
@@ -463,7 +539,7 @@ def batch_leg(dev, steps=200):
            "config": cfg, "autotune_us_per_step": {f"{t}/{k}": v for (t, k), v in table.items()},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                        "alg_bytes_per_cell": bpc, "peak_kind": kind},
+                        "alg_bytes_per_cell": bpc},
            "gpu_launches_per_step": 1}
     b.close()
     for d in doms:
@@ -474,19 +550,19 @@ def batch_leg(dev, steps=200):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_fp16"])
-    ap.add_argument("--quick", action="store_true", help="skip the FP64, e2e and CPU legs")
+    ap.add_argument("--precision", default=DEFAULT_PRECISION,
+                    choices=["fp32", "fp64", "fp32_fp16"])
+    ap.add_argument("--quick", action="store_true", help="the headline only, no legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
 
     world, rank, local, pg = dist_setup(args.gpus)
-    prob = I.config2(precision=args.precision)
-    fields = I.config2_fields(prob)
-    porosity = fields["info"]["porosity_bed"]
+    prob = I.config3(precision=args.precision)
+    fields = I.config3_fields(prob)
 
     if args.impl == "reference":
         run_reference(args, prob, fields, world, rank, pg)
@@ -495,79 +571,91 @@ def main():
     import torch
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
     N = fields["phi"].size
+    peaks, peak_kind = measured_peaks()
 
-    dom, ms, wall, clk, sc = time_gpu(prob, fields, args.precision, args.steps, args.warmup,
-                                      dev, flush, pg, clocks=(rank == 0))
+    dom = make_domain(prob, fields, args.precision, dev, st.cuda_stream)
+    ms, wall, clk = time_steps(dom, args.steps, args.warmup, dev, st, pg=pg, clocks=(rank == 0))
+    final_step = dom.scalars()["step"]
     dom.close()
     t_sum = sum(ms) / 1e3
     t_max = max_over_ranks(pg, t_sum)
     value = world * N * args.steps / t_max / 1e6
-    peaks, peak_kind = measured_peaks()
     bpc = alg_bytes_per_cell(prob, args.precision)
     per_launch = t_sum / args.steps
     achieved = bpc * N / per_launch / 1e9
-    workload = f"reactive_bed_{prob['nx']}x{prob['ny']}_d2q9_k5"
-    traffic = recorded_traffic(workload, args.precision)
+    workload = workload_name(prob)
+    kname = {"fp32": "float,float", "fp32_fp16": "float,__half", "fp64": "double,double"}
+    kernel = f"step_kernel<3,5,{kname[args.precision]}>"
 
     extra = {}
     if not args.quick and rank == 0:
-        d64, ms64, wall64, _, _ = time_gpu(prob, fields, "fp64", max(20, args.steps // 4),
-                                           args.warmup, dev, flush)
-        d64.close()
-        t64 = sum(ms64) / len(ms64) / 1e3
-        extra["fp64_step"] = {"value": N / t64 / 1e6, "unit": "MLUPS",
-                              "ms_per_step": t64 * 1e3, "steps": len(ms64),
-                              "alg_bytes_per_cell": alg_bytes_per_cell(prob, "fp64"),
-                              "achieved_gbs": alg_bytes_per_cell(prob, "fp64") * N / t64 / 1e9}
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        legs = {}
+        for prec in ("fp32", "fp32_fp16", "fp64"):
+            if prec == args.precision:
+                continue
+            d = make_domain(prob, fields, prec, dev, st.cuda_stream)
+            n = 10 if prec == "fp64" else 50
+            m, _, _ = time_steps(d, n, 3, dev, st)
+            d.close()
+            t = sum(m) / len(m) / 1e3
+            b = alg_bytes_per_cell(prob, prec)
+            legs[prec] = {"ms_per_step": t * 1e3, "mlups": N / t / 1e6,
+                          "alg_bytes_per_cell": b, "achieved_gbs": b * N / t / 1e9,
+                          "hbm_frac": b * N / t / 1e9 / peaks["hbm_gbs"]}
+        legs[args.precision] = {"ms_per_step": per_launch * 1e3, "mlups": N / per_launch / 1e6,
+                                "alg_bytes_per_cell": bpc, "achieved_gbs": achieved,
+                                "hbm_frac": achieved / peaks["hbm_gbs"]}
         # the FP64 step is bound by the FP64 pipe: its roofline is the probed FMA rate
         from paper_2310_17214_gb300._native import probe_fp64_tflops
         peak64 = probe_fp64_tflops(dev.index)
         fpc = recorded_fp64_flops(workload)
+        t64 = legs["fp64"]["ms_per_step"] / 1e3
         ach64 = fpc * N / t64 / 1e12 if fpc else None
-        extra["fp64_step"]["roofline"] = {
+        legs["fp64"]["roofline"] = {
             "bound": "alu", "unit": "TFLOP/s", "peak": peak64,
             "peak_kind": "measured FP64 FMA rate (pflb_probe_fp64_fma)",
-            "flops_per_cell": fpc, "achieved": ach64,
-            "frac": ach64 / peak64 if ach64 else None}
-        extra["speedup_vs_fp64"] = t64 / per_launch
-        extra["error_vs_fp64"] = error_vs_fp64(prob, fields, 500, dev)
+            "flops_per_cell": fpc, "achieved": ach64, "frac": ach64 / peak64 if ach64 else None}
+        extra["precision_legs"] = legs
+        extra["speedup_vs_fp64"] = {p_: t64 / (legs[p_]["ms_per_step"] / 1e3)
+                                    for p_ in ("fp32", "fp32_fp16")}
+        extra["error_vs_fp64"] = errors_vs_fp64(prob, fields, 2000, dev, ("fp32", "fp32_fp16"))
+        extra["bed_2d"] = bed2d_leg(dev, flush, peaks)
         extra["surrogate"] = surrogate_leg(dev, flush)
-        extra["batch"] = batch_leg(dev)
-        e2e_v, nb = e2e_measure(prob, fields, args.precision, 30, dev)
+        extra["batch"] = batch_leg(dev, peaks)
+        e2e_v, nb = e2e_measure(prob, fields, args.precision, 10, dev)
         e2e = {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb,
                "what": "pflb_set_state from pinned host + pflb_step(1) + pflb_get_state to "
                        "pinned host, per step"}
         from oracle import oracle as O
         O.build()
-        cv, cn, ce = time_oracle(prob, fields, budget_s=12.0)
-        cpu = {"value": cv, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"full {prob['nx']}x{prob['ny']} grid, {cn} steps ({ce:.1f} s, "
-                         f"single-threaded FP64 C)"}
+        cpu = cpu_baseline()
     else:
         e2e, cpu = None, None
 
     if rank != 0:
         return
+    cfg = config_of(prob, fields, args.precision)
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_fp16": "f32 (f16-stored populations)"}[
             args.precision],
-        "data": "synthetic (seeded ellipse packing, porosity %.3f in the bed)" % porosity,
-        "config": {"workload": workload, "nx": prob["nx"], "ny": prob["ny"], "lattice": "D2Q9",
-                   "species": prob["K"], "precision": args.precision,
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "data": "synthetic (seeded ellipsoid packing, porosity %.3f in the bed)" %
+                fields["info"]["porosity_bed"],
+        "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": recorded_traffic(workload, args.precision),
                      "peak_kind": peak_kind + " (copy burst)",
-                     "alg_bytes_per_cell": bpc, "kernel": "step_kernel<2,5,float,float>"},
+                     "alg_bytes_per_cell": bpc, "kernel": kernel},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-        "clocks": clk, "wall_s_timed": wall, "final_step": sc["step"],
+        "clocks": clk, "wall_s_timed": wall, "final_step": final_step,
     }
     line.update(extra)
     print(json.dumps(line), flush=True)

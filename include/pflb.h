@@ -51,7 +51,9 @@ extern "C" {
 /* precision modes */
 #define PFLB_FP64 0             /* FP64 compute and storage */
 #define PFLB_FP32 1             /* FP32 compute and storage; P0 / mass reductions in FP64 */
-#define PFLB_FP32_FP16STORE 2   /* FP32 compute, populations stored as scaled FP16 */
+#define PFLB_FP32_FP16STORE 2   /* FP32 compute; populations stored as FP16 residuals from the
+                                   cell's first-order equilibrium w_i (P + 3 c_i.j), with the
+                                   cell's moments (P, j) in FP32 */
 
 /* boundary kinds per face (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) */
 #define PFLB_BC_PERIODIC 0
@@ -168,7 +170,8 @@ typedef struct pflb_scalars {
  *     thermal diffusion number lambda dt / (rho cp dx^2) above 1/(2 dim)
  *     (1/4 in 2-D, 1/6 in 3-D), solid diffusion number above the same
  *     limit, interface exchange number A_T lambda dt / (rho cp (eta dx)^2)
- *     above 1, or |u_in| at or above the lattice sound speed 1/sqrt(3).
+ *     not below 2 (the forward-Euler bound of the relaxation toward Ts), or
+ *     |u_in| at or above the lattice sound speed 1/sqrt(3).
  *     pflb_set_mechanism repeats the check with the inlet mixture and the
  *     species diffusion numbers D_k(T) dt / dx^2.
  * Other errors: PFLB_ERR_OOM, PFLB_ERR_CUDA.  On error *out is NULL and
@@ -215,7 +218,8 @@ int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int 
 int pflb_get_scalars(pflb_domain* d, pflb_scalars* out);
 
 /* Size in bytes of a serialised state of this domain (header, scalars,
- * populations in their storage precision, T, Y, Ts). */
+ * populations in their storage precision -- with FP16 storage the residuals
+ * and then the FP32 cell moments (P, j) -- T, Y, Ts). */
 int pflb_state_bytes(const pflb_domain* d, size_t* bytes);
 
 /* Serialise the complete time-step state (checkpoint) into dst (host or

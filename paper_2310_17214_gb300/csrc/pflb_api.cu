@@ -57,16 +57,28 @@ __global__ void convert_kernel(const S* __restrict__ s, D* __restrict__ d, size_
     d[i] = D(s[i]);
 }
 
-struct Weights { float w_over_scale[19]; int Q; };
+struct Weights {
+  float w_over_scale[19], w[19];
+  int c[19][3];
+  int Q, dim;
+};
 
+// Stored populations -> populations.  FP16 storage keeps residuals from the
+// cell's first-order equilibrium: g_i = w_i (P + 3 c_i . j) + h_i w_i / S.
 template <class Store, class D>
-__global__ void decode_g_kernel(const Store* __restrict__ s, D* __restrict__ d, size_t N,
-                                Weights W) {
+__global__ void decode_g_kernel(const Store* __restrict__ s, const float* __restrict__ M,
+                                D* __restrict__ d, size_t N, Weights W) {
   const size_t n = N * (size_t)W.Q;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {
-    if constexpr (sizeof(Store) == 2) d[i] = D(__half2float(s[i]) * W.w_over_scale[i / N]);
-    else d[i] = D(s[i]);
+    if constexpr (sizeof(Store) == 2) {
+      const size_t q = i / N, c = i - q * N;
+      float cj = 0.f;
+      for (int a = 0; a < W.dim; ++a) cj += float(W.c[q][a]) * M[(1 + a) * N + c];
+      d[i] = D(__half2float(s[i]) * W.w_over_scale[q] + W.w[q] * (M[c] + 3.f * cj));
+    } else {
+      d[i] = D(s[i]);
+    }
   }
 }
 
@@ -126,7 +138,7 @@ Launcher* make_launcher(const pflb_domain* d) {
 }
 
 void free_buffers(pflb_domain* d) {
-  void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
+  void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.M[0], d->B.M[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
                   d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
                   d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats, d->B.tile_ctr};
   for (void* p : ptrs)
@@ -236,8 +248,10 @@ int check_stability(const pflb_domain_desc& D, const pflb_mechanism* m, std::str
       msg = buf;
       return PFLB_ERR_UNSTABLE;
     }
-    if (!(D.A_T * a / (D.eta * D.eta) <= 1.0)) {
-      std::snprintf(buf, sizeof(buf), "interface exchange number A_T a / eta^2 = %.4g above 1 at T = %g K",
+    // forward-Euler relaxation toward Ts: stable while the rate per step,
+    // at most A_T a / eta^2 (phi_s = 1), stays below 2
+    if (!(D.A_T * a / (D.eta * D.eta) < 2.0)) {
+      std::snprintf(buf, sizeof(buf), "interface exchange number A_T a / eta^2 = %.4g not below 2 at T = %g K",
                     D.A_T * a / (D.eta * D.eta), T);
       msg = buf;
       return PFLB_ERR_UNSTABLE;
@@ -355,6 +369,7 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   };
   for (int b = 0; b < 2; ++b) {
     al(&d->B.g[b], n * d->Q * d->store_sz);
+    if (d->mode == MODE_FP16) al(&d->B.M[b], n * (D.dim + 1) * sizeof(float));
     al(&d->B.T[b], n * d->real_sz);
     if (D.Ts_field) al(&d->B.Ts[b], n * d->real_sz);
   }
@@ -558,24 +573,28 @@ int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int 
   if (e == cudaSuccess && (mask & PFLB_FIELD_G)) {
     Weights W;
     W.Q = d->Q;
+    W.dim = d->dim;
     const float s = d->L->g_scale();
     for (int i = 0; i < d->Q; ++i) {
       double w = d->dim == 2 ? Lattice<2>::w(i) : Lattice<3>::w(i);
       W.w_over_scale[i] = float(w / s);
+      W.w[i] = float(w);
+      for (int a = 0; a < 3; ++a) W.c[i][a] = d->dim == 2 ? Lattice<2>::c(i, a) : Lattice<3>::c(i, a);
     }
+    const float* Mc = static_cast<const float*>(d->B.M[d->cur]);
     const size_t cnt = n * d->Q;
     int blocks = (int)((cnt + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     const void* g = d->B.g[d->cur];
     if (d->mode == MODE_FP64) {
-      if (esz == 8) decode_g_kernel<double, double><<<blocks, 256, 0, d->stream>>>((const double*)g, (double*)p, n, W);
-      else decode_g_kernel<double, float><<<blocks, 256, 0, d->stream>>>((const double*)g, (float*)p, n, W);
+      if (esz == 8) decode_g_kernel<double, double><<<blocks, 256, 0, d->stream>>>((const double*)g, Mc, (double*)p, n, W);
+      else decode_g_kernel<double, float><<<blocks, 256, 0, d->stream>>>((const double*)g, Mc, (float*)p, n, W);
     } else if (d->mode == MODE_FP32) {
-      if (esz == 8) decode_g_kernel<float, double><<<blocks, 256, 0, d->stream>>>((const float*)g, (double*)p, n, W);
-      else decode_g_kernel<float, float><<<blocks, 256, 0, d->stream>>>((const float*)g, (float*)p, n, W);
+      if (esz == 8) decode_g_kernel<float, double><<<blocks, 256, 0, d->stream>>>((const float*)g, Mc, (double*)p, n, W);
+      else decode_g_kernel<float, float><<<blocks, 256, 0, d->stream>>>((const float*)g, Mc, (float*)p, n, W);
     } else {
-      if (esz == 8) decode_g_kernel<__half, double><<<blocks, 256, 0, d->stream>>>((const __half*)g, (double*)p, n, W);
-      else decode_g_kernel<__half, float><<<blocks, 256, 0, d->stream>>>((const __half*)g, (float*)p, n, W);
+      if (esz == 8) decode_g_kernel<__half, double><<<blocks, 256, 0, d->stream>>>((const __half*)g, Mc, (double*)p, n, W);
+      else decode_g_kernel<__half, float><<<blocks, 256, 0, d->stream>>>((const __half*)g, Mc, (float*)p, n, W);
     }
     e = cudaGetLastError();
     p += cnt * esz;
@@ -601,10 +620,14 @@ struct StateHeader {
   int reserved[4];
 };
 
+size_t mom_bytes(const pflb_domain* d) {
+  return d->mode == MODE_FP16 ? (size_t)d->N * (d->dim + 1) * sizeof(float) : 0;
+}
+
 size_t state_bytes(const pflb_domain* d) {
   const size_t n = (size_t)d->N;
   size_t b = sizeof(StateHeader) + sizeof(DevScalars);
-  b += n * d->Q * d->store_sz + n * d->real_sz + n * d->K * d->real_sz;
+  b += n * d->Q * d->store_sz + mom_bytes(d) + n * d->real_sz + n * d->K * d->real_sz;
   if (d->desc.Ts_field) b += n * d->real_sz;
   return b;
 }
@@ -614,8 +637,9 @@ template <class F>
 int for_each_array(pflb_domain* d, F f) {
   const size_t n = (size_t)d->N;
   size_t off = sizeof(StateHeader) + sizeof(DevScalars);
-  struct A { void* p; size_t b; } arr[4] = {
-      {d->B.g[d->cur], n * d->Q * d->store_sz}, {d->B.T[d->cur], n * d->real_sz},
+  struct A { void* p; size_t b; } arr[5] = {
+      {d->B.g[d->cur], n * d->Q * d->store_sz}, {d->B.M[d->cur], mom_bytes(d)},
+      {d->B.T[d->cur], n * d->real_sz},
       {d->B.Y[d->cur], n * d->K * d->real_sz},
       {d->desc.Ts_field ? d->B.Ts[d->cur] : nullptr, d->desc.Ts_field ? n * d->real_sz : 0}};
   for (auto& a : arr) {

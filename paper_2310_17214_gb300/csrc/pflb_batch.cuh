@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(BLOCK, (BatchMinBlocks<Real, Store, T_>::value
 batch_step_kernel(const BatchDom<K, Real, Store>* __restrict__ doms,
                   const int* __restrict__ tile_begin, int ndom, int flip,
                   unsigned* __restrict__ tile_ctr) {
-  using PL = Plane<Real, K, T_::HP>;
+  using PL = Plane<Real, K, T_::HP, n_mom<2, Store>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PL* planes = reinterpret_cast<PL*>(smem_raw);
   __shared__ double red_sh[96];
@@ -100,9 +100,9 @@ batch_step_kernel(const BatchDom<K, Real, Store>* __restrict__ doms,
   }
 }
 
-template <int K, class Real, class T_>
+template <int K, class Real, class Store, class T_>
 constexpr size_t batch_smem_bytes() {
-  return sizeof(Plane<Real, K, T_::HP>);
+  return sizeof(Plane<Real, K, T_::HP, n_mom<2, Store>()>);
 }
 
 }  // namespace pflb

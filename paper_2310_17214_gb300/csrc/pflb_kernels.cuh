@@ -160,10 +160,22 @@ struct DevScalars {
   float P0_f, dlnP0_f, dP0r_f, pad_f;
 };
 
+// FP16 storage keeps, per cell, the FP32 moments (P, j) = (sum g*, sum c g*)
+// of the post-collision populations and, per direction, the FP16 residual
+// h_i = (g*_i - w_i (P + 3 c_i . j)) S / w_i (the first-order equilibrium of
+// the cell's own moments removed, so that the narrowed quantity is second
+// order in u).  A reader adds w_i (P + 3 c_i . j) of the source cell back.
+template <class Store> struct IsHalf { static constexpr bool value = false; };
+template <> struct IsHalf<__half> { static constexpr bool value = true; };
+template <int DIM, class Store>
+__host__ __device__ constexpr int n_mom() { return IsHalf<Store>::value ? DIM + 1 : 0; }
+
 template <class Real, class Store>
 struct State {
   const Store* __restrict__ g_in;
   Store* __restrict__ g_out;
+  const Real* __restrict__ M_in;   // FP16 storage: moments [DIM+1][N] of g_in (else null)
+  Real* __restrict__ M_out;        // FP16 storage: moments of g_out
   const Real* __restrict__ T_in;
   Real* __restrict__ T_out;
   const Real* __restrict__ Y_in;
@@ -190,7 +202,9 @@ template <> struct Codec<float, float> {
   __device__ static float get(const float* p, float) { return *p; }
   __device__ static void store(float* p, float v, float) { *p = v; }
 };
-// FP16: h = g / w * scale (weights folded so every direction has the same range)
+// FP16: residual r_i = g_i - w_i (P + 3 c_i . j), stored as h = r / w * scale
+// (weights folded so every direction has the same range); load/get return
+// r_i, the caller adds the first-order part of the source cell.
 template <> struct Codec<__half, float> {
   __device__ static float load(const __half* p, float w_over_scale) {
     return __half2float(__ldg(p)) * w_over_scale;
@@ -512,6 +526,30 @@ __device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
   *dT = zs[K] - T0;
 }
 
+// Moments read straight from global memory (the moments kernel, no staging).
+template <class Real>
+struct GlobalMom {
+  const Real* M;
+  int N;
+  __device__ __forceinline__ Real mom(int a, int src, int, int, int) const {
+    return M[(size_t)a * N + src];
+  }
+};
+
+// First-order part w_i (P + 3 c_i . j) of direction i at the source cell
+// (global index src, offset (dx, dy, dz) from the pulling cell).
+template <int DIM, class Real, class MA>
+__device__ __forceinline__ Real first_order(const MA& A, int i, int src, int dx, int dy, int dz) {
+  using L = Lattice<DIM>;
+  Real cj = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (L::c(i, a) > 0) cj += A.mom(1 + a, src, dx, dy, dz);
+    if (L::c(i, a) < 0) cj -= A.mom(1 + a, src, dx, dy, dz);
+  }
+  return Real(L::w(i)) * (A.mom(0, src, dx, dy, dz) + Real(3) * cj);
+}
+
 template <class Real, int K>
 __device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, const int xyz[3], int dim) {
   Real u = P.u_in;
@@ -529,21 +567,24 @@ __device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, const int xyz[
 // half-way bounce-back on walls (moving walls add 2 w rho c.u_w), the inlet
 // as a moving wall with the inlet velocity and inlet density, the outlet as
 // anti-bounce-back at P_h = 0 with wall velocity uw.
-template <int DIM, class Real, class Store, int K>
+template <int DIM, class Real, class Store, int K, class MA>
 __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real, Store>& S, int c,
                                      const int xyz[3], bool edge, Real rho_c, Real rho_in,
-                                     const Real* uw, Real* gin) {
+                                     const Real* uw, Real* gin, const MA& mom) {
   using L = Lattice<DIM>;
+  constexpr bool FO = IsHalf<Store>::value;  // residual storage: add the first-order part
   const int sy = P.nx, sz = P.nx * P.ny;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const Real wos = Real(L::w(i)) * P.g_inv_scale;
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = DIM == 3 ? L::c(i, 2) : 0;
     if (!edge) {
-      const int src = c - L::c(i, 0) - L::c(i, 1) * sy - (DIM == 3 ? L::c(i, 2) * sz : 0);
+      const int src = c - cx - cy * sy - cz * sz;
       gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos);
+      if constexpr (FO) gin[i] += first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz);
       continue;
     }
-    int sx[3] = {xyz[0] - L::c(i, 0), xyz[1] - L::c(i, 1), DIM == 3 ? xyz[2] - L::c(i, 2) : 0};
+    int sx[3] = {xyz[0] - cx, xyz[1] - cy, DIM == 3 ? xyz[2] - cz : 0};
     int wall = -1;
     bool inlet = false, outlet = false;
 #pragma unroll
@@ -561,7 +602,8 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
     const int ib = L::opp(i);
     if (wall >= 0 || inlet || outlet) {
       const Real wob = Real(L::w(ib)) * P.g_inv_scale;
-      const Real own = Codec<Store, Real>::load(S.g_in + (size_t)ib * P.N + c, wob);
+      Real own = Codec<Store, Real>::load(S.g_in + (size_t)ib * P.N + c, wob);
+      if constexpr (FO) own += first_order<DIM, Real>(mom, ib, c, 0, 0, 0);
       if (wall >= 0) {
         Real cu = 0;
 #pragma unroll
@@ -582,6 +624,8 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
     } else {
       const int src = sx[0] + P.nx * (sx[1] + P.ny * sx[2]);
       gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos);
+      // a periodic source: the staged halo holds its image at the same offset
+      if constexpr (FO) gin[i] += first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz);
     }
   }
 }
@@ -733,7 +777,8 @@ __device__ __forceinline__ void combine_partials(const double* partials, unsigne
       scal->flux_in = v1;
       scal->flux_out = v2;
       scal->step += 1;
-      if (!(I == I) || !(P0 == P0) || I <= 0.0) scal->status = -5;
+      // latch only the first failure (a timeout is not overwritten)
+      if (scal->status == 0 && (!(I == I) || !(P0 == P0) || I <= 0.0)) scal->status = -5;
     }
     scal->P0_prev = P0p;
     scal->P0 = P0;
@@ -802,18 +847,19 @@ static __global__ void finalize_kernel(const double* partials, unsigned nb, DevS
 // (diffusivity factor), Ts, phi_f rho f_D, then Y_k.
 enum { F_T = 0, F_PHI, F_RHO, F_KT, F_MU, F_FD, F_TS, F_RF, F_Y0 };
 
-template <class Real, int K, int HP>
+template <class Real, int K, int HP, int NM = 0>
 struct Plane {
-  Real f[F_Y0 + K][HP];
+  Real f[F_Y0 + K + NM][HP];  // NM moment fields (P, j) after the species
 };
 
 // Stage plane z (may be -1 or nz: ghost plane) of the block's tile with its
 // xy halo.  Out-of-domain halo cells follow the ghost rules: periodic faces
 // wrap; otherwise the adjacent cell's values, with the inlet state (T_in,
 // Y_in) on the inlet face and the wall temperature on a wall that has one.
-template <int DIM, class Real, class Store, int K, int HP, class T_ = Tile<DIM>>
+template <int DIM, class Real, class Store, int K, int HP, class T_ = Tile<DIM>,
+          int NM = n_mom<DIM, Store>()>
 __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const State<Real, Store>& S,
-                                            Plane<Real, K, HP>& pl, int x0, int y0, int z,
+                                            Plane<Real, K, HP, NM>& pl, int x0, int y0, int z,
                                             Real P0) {
   static_assert(T_::HP == HP, "plane and tile shape disagree");
   // tiles whose halo lies inside the lattice need no ghost rules
@@ -875,12 +921,16 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
     pl.f[F_RF][h] = phif * rho * fD;
 #pragma unroll
     for (int k = 0; k < K; ++k) pl.f[F_Y0 + k][h] = Y[k];
+    if constexpr (NM > 0) {
+#pragma unroll
+      for (int a = 0; a < NM; ++a) pl.f[F_Y0 + K + a][h] = __ldg(S.M_in + (size_t)a * P.N + c);
+    }
   }
 }
 
 // Staged-plane accessor: own and neighbour values of the staged fields and
 // properties (the populations come from global memory).
-template <int DIM, class Real, bool PRE = false, class TL = Tile<DIM>>
+template <int DIM, class Real, bool PRE = false, class TL = Tile<DIM>, int MF = 0>
 struct PlaneAcc {
   static constexpr int HP = TL::HP;
   static constexpr bool has_pops = PRE;  // populations prefetched into registers
@@ -897,7 +947,14 @@ struct PlaneAcc {
   }
   template <class Store>
   __device__ __forceinline__ Real pop(int i, Real) const { return PRE ? pre[i] : Real(0); }
+  // moment a of the staged cell at offset (dx, dy, dz) (FP16 storage; MF is
+  // the first moment field, src the cell's global index, unused here)
+  __device__ __forceinline__ Real mom(int a, int, int dx, int dy, int dz) const {
+    const Real* p = dz < 0 ? zm : (dz > 0 ? zp : cen);
+    return p[(MF + a) * HP + h + dx + dy * TL::HX];
+  }
 };
+
 
 // ------------------------------------------------------ the fused step
 // Per cell: (a1) pull + moments + implicit drag, (c) reaction source,
@@ -940,17 +997,21 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     for (int k = 0; k < K; ++k) Yin[k] = P.Y_in[k];
     rho_in = fdiv(P0 * P.eos_cr, P.T_in * mixture_invMw(P, Yin));
   }
+  constexpr bool FO = IsHalf<Store>::value;  // FP16 residual storage
   Real gin[Q];
-  Real u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
+  Real u[3] = {0, 0, 0}, uw[3] = {0, 0, 0}, mraw[3] = {0, 0, 0};
   const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
   const Real inv_rk = fdiv(Real(1), rho + Real(0.5) * Kd);
   for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
     if (Acc::has_pops && !edge) {
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
+      for (int i = 0; i < Q; ++i) {
         gin[i] = A.template pop<Store>(i, Real(L::w(i)) * P.g_inv_scale);
+        if constexpr (FO)
+          gin[i] += first_order<DIM, Real>(A, i, 0, -L::c(i, 0), -L::c(i, 1), 0);
+      }
     } else {
-      pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin);
+      pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin, A);
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -958,6 +1019,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
 #pragma unroll
       for (int i = 0; i < Q; ++i)
         if (L::c(i, a) != 0) m += Real(L::c(i, a)) * gin[i];
+      mraw[a] = m;
       u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) * inv_rk;
       uw[a] = u[a];
     }
@@ -988,7 +1050,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   // (b) species; the face factors (phi_f rho f_D averaged over the face) are
   // shared by every species, and the central differences of Y_k feed the
   // enthalpy-flux cross term of the temperature equation
-  Real Yn[KK];
+  Real Yn[KK], dYn[KK];
   Real sx[3] = {0, 0, 0};  // sum_k cp_k D_k (Y_k(+) - Y_k(-)) per axis
   {
     Real fm[DIM], fp[DIM];
@@ -1007,13 +1069,13 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
         dif += fp[a] * dp - fm[a] * dm;
         sx[a] += P.cpD[k] * (dp + dm);
       }
-      Yn[k] = fluid_on ? Y0[k] + (-phif * rho * adv + P.Dlat[k] * dif + phif * om[k]) * iphr
-                       : Y0[k];
+      dYn[k] = fluid_on ? (-phif * rho * adv + P.Dlat[k] * dif + phif * om[k]) * iphr : Real(0);
+      Yn[k] = Y0[k] + dYn[k];
     }
   }
 
   // (b) temperature
-  Real Tn = Ts0;
+  Real Tn = Ts0, dTn = Ts0 - T0;
   if (fluid_on) {
     Real adv = 0, dif = 0, cross = 0;
     const Real kc = A.c(F_KT);
@@ -1027,7 +1089,8 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
       if constexpr (K > 0) cross += Real(0.25) * fD * sx[a] * (tp - tm);
     }
     const Real rhs = -phif * rho * cp * adv + dif + phif * (rho * cross + dP0r + omT + SI);
-    Tn = T0 + rhs * iphr * fdiv(Real(1), cp);
+    dTn = rhs * iphr * fdiv(Real(1), cp);
+    Tn = T0 + dTn;
   }
 
   // solid temperature
@@ -1046,12 +1109,17 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     S.Ts_out[c] = Tsn;
   }
 
-  // low-Mach divergence D = (1/T) dT + Mw sum dY_k / M_k - dP0 / P0
-  Real D = (Tn - T0) * invT;
+  // low-Mach divergence D = (1/T) dT + Mw sum dY_k / M_k - dP0 / P0.  FP32
+  // takes the increments as computed (T^{n+1} - T^n rounded in FP32 would
+  // keep only a few digits of a small increment of a large T); FP64 forms
+  // the differences as the scheme writes them
+  Real D;
+  if constexpr (sizeof(Real) == 4) D = dTn * invT;
+  else D = (Tn - T0) * invT;
   if constexpr (K > 0) {
     Real sY = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) sY += (Yn[k] - Y0[k]) * P.invM[k];
+    for (int k = 0; k < K; ++k) sY += (sizeof(Real) == 4 ? dYn[k] : Yn[k] - Y0[k]) * P.invM[k];
     D += fdiv(sY, invMw);
   }
   D -= dlnP0;
@@ -1088,19 +1156,36 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const Real B = omega * rho3;
   const Real uu15 = Real(1.5) * uu;
   const Real keep = Real(1) - omega;
+  // FP16 storage: the post-collision moments of this cell in closed form
+  // (sum_i w_i e_i = 0, sum_i w_i x_i = u.G, sum_i w_i c_i e_i = u,
+  // sum_i w_i c_i x_i = F / 3 on the isotropic lattice); any values would do,
+  // since readers add back exactly what is subtracted here, but these leave
+  // a residual of second order in u
+  Real Pst = 0, jst[3] = {0, 0, 0};
+  if constexpr (FO) {
+    Pst = keep * sg + A0 + src_w * (uH - uF);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) jst[a] = keep * mraw[a] + B * u[a] + src_w * CS2 * F[a];
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const Real w = Real(L::w(i));
-    Real cu = 0, cH = 0, cF = 0;
+    Real cu = 0, cH = 0, cF = 0, cj = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      if (L::c(i, a) > 0) { cu += u[a]; cH += H[a]; cF += F[a]; }
-      if (L::c(i, a) < 0) { cu -= u[a]; cH -= H[a]; cF -= F[a]; }
+      if (L::c(i, a) > 0) { cu += u[a]; cH += H[a]; cF += F[a]; cj += jst[a]; }
+      if (L::c(i, a) < 0) { cu -= u[a]; cH -= H[a]; cF -= F[a]; cj -= jst[a]; }
     }
     const Real e = cu * (Real(3) + Real(4.5) * cu) - uu15;
     const Real x = (cH - uH) * e + (cF - uF);
-    const Real g = keep * gin[i] + w * (A0 + B * e + src_w * x);
+    Real g = keep * gin[i] + w * (A0 + B * e + src_w * x);
+    if constexpr (FO) g -= w * (Pst + Real(3) * cj);
     Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g, P.g_scale * Real(1.0 / L::w(i)));
+  }
+  if constexpr (FO) {
+    S.M_out[c] = Pst;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) S.M_out[(size_t)(1 + a) * P.N + c] = jst[a];
   }
 
   S.T_out[c] = Tn;
@@ -1130,7 +1215,8 @@ template <int DIM, class Real, class Store> struct MinBlocks {
 template <int DIM, int K, class Real, class Store, class T_ = Tile<DIM>>
 __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<Real, Store>& S,
                                           int bx, int by, int bz,
-                                          Plane<Real, K, T_::HP>* planes, double* red_sh,
+                                          Plane<Real, K, T_::HP, n_mom<DIM, Store>()>* planes,
+                                          double* red_sh,
                                           double& sI, double& sIn, double& sOut) {
   const Real P0 = scal_P0<Real>(S.scal);
   const Real dlnP0 = scal_dlnP0<Real>(S.scal);
@@ -1178,8 +1264,8 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
         const int xyz[3] = {x, yr, 0};
         const int hr = (ty + r * RS + 1) * T_::HX + (tx + 1);
         Real fi, fo;
-        const PlaneAcc<DIM, Real, T_::PREFETCH, T_> A{&planes[0].f[0][0], nullptr, nullptr, hr,
-                                                      pre[r]};
+        const PlaneAcc<DIM, Real, T_::PREFETCH, T_, F_Y0 + K> A{&planes[0].f[0][0], nullptr,
+                                                                nullptr, hr, pre[r]};
         accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
@@ -1197,7 +1283,7 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
         const int c = x + P.nx * (y + P.ny * z);
         const int xyz[3] = {x, y, z};
         Real fi, fo;
-        const PlaneAcc<DIM, Real, false, T_> A{&planes[z % 3].f[0][0],
+        const PlaneAcc<DIM, Real, false, T_, F_Y0 + K> A{&planes[z % 3].f[0][0],
                                                &planes[(z + 2) % 3].f[0][0],
                                                &planes[(z + 1) % 3].f[0][0], h, nullptr};
         accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
@@ -1217,7 +1303,7 @@ __global__ void __launch_bounds__(BLOCK, MinBlocks<DIM, Real, Store>::value)
 step_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
             const double* __restrict__ prev_partials, unsigned prev_nb) {
   using T_ = Tile<DIM>;
-  using PL = Plane<Real, K, T_::HP>;
+  using PL = Plane<Real, K, T_::HP, n_mom<DIM, Store>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PL* planes = reinterpret_cast<PL*>(smem_raw);
   __shared__ double red_sh[96];
@@ -1247,7 +1333,7 @@ step_persistent_kernel(const Params<Real, K> P, const State<Real, Store> S, int 
                        const double* __restrict__ prev_partials, unsigned prev_nb,
                        unsigned* __restrict__ tile_ctr, int parity) {
   static_assert(DIM == 2, "the persistent step walks 2-D tiles");
-  using PL = Plane<Real, K, T_::HP>;
+  using PL = Plane<Real, K, T_::HP, n_mom<DIM, Store>()>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PL* planes = reinterpret_cast<PL*>(smem_raw);
   __shared__ double red_sh[96];
@@ -1277,9 +1363,9 @@ step_persistent_kernel(const Params<Real, K> P, const State<Real, Store> S, int 
   }
 }
 
-template <int DIM, int K, class Real, class T_ = Tile<DIM>>
+template <int DIM, int K, class Real, class Store, class T_ = Tile<DIM>>
 constexpr size_t step_smem_bytes() {
-  return sizeof(Plane<Real, K, T_::HP>) * T_::NPL;
+  return sizeof(Plane<Real, K, T_::HP, n_mom<DIM, Store>()>) * T_::NPL;
 }
 
 // ------------------------------------------- chemistry pre-pass (implicit)
@@ -1338,13 +1424,20 @@ init_kernel(const Params<Real, K> P, const State<Real, Store> S, const Real* __r
       for (int a = 0; a < DIM; ++a) u[a] = u_init[(size_t)a * P.N + c];
     Real uu = 0;
     for (int a = 0; a < DIM; ++a) uu += u[a] * u[a];
+    // FP16 storage: moments P = 0, j = rho u / 3 of g_eq; the stored residual
+    // drops the first-order part w rho c.u
+    constexpr bool FO = IsHalf<Store>::value;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       const Real w = Real(L::w(i));
       Real cu = 0;
       for (int a = 0; a < DIM; ++a) cu += Real(L::c(i, a)) * u[a];
-      const Real geq = w * rho * (cu + Real(1.5) * cu * cu - Real(0.5) * uu);
+      const Real geq = w * rho * ((FO ? Real(0) : cu) + Real(1.5) * cu * cu - Real(0.5) * uu);
       Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, geq, P.g_scale * Real(1.0 / L::w(i)));
+    }
+    if constexpr (FO) {
+      S.M_out[c] = Real(0);
+      for (int a = 0; a < DIM; ++a) S.M_out[(size_t)(1 + a) * P.N + c] = rho * u[a] * Real(1.0 / 3.0);
     }
     acc = (Real(1) - S.phi[c]) / (T * invMw);
   }
@@ -1383,7 +1476,7 @@ moments_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __re
   const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
   Real gin[Q], u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
   for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
-    pull<DIM>(P, S, c, xyz, true, rho, rho_in, uw, gin);
+    pull<DIM>(P, S, c, xyz, true, rho, rho_in, uw, gin, GlobalMom<Real>{S.M_in, P.N});
     for (int a = 0; a < DIM; ++a) {
       Real m = 0;
       for (int i = 0; i < Q; ++i) m += Real(L::c(i, a)) * gin[i];

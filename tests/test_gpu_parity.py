@@ -176,22 +176,43 @@ def test_fp32_config1_error_after_2000_steps():
 
 
 def test_fp16_storage_config1_error_after_2000_steps():
+    """FP16 residuals from the first-order equilibrium with FP32 cell moments
+    on the 128x64 channel: L2 relative error of u and T after 2000 steps
+    <= 1e-4, the bar of the FP32 path."""
     p = I.config1()
     f = I.with_initial_u(p, I.config1_fields(p))
     got, ref, sc, ora = run_pair(p, f, 2000, precision="fp32_fp16", chunks=4)
     eu = l2rel(got["u"], ref["u"])
     eT = l2rel(got["T"] - 300.0, ref["T"] - 300.0)
     print(f"fp16-stored cfg1 2000 steps: L2 rel u {eu:.3e}, T-T_in {eT:.3e}")
-    assert eu <= 5e-3 and eT <= 5e-3
+    assert eu <= 1e-4 and eT <= 1e-4
 
 
-@pytest.mark.parametrize("precision,bar", [("fp32", 1e-4), ("fp32_fp16", 5e-3)])
+def test_fp16_storage_decodes_populations():
+    """get_fields(G) of an FP16-stored domain returns the populations (first-
+    order part plus residual): after the same steps they agree with the FP32
+    domain's populations to the residual's FP16 resolution."""
+    p = I.config2(nx=96, ny=40, precision="fp32_fp16")
+    p["bed"] = {"count": 4, "amin": 5, "amax": 9, "porosity": 0.6, "x0": 30}
+    f = I.config2_fields(p)
+    out = {}
+    for prec in ("fp32", "fp32_fp16"):
+        d = Domain(p, prec)
+        d.set_phase_field(f["phi"], f["Ts"])
+        d.set_fields(f["T"], f["Y"])
+        d.step(20)
+        out[prec] = d.get("g", "u")
+        d.close()
+    assert maxrel(out["fp32_fp16"]["g"], out["fp32"]["g"]) <= 1e-5
+    assert l2rel(out["fp32_fp16"]["u"], out["fp32"]["u"]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision,bar", [("fp32", 1e-4), ("fp32_fp16", 1e-4)])
 def test_fp32_reactive_bed_2000_steps(precision, bar):
     """The reduced reactive bed (160 x 48, one-step chemistry through
     ignition, transported solid temperature) after 2000 steps against the
-    oracle: L2 relative error of u, T - T_in and Y.  FP32 meets the 1e-4 bar;
-    the FP16-stored bar is the regression guard of the storage format in use
-    (the measured errors are printed)."""
+    oracle: L2 relative error of u, T - T_in and Y <= 1e-4 for FP32 storage
+    and FP16-stored residuals (the measured errors are printed)."""
     p = I.config2(nx=160, ny=48, precision=precision)
     p["bed"] = {"count": 6, "amin": 6, "amax": 10, "porosity": 0.6, "x0": 40}
     p["reactions"] = I.one_step_mechanism(3.3e8)
@@ -221,10 +242,12 @@ def _two_kernels(p, f, precision, nsteps):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_fp16"])
+@pytest.mark.parametrize("precision", ["fp32"])
 def test_tma_kernel_agrees_with_tiled_kernel(precision):
     """The TMA-pipelined kernel runs the same per-cell arithmetic on staged
-    copies of the same data: results agree to FP32 rounding."""
+    copies of the same data: results agree to FP32 rounding.  (FP16 storage
+    carries per-cell moments that the TMA stage does not fetch: that kernel
+    runs FP32 storage only.)"""
     p = I.config1()
     f = I.with_initial_u(p, I.config1_fields(p))
     out = _two_kernels(p, f, precision, 300)
