@@ -246,7 +246,14 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
  * atomic counter, so no second wave and no idle SMs at the end. */
 #define PFLB_KERNEL_PERSISTENT 2
 #define PFLB_KERNEL_PERSISTENT_32x16 3
-#define PFLB_KERNELS 4
+/* PFLB_KERNEL_MARCH(_PREFETCH): 3-D only; a resident grid in which each block
+ * marches a contiguous, equal share of the tile-planes along z (ring of three
+ * staged planes holding only what neighbours read); _PREFETCH also issues the
+ * next plane's pulls into registers before the current plane is updated,
+ * periodic faces wrapped in the addresses. */
+#define PFLB_KERNEL_MARCH 4
+#define PFLB_KERNEL_MARCH_PREFETCH 5
+#define PFLB_KERNELS 6
 
 /* Select the step kernel of a domain (after pflb_set_fields).  Returns
  * PFLB_ERR_UNSUPPORTED if the kernel cannot run this domain. */

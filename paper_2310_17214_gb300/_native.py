@@ -312,7 +312,8 @@ class Domain:
         _check(lib().pflb_get_scalars(self._h, C.byref(s)), self._h)
         return {f: getattr(s, f) for f, _ in Scalars._fields_}
 
-    KERNELS = {"tiled": 0, "tma": 1, "persistent": 2, "persistent_32x16": 3}
+    KERNELS = {"tiled": 0, "tma": 1, "persistent": 2, "persistent_32x16": 3, "march": 4,
+               "march_prefetch": 5}
 
     def select_kernel(self, name: str):
         _check(lib().pflb_select_kernel(self._h, self.KERNELS[name]), self._h)

@@ -279,7 +279,9 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
   Real C[Params<Real, K>::KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) C[k] = rho * P.rho_ref_M[k] * (Y[k] > Real(0) ? Y[k] : Real(0));
-  for (int j = 0; j < P.J; ++j) {
+#pragma unroll
+  for (int j = 0; j < JMAX; ++j) {
+    if (j >= P.J) break;  // static indices into the parameters
     Real kf = P.A_lat[j] * fexp(-P.EaR[j] * invT);
     if (P.b[j] != Real(0)) kf *= fpow(T, P.b[j]);
     Real q = kf;
@@ -934,6 +936,7 @@ template <int DIM, class Real, bool PRE = false, class TL = Tile<DIM>, int MF = 
 struct PlaneAcc {
   static constexpr int HP = TL::HP;
   static constexpr bool has_pops = PRE;  // populations prefetched into registers
+  static constexpr bool wrap_pops = false;  // ... for cells off every domain face only
   const Real* __restrict__ cen;
   const Real* __restrict__ zm;
   const Real* __restrict__ zp;
@@ -986,8 +989,19 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const Real Kd = P.Au_eta2 * mu * phif * phis * phis;
   const Real invT = fdiv(Real(1), T0);
 
-  bool edge = xyz[0] == 0 || xyz[0] == P.nx - 1 || xyz[1] == 0 || xyz[1] == P.ny - 1;
-  if (DIM == 3) edge = edge || xyz[2] == 0 || xyz[2] == P.nz - 1;
+  // cells whose pull needs the boundary rules; with pops prefetched across
+  // periodic faces (Acc::wrap_pops) only the non-periodic faces count
+  bool edge;
+  if constexpr (Acc::wrap_pops) {
+    edge = (xyz[0] == 0 && P.bc[0] != BC_PERIODIC) || (xyz[0] == P.nx - 1 && P.bc[1] != BC_PERIODIC) ||
+           (xyz[1] == 0 && P.bc[2] != BC_PERIODIC) || (xyz[1] == P.ny - 1 && P.bc[3] != BC_PERIODIC);
+    if (DIM == 3)
+      edge = edge || (xyz[2] == 0 && P.bc[4] != BC_PERIODIC) ||
+             (xyz[2] == P.nz - 1 && P.bc[5] != BC_PERIODIC);
+  } else {
+    edge = xyz[0] == 0 || xyz[0] == P.nx - 1 || xyz[1] == 0 || xyz[1] == P.ny - 1;
+    if (DIM == 3) edge = edge || xyz[2] == 0 || xyz[2] == P.nz - 1;
+  }
 
   // (a1) pull streaming, moments, implicit drag
   Real rho_in = 0;
@@ -1008,7 +1022,8 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
       for (int i = 0; i < Q; ++i) {
         gin[i] = A.template pop<Store>(i, Real(L::w(i)) * P.g_inv_scale);
         if constexpr (FO)
-          gin[i] += first_order<DIM, Real>(A, i, 0, -L::c(i, 0), -L::c(i, 1), 0);
+          gin[i] += first_order<DIM, Real>(A, i, 0, -L::c(i, 0), -L::c(i, 1),
+                                           DIM == 3 ? -L::c(i, 2) : 0);
       }
     } else {
       pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin, A);

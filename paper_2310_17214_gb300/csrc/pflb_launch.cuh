@@ -14,6 +14,7 @@
 #include "../../include/pflb.h"
 #include "pflb_batch.cuh"
 #include "pflb_chem.cuh"
+#include "pflb_step3d.cuh"
 #include "pflb_kernels.cuh"
 #include "pflb_surrogate.cuh"
 #include "pflb_tma.cuh"
@@ -331,7 +332,36 @@ struct LauncherImpl final : Launcher {
     if (k == 0) { kernel_sel = 0; return true; }
     if (k == 1 && tma_usable(B, cur) && tma_usable(B, 1 - cur)) { kernel_sel = 1; return true; }
     if ((k == 2 || k == 3) && DIM == 2 && B.tile_ctr) { kernel_sel = k; return true; }
+    if ((k == 4 || k == 5) && DIM == 3) { kernel_sel = k; return true; }
     return false;
+  }
+
+  // persistent z-march (3-D): grid = resident blocks per SM x SMs
+  int mgrid[2] = {0, 0};
+  template <bool PRE>
+  cudaError_t step_march(Buffers& B, int cur, cudaStream_t st, const double* prev) {
+    if constexpr (DIM == 3) {
+      constexpr size_t smem = march_smem_bytes<K, Real, Store>();
+      auto kern = step3d_march_kernel<K, Real, Store, PRE>;
+      int& grid = mgrid[PRE ? 1 : 0];
+      if (grid == 0) {
+        int dev = 0, sms = 0, occ = 0;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BLOCK, smem);
+        if (e != cudaSuccess) return e;
+        grid = std::max(1, occ) * sms;
+        if (grid > B.slots) grid = (int)B.slots;
+      }
+      kern<<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed, prev, (unsigned)B.last_nb);
+      B.last_nb = grid;
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
   }
 
   // persistent 2-D step with tile shape T_ (kernels 2: 32 x 8, 3: 32 x 16)
@@ -532,6 +562,9 @@ struct LauncherImpl final : Launcher {
         if (e != cudaSuccess) return e;
       } else if (kernel_sel == 3) {
         e = step_persistent<Tile<DIM, 32, 2>>(B, cur, st, prev, pgrid[1]);
+        if (e != cudaSuccess) return e;
+      } else if (kernel_sel == 4 || kernel_sel == 5) {
+        e = kernel_sel == 5 ? step_march<true>(B, cur, st, prev) : step_march<false>(B, cur, st, prev);
         if (e != cudaSuccess) return e;
       } else {
         step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,

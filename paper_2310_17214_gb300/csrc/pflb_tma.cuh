@@ -138,6 +138,7 @@ template <int K, class Store>
 struct TmaAcc {
   using LY = TmaLayout<K, Store>;
   static constexpr bool has_pops = true;
+  static constexpr bool wrap_pops = false;
   const float* __restrict__ raw;
   const Store* __restrict__ pops;
   const float* __restrict__ der;
