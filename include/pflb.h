@@ -217,6 +217,32 @@ int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int 
 /* Host copy of the scalar state; synchronises the stream. */
 int pflb_get_scalars(pflb_domain* d, pflb_scalars* out);
 
+/* Diagnostics of the current state (the state the next step sees), FP64 sums
+ * over the cells in lattice units (dx = dt = rho_ref = 1):
+ *   drag     sum K_d u, the force of the fluid on the solid phase (Sec.
+ *            3.2.1, eq. Fdrag-empirical-law with u_s = 0); a drag coefficient
+ *            is 2 drag_x / (rho u_ref^2 D);
+ *   heat     sum phi_f S_I, the heat passing from the solid into the fluid per
+ *            step (Sec. 3.3, eq. diffusion-heat-flux-3, read as relaxation
+ *            toward Ts), in lattice units of rho_ref cp T; a Nusselt number of
+ *            a particle of diameter D is heat / (pi lambda dT) in 2-D;
+ *   mass     sum phi_f rho, the fluid mass;
+ *   outlet_Tm  mixing-cup temperature of the outlet column (Sec. 4.2, eq.
+ *            Tmean-def), 0 without an outlet or outflow;
+ *   flux_in_total, flux_out_total  inlet and outlet mass fluxes summed over
+ *            every step since pflb_set_fields (a mass balance is mass(t) -
+ *            mass(0) against flux_in_total - flux_out_total).
+ * Allocates temporary device memory and synchronises the stream. */
+typedef struct pflb_diagnostics {
+  double drag[3];
+  double heat;
+  double mass;
+  double outlet_Tm;
+  double flux_in_total, flux_out_total;
+  long long step;
+} pflb_diagnostics;
+int pflb_get_diagnostics(pflb_domain* d, pflb_diagnostics* out);
+
 /* Size in bytes of a serialised state of this domain (header, scalars,
  * populations in their storage precision -- with FP16 storage the residuals
  * and then the FP32 cell moments (P, j) -- T, Y, Ts). */

@@ -93,6 +93,7 @@ def lib():
         L.orc_moments.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_step.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_void_p]
         L.orc_run.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_int]
+        L.orc_diagnostics.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, dp]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
         _lib = L
@@ -186,7 +187,7 @@ class OracleState:
         self.Ts = (np.ascontiguousarray(Ts, dtype=np.float64).reshape(N).copy()
                    if Ts is not None else None)
         self.g = np.zeros(Q * N)
-        self.scal = np.zeros(8)
+        self.scal = np.zeros(10)
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
         pp = None if Ph is None else np.ascontiguousarray(Ph, dtype=np.float64).reshape(-1)
         lib().orc_init(C.byref(self.p), self.phi, self.g, self.T, self.Y, _ptr(uu), _ptr(pp),
@@ -218,6 +219,17 @@ class OracleState:
         ph = np.zeros(self.N)
         lib().orc_moments(C.byref(self.p), self.phi, self.g, self.T, self.Y, self.scal, u, rho, ph)
         return u.reshape(dim, self.N), rho, ph
+
+    def diagnostics(self):
+        """Drag force (dim), heat from the solid, fluid mass, outlet mixing-cup
+        sums (rho u cp T, rho u cp) and the summed inlet / outlet fluxes."""
+        out = np.zeros(7)
+        lib().orc_diagnostics(C.byref(self.p), self.phi, self.g, self.T, self.Y, _ptr(self.Ts),
+                              self.scal, out)
+        dim = self.prob["dim"]
+        Tm = out[5] / out[6] if out[6] != 0 else 0.0
+        return {"drag": out[:dim].copy(), "heat": out[3], "mass": out[4], "outlet_Tm": Tm,
+                "flux_in_total": self.scal[7], "flux_out_total": self.scal[8]}
 
     @property
     def P0(self):

@@ -659,7 +659,7 @@ static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, 
 /* ----------------------------------------------------------- public API */
 /* scal: [0] P0, [1] P0 of the previous step, [2] fluid mass m (lattice),
  * [3] I = sum phi_f Mw / T, [4] inlet mass flux, [5] outlet mass flux,
- * [6] step counter. */
+ * [6] step counter, [7] / [8] inlet / outlet mass flux summed over the steps. */
 static double reduce_I(const orc_params* p, const double* phi, const double* T, const double* Y) {
   int N = ncell(p);
   double I = 0;
@@ -694,6 +694,7 @@ int orc_init(const orc_params* p, const double* phi, double* g, const double* T,
   scal[3] = I;
   scal[4] = scal[5] = 0;
   scal[6] = 0;
+  scal[7] = scal[8] = 0; /* inlet / outlet mass flux summed over the steps */
   return 0;
 }
 
@@ -806,9 +807,56 @@ int orc_step(const orc_params* p, const double* phi, double* g, double* T, doubl
   scal[4] = fin;
   scal[5] = fout;
   scal[6] += 1;
+  scal[7] += fin;
+  scal[8] += fout;
 
   free(gin); free(u); free(rho); free(Kd); free(mu); free(Tn); free(Yn);
   if (Tsn) free(Tsn);
+  return 0;
+}
+
+/* Diagnostics of the current state (what the next step sees), plain sums
+ * over the cells, lattice units:
+ *   out[0..2] drag: sum K_d u, the force of the fluid on the solid phase
+ *             (Sec. 3.2.1, eq. Fdrag-empirical-law with u_s = 0);
+ *   out[3]    heat: sum phi_f S_I, the heat flowing from the solid into the
+ *             fluid per step (Sec. 3.3, eq. diffusion-heat-flux-3, read as
+ *             relaxation toward Ts);
+ *   out[4]    fluid mass: sum phi_f rho;
+ *   out[5]    sum over the outlet column of rho u_x cp T, and
+ *   out[6]    of rho u_x cp: their ratio is the mixing-cup temperature T_m of
+ *             Sec. 4.2, eq. Tmean-def (0 / 0 without an outlet). */
+int orc_diagnostics(const orc_params* p, const double* phi, const double* g, const double* T,
+                    const double* Y, const double* Ts, const double* scal, double* out) {
+  lat_t L = lattice_of(p->dim);
+  int N = ncell(p), dim = p->dim;
+  double* gin = malloc(sizeof(double) * (size_t)L.Q * N);
+  double* u = malloc(sizeof(double) * (size_t)dim * N);
+  double* rho = malloc(sizeof(double) * N);
+  double* Kd = malloc(sizeof(double) * N);
+  double* mu = malloc(sizeof(double) * N);
+  stream_and_moments(p, L, phi, g, T, Y, scal[0], gin, u, rho, Kd, mu);
+  for (int k = 0; k < 7; ++k) out[k] = 0;
+  double eta2 = p->eta * p->eta;
+  for (int c = 0; c < N; ++c) {
+    int xyz[3];
+    coords(p, c, xyz);
+    cellv v;
+    derv d;
+    own(p, phi, T, Y, p->Ts_field ? Ts : NULL, N, c, &v);
+    derive(p, &v, scal[0], &d);
+    double phis = v.phi, phif = 1.0 - phis;
+    for (int a = 0; a < dim; ++a) out[a] += Kd[c] * u[(size_t)a * N + c];
+    int fluid_on = phif >= p->phi_min;
+    int solid_on = p->Ts_field ? (phis >= p->phi_min) : 1;
+    if (fluid_on && solid_on) out[3] += phif * (p->A_T * d.lam * phif * phis * phis / eta2 * (v.Ts - v.T));
+    out[4] += phif * rho[c];
+    if (p->bc[1] == ORC_BC_OUTLET && xyz[0] == p->nx - 1) {
+      out[5] += rho[c] * u[c] * d.cp * v.T;
+      out[6] += rho[c] * u[c] * d.cp;
+    }
+  }
+  free(gin); free(u); free(rho); free(Kd); free(mu);
   return 0;
 }
 

@@ -60,6 +60,12 @@ class Scalars(C.Structure):
                 ("step", C.c_longlong), ("status", C.c_int)]
 
 
+class Diagnostics(C.Structure):
+    _fields_ = [("drag", C.c_double * 3), ("heat", C.c_double), ("mass", C.c_double),
+                ("outlet_Tm", C.c_double), ("flux_in_total", C.c_double),
+                ("flux_out_total", C.c_double), ("step", C.c_longlong)]
+
+
 class Surrogate(C.Structure):
     _fields_ = [
         ("x_mean", C.c_double * 8), ("x_std", C.c_double * 8),
@@ -93,6 +99,7 @@ def lib():
         L.pflb_step.argtypes = [vp, C.c_int]
         L.pflb_get_fields.argtypes = [vp, C.c_uint, vp, C.c_size_t, C.c_int, C.c_int]
         L.pflb_get_scalars.argtypes = [vp, C.POINTER(Scalars)]
+        L.pflb_get_diagnostics.argtypes = [vp, C.POINTER(Diagnostics)]
         L.pflb_lattice.argtypes = [C.c_int, vp, vp]
         L.pflb_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.pflb_get_state.argtypes = [vp, vp, C.c_size_t, C.c_int]
@@ -311,6 +318,15 @@ class Domain:
         s = Scalars()
         _check(lib().pflb_get_scalars(self._h, C.byref(s)), self._h)
         return {f: getattr(s, f) for f, _ in Scalars._fields_}
+
+    def diagnostics(self) -> dict:
+        """Drag force (dim), heat from the solid, fluid mass, outlet mixing-cup
+        temperature and the summed inlet / outlet fluxes (lattice units)."""
+        s = Diagnostics()
+        _check(lib().pflb_get_diagnostics(self._h, C.byref(s)), self._h)
+        return {"drag": np.array(s.drag[:self.dim]), "heat": s.heat, "mass": s.mass,
+                "outlet_Tm": s.outlet_Tm, "flux_in_total": s.flux_in_total,
+                "flux_out_total": s.flux_out_total, "step": s.step}
 
     KERNELS = {"tiled": 0, "tma": 1, "persistent": 2, "persistent_32x16": 3, "march": 4,
                "march_prefetch": 5}

@@ -517,6 +517,34 @@ int pflb_get_scalars(pflb_domain* d, pflb_scalars* out) {
   return PFLB_OK;
 }
 
+int pflb_get_diagnostics(pflb_domain* d, pflb_diagnostics* out) {
+  if (!d || !out) return fail(d, PFLB_ERR_ARG, "NULL argument");
+  if (!d->has_fields || !d->L) return fail(d, PFLB_ERR_STATE, "no fields yet");
+  CK(d, cudaSetDevice(d->desc.device));
+  CK(d, d->L->finalize(d->B, d->stream));
+  double* buf = nullptr;
+  const int nb = d->L->diag_blocks();
+  CK(d, cudaMallocAsync((void**)&buf, ((size_t)nb + 1) * NDIAG * sizeof(double), d->stream));
+  cudaError_t e = d->L->diagnostics(d->B, d->cur, buf + NDIAG, buf, d->stream);
+  double h[NDIAG];
+  DevScalars s;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, buf, sizeof(h), cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s, d->B.scal, sizeof(s), cudaMemcpyDeviceToHost, d->stream);
+  cudaFreeAsync(buf, d->stream);
+  CK(d, e);
+  CK(d, cudaStreamSynchronize(d->stream));
+  for (int a = 0; a < 3; ++a) out->drag[a] = h[a];
+  out->heat = h[3];
+  out->mass = h[4];
+  out->outlet_Tm = h[6] != 0.0 ? h[5] / h[6] : 0.0;
+  out->flux_in_total = s.flux_in_sum;
+  out->flux_out_total = s.flux_out_sum;
+  out->step = s.step;
+  if (s.status != 0) return fail(d, s.status, "%s", status_message(s.status));
+  return PFLB_OK;
+}
+
 int pflb_get_fields(pflb_domain* d, unsigned mask, void* dst, size_t bytes, int dtype, int where) {
   if (!d || !dst) return fail(d, PFLB_ERR_ARG, "NULL argument");
   int r = check_dtype_where(d, dtype, where);
@@ -669,7 +697,7 @@ int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where) {
   CK(d, d->L->finalize(d->B, d->stream));
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
-  std::memcpy(h.magic, "PFLBSTv1", 8);
+  std::memcpy(h.magic, "PFLBSTv2", 8);
   h.version = 1;
   h.dim = d->dim; h.nx = d->desc.nx; h.ny = d->desc.ny; h.nz = d->desc.nz;
   h.precision = d->desc.precision; h.K = d->K; h.Ts_field = d->desc.Ts_field; h.N = d->N;
@@ -696,7 +724,7 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
   StateHeader h;
   if (where == PFLB_HOST) std::memcpy(&h, src, sizeof(h));
   else CK(d, cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDeviceToHost));
-  if (std::memcmp(h.magic, "PFLBSTv1", 8) != 0 || h.dim != d->dim || h.nx != d->desc.nx ||
+  if (std::memcmp(h.magic, "PFLBSTv2", 8) != 0 || h.dim != d->dim || h.nx != d->desc.nx ||
       h.ny != d->desc.ny || h.nz != d->desc.nz || h.precision != d->desc.precision ||
       h.K != d->K || h.Ts_field != d->desc.Ts_field || h.N != d->N)
     return fail(d, PFLB_ERR_ARG, "state does not match this domain");

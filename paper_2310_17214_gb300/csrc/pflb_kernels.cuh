@@ -153,6 +153,7 @@ struct Params {
 // reduction, in FP64 and in FP32.
 struct DevScalars {
   double P0, P0_prev, mass, I, flux_in, flux_out, mass_now;
+  double flux_in_sum, flux_out_sum;  // inlet / outlet mass flux summed over the steps
   long long step;
   int status;
   int pad;
@@ -192,12 +193,19 @@ struct State {
 // ----------------------------------------------------- storage codecs
 template <class Store, class Real> struct Codec;
 // load: from global memory (read-only path); get: from shared memory.
+// raw: the stored value as a number; dec(raw, w/S, fo): the population from it
+// and the first-order part fo of the source cell (FP16 storage: one FMA, the
+// same on every path that decodes, so all paths round alike).
 template <> struct Codec<double, double> {
+  __device__ static double raw(const double* p) { return __ldg(p); }
+  __device__ static double dec(double r, double, double) { return r; }
   __device__ static double load(const double* p, double) { return __ldg(p); }
   __device__ static double get(const double* p, double) { return *p; }
   __device__ static void store(double* p, double v, double) { *p = v; }
 };
 template <> struct Codec<float, float> {
+  __device__ static float raw(const float* p) { return __ldg(p); }
+  __device__ static float dec(float r, float, float) { return r; }
   __device__ static float load(const float* p, float) { return __ldg(p); }
   __device__ static float get(const float* p, float) { return *p; }
   __device__ static void store(float* p, float v, float) { *p = v; }
@@ -206,6 +214,10 @@ template <> struct Codec<float, float> {
 // (weights folded so every direction has the same range); load/get return
 // r_i, the caller adds the first-order part of the source cell.
 template <> struct Codec<__half, float> {
+  __device__ static float raw(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static float dec(float r, float w_over_scale, float fo) {
+    return __fmaf_rn(r, w_over_scale, fo);
+  }
   __device__ static float load(const __half* p, float w_over_scale) {
     return __half2float(__ldg(p)) * w_over_scale;
   }
@@ -279,9 +291,8 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
   Real C[Params<Real, K>::KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) C[k] = rho * P.rho_ref_M[k] * (Y[k] > Real(0) ? Y[k] : Real(0));
-#pragma unroll
-  for (int j = 0; j < JMAX; ++j) {
-    if (j >= P.J) break;  // static indices into the parameters
+#pragma unroll 1
+  for (int j = 0; j < P.J; ++j) {
     Real kf = P.A_lat[j] * fexp(-P.EaR[j] * invT);
     if (P.b[j] != Real(0)) kf *= fpow(T, P.b[j]);
     Real q = kf;
@@ -569,24 +580,53 @@ __device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, const int xyz[
 // half-way bounce-back on walls (moving walls add 2 w rho c.u_w), the inlet
 // as a moving wall with the inlet velocity and inlet density, the outlet as
 // anti-bounce-back at P_h = 0 with wall velocity uw.
-template <int DIM, class Real, class Store, int K, class MA>
-__device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real, Store>& S, int c,
-                                     const int xyz[3], bool edge, Real rho_c, Real rho_in,
-                                     const Real* uw, Real* gin, const MA& mom) {
-  using L = Lattice<DIM>;
-  constexpr bool FO = IsHalf<Store>::value;  // residual storage: add the first-order part
-  const int sy = P.nx, sz = P.nx * P.ny;
+// Lattice tables for the rolled boundary path of the pull (same order as
+// Lattice<DIM>).
+struct LatTab {
+  int c[19][3];
+  int opp[19];
+  float w[19];
+};
+template <int DIM>
+__host__ __device__ constexpr LatTab lat_tab() {
+  LatTab t{};
+  for (int i = 0; i < Lattice<DIM>::Q; ++i) {
+    for (int a = 0; a < 3; ++a) t.c[i][a] = Lattice<DIM>::c(i, a);
+    t.opp[i] = Lattice<DIM>::opp(i);
+    t.w[i] = float(Lattice<DIM>::w(i));
+  }
+  return t;
+}
+static __constant__ LatTab c_lat2 = lat_tab<2>();
+static __constant__ LatTab c_lat3 = lat_tab<3>();
+
+// First-order part of direction (cx, cy, cz) with weight w at runtime.
+template <int DIM, class Real, class MA>
+__device__ __forceinline__ Real first_order_rt(const MA& A, const int* cv, Real w, int src, int dx,
+                                               int dy, int dz) {
+  Real cj = 0;
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    const Real wos = Real(L::w(i)) * P.g_inv_scale;
-    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = DIM == 3 ? L::c(i, 2) : 0;
-    if (!edge) {
-      const int src = c - cx - cy * sy - cz * sz;
-      gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos);
-      if constexpr (FO) gin[i] += first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz);
-      continue;
-    }
-    int sx[3] = {xyz[0] - cx, xyz[1] - cy, DIM == 3 ? xyz[2] - cz : 0};
+  for (int a = 0; a < DIM; ++a)
+    if (cv[a] != 0) cj += Real(cv[a]) * A.mom(1 + a, src, dx, dy, dz);
+  return w * (A.mom(0, src, dx, dy, dz) + Real(3) * cj);
+}
+
+// Boundary path of the pull for one cell on a domain face: a rolled loop over
+// the directions (one copy of the code) writing ge[]; the rules: periodic
+// wrap; half-way bounce-back on walls (moving walls add 2 w rho c.u_w); the
+// inlet as a moving wall with the inlet velocity and inlet density; the
+// outlet as anti-bounce-back at P_h = 0 with wall velocity uw.
+template <int DIM, class Real, class Store, int K, class MA>
+__device__ __noinline__ void pull_edge(const Params<Real, K>& P, const State<Real, Store>& S, int c,
+                                       const int* xyz, Real rho_c, Real rho_in, const Real* uw,
+                                       Real* ge, const MA& mom) {
+  constexpr bool FO = IsHalf<Store>::value;
+  const LatTab& L = DIM == 2 ? c_lat2 : c_lat3;
+  const Real u_inl = inlet_u(P, xyz, DIM);
+#pragma unroll 1
+  for (int i = 0; i < Lattice<DIM>::Q; ++i) {
+    const int* cv = L.c[i];
+    int sx[3] = {xyz[0] - cv[0], xyz[1] - cv[1], DIM == 3 ? xyz[2] - cv[2] : 0};
     int wall = -1;
     bool inlet = false, outlet = false;
 #pragma unroll
@@ -601,34 +641,62 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
         else outlet = true;
       }
     }
-    const int ib = L::opp(i);
+    const Real w = Real(L.w[i]);
     if (wall >= 0 || inlet || outlet) {
-      const Real wob = Real(L::w(ib)) * P.g_inv_scale;
-      Real own = Codec<Store, Real>::load(S.g_in + (size_t)ib * P.N + c, wob);
-      if constexpr (FO) own += first_order<DIM, Real>(mom, ib, c, 0, 0, 0);
-      if (wall >= 0) {
-        Real cu = 0;
+      const int ib = L.opp[i];
+      const Real wb = Real(L.w[ib]);
+      const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)ib * P.N + c);
+      Real own;
+      if constexpr (FO) own = Codec<Store, Real>::dec(r, wb * P.g_inv_scale,
+                                                      first_order_rt<DIM, Real>(mom, L.c[ib], wb, c, 0, 0, 0));
+      else own = r;
+      Real cu = 0, uu = 0;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) cu += Real(L::c(i, a)) * P.wall_u[wall][a];
-        gin[i] = own + Real(2) * Real(L::w(i)) * rho_c * cu;
-      } else if (inlet) {
-        const Real cu = Real(L::c(i, 0)) * inlet_u(P, xyz, DIM);
-        gin[i] = own + Real(2) * Real(L::w(i)) * rho_in * cu;
-      } else {
-        Real cu = 0, uu = 0;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          cu += Real(L::c(i, a)) * uw[a];
-          uu += uw[a] * uw[a];
-        }
-        gin[i] = -own + Real(L::w(i)) * rho_c * (Real(3) * cu * cu - uu);
+      for (int a = 0; a < DIM; ++a) {
+        const Real ub = wall >= 0 ? P.wall_u[wall][a] : (outlet ? uw[a] : (a == 0 ? u_inl : Real(0)));
+        cu += Real(cv[a]) * ub;
+        uu += ub * ub;
       }
+      if (outlet) ge[i] = -own + w * rho_c * (Real(3) * cu * cu - uu);
+      else ge[i] = own + Real(2) * w * (inlet ? rho_in : rho_c) * cu;
     } else {
       const int src = sx[0] + P.nx * (sx[1] + P.ny * sx[2]);
-      gin[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src, wos);
+      const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)i * P.N + src);
       // a periodic source: the staged halo holds its image at the same offset
-      if constexpr (FO) gin[i] += first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz);
+      if constexpr (FO)
+        ge[i] = Codec<Store, Real>::dec(r, w * P.g_inv_scale,
+                                        first_order_rt<DIM, Real>(mom, cv, w, src, -cv[0], -cv[1],
+                                                                  DIM == 3 ? -cv[2] : 0));
+      else ge[i] = r;
     }
+  }
+}
+
+// Pull streaming of every population into the cell: interior cells read the
+// 19 (9) upstream neighbours; cells on a domain face take the boundary path.
+template <int DIM, class Real, class Store, int K, class MA>
+__device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real, Store>& S, int c,
+                                     const int xyz[3], bool edge, Real rho_c, Real rho_in,
+                                     const Real* uw, Real* gin, const MA& mom) {
+  using L = Lattice<DIM>;
+  constexpr bool FO = IsHalf<Store>::value;  // residual storage: add the first-order part
+  if (edge) {
+    Real ge[L::Q];
+    pull_edge<DIM, Real, Store, K>(P, S, c, xyz, rho_c, rho_in, uw, ge, mom);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) gin[i] = ge[i];
+    return;
+  }
+  const int sy = P.nx, sz = P.nx * P.ny;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = DIM == 3 ? L::c(i, 2) : 0;
+    const int src = c - cx - cy * sy - cz * sz;
+    const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)i * P.N + src);
+    if constexpr (FO)
+      gin[i] = Codec<Store, Real>::dec(r, Real(L::w(i)) * P.g_inv_scale,
+                                       first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz));
+    else gin[i] = r;
   }
 }
 
@@ -770,6 +838,7 @@ __device__ __forceinline__ void combine_partials(const double* partials, unsigne
       P0 = P0p = init_P0;
       scal->mass = init_P0 * I * eos_c;
       scal->flux_in = scal->flux_out = 0;
+      scal->flux_in_sum = scal->flux_out_sum = 0;
       scal->step = 0;
       scal->status = 0;
     } else {
@@ -778,6 +847,8 @@ __device__ __forceinline__ void combine_partials(const double* partials, unsigne
       if (p0_closed) P0 = scal->mass / (I * eos_c);
       scal->flux_in = v1;
       scal->flux_out = v2;
+      scal->flux_in_sum += v1;
+      scal->flux_out_sum += v2;
       scal->step += 1;
       // latch only the first failure (a timeout is not overwritten)
       if (scal->status == 0 && (!(I == I) || !(P0 == P0) || I <= 0.0)) scal->status = -5;
@@ -1020,10 +1091,12 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     if (Acc::has_pops && !edge) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
+        // prefetched values are raw stored numbers (scaled residuals with FP16)
         gin[i] = A.template pop<Store>(i, Real(L::w(i)) * P.g_inv_scale);
         if constexpr (FO)
-          gin[i] += first_order<DIM, Real>(A, i, 0, -L::c(i, 0), -L::c(i, 1),
-                                           DIM == 3 ? -L::c(i, 2) : 0);
+          gin[i] = Codec<Store, Real>::dec(gin[i], Real(L::w(i)) * P.g_inv_scale,
+                                           first_order<DIM, Real>(A, i, 0, -L::c(i, 0), -L::c(i, 1),
+                                                                  DIM == 3 ? -L::c(i, 2) : 0));
       }
     } else {
       pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin, A);
@@ -1065,7 +1138,8 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   // (b) species; the face factors (phi_f rho f_D averaged over the face) are
   // shared by every species, and the central differences of Y_k feed the
   // enthalpy-flux cross term of the temperature equation
-  Real Yn[KK], dYn[KK];
+  Real Yn[KK];
+  Real sYd = 0;  // sum_k (Y_k^{n+1} - Y_k^n) / M_k for the divergence
   Real sx[3] = {0, 0, 0};  // sum_k cp_k D_k (Y_k(+) - Y_k(-)) per axis
   {
     Real fm[DIM], fp[DIM];
@@ -1084,8 +1158,11 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
         dif += fp[a] * dp - fm[a] * dm;
         sx[a] += P.cpD[k] * (dp + dm);
       }
-      dYn[k] = fluid_on ? (-phif * rho * adv + P.Dlat[k] * dif + phif * om[k]) * iphr : Real(0);
-      Yn[k] = Y0[k] + dYn[k];
+      const Real dY = fluid_on ? (-phif * rho * adv + P.Dlat[k] * dif + phif * om[k]) * iphr
+                               : Real(0);
+      Yn[k] = Y0[k] + dY;
+      // FP32 takes the increment as computed; FP64 the difference as written
+      sYd += (sizeof(Real) == 4 ? dY : Yn[k] - Y0[k]) * P.invM[k];
     }
   }
 
@@ -1131,12 +1208,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   Real D;
   if constexpr (sizeof(Real) == 4) D = dTn * invT;
   else D = (Tn - T0) * invT;
-  if constexpr (K > 0) {
-    Real sY = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) sY += (sizeof(Real) == 4 ? dYn[k] : Yn[k] - Y0[k]) * P.invM[k];
-    D += fdiv(sY, invMw);
-  }
+  if constexpr (K > 0) D += fdiv(sYd, invMw);
   D -= dlnP0;
 
   // (a) source and BGK collision: omega = 1/tau = 2 rho / (rho + 6 mu)
@@ -1263,9 +1335,8 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
           const int c = x + P.nx * yr;
 #pragma unroll
           for (int i = 0; i < L::Q; ++i)
-            pre[r][i] = Codec<Store, Real>::load(
-                S.g_in + (size_t)i * P.N + c - L::c(i, 0) - L::c(i, 1) * P.nx,
-                Real(L::w(i)) * P.g_inv_scale);
+            pre[r][i] = Codec<Store, Real>::raw(
+                S.g_in + (size_t)i * P.N + c - L::c(i, 0) - L::c(i, 1) * P.nx);
         }
       }
     }
@@ -1504,6 +1575,84 @@ moments_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __re
   for (int a = 0; a < DIM; ++a) u_out[(size_t)a * P.N + c] = double(u[a]);
   rho_out[c] = double(rho);
   ph_out[c] = double(sg);
+}
+
+// ------------------------------------------------- diagnostics (on demand)
+// Per-cell terms of the domain diagnostics of the state the next step sees,
+// summed per block in FP64: drag sum K_d u (the force of the fluid on the
+// solid phase, Sec. 3.2.1), heat sum phi_f S_I (Sec. 3.3, eq.
+// diffusion-heat-flux-3), fluid mass sum phi_f rho, and over the outlet
+// column rho u_x cp T and rho u_x cp (mixing-cup temperature, Sec. 4.2).
+constexpr int NDIAG = 8;
+template <int DIM, int K, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK)
+diag_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __restrict__ part) {
+  using L = Lattice<DIM>;
+  constexpr int Q = L::Q;
+  constexpr int KK = Params<Real, K>::KK;
+  __shared__ double red_sh[32];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (c < P.N) {
+    const Real P0 = Real(S.scal->P0);
+    int xyz[3];
+    xyz[0] = c % P.nx;
+    xyz[1] = (c / P.nx) % P.ny;
+    xyz[2] = DIM == 3 ? c / (P.nx * P.ny) : 0;
+    const Real T = S.T_in[c];
+    Real Y[KK];
+#pragma unroll
+    for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
+    const Real rho = P0 * Real(P.eos_c) / (T * mixture_invMw(P, Y));
+    const Real phis = S.phi[c], phif = Real(1) - phis;
+    const Real mu = viscosity(P, T);
+    const Real cp = mixture_cp(P, Y);
+    const Real Kd = P.Au_eta2 * mu * phif * phis * phis;
+    Real Yin[KK];
+#pragma unroll
+    for (int k = 0; k < K; ++k) Yin[k] = P.Y_in[k];
+    const Real rho_in = P0 * Real(P.eos_c) / (P.T_in * mixture_invMw(P, Yin));
+    const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
+    Real gin[Q], u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
+    for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
+      pull<DIM>(P, S, c, xyz, true, rho, rho_in, uw, gin, GlobalMom<Real>{S.M_in, P.N});
+      for (int a = 0; a < DIM; ++a) {
+        Real m = 0;
+        for (int i = 0; i < Q; ++i) m += Real(L::c(i, a)) * gin[i];
+        u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) / (rho + Real(0.5) * Kd);
+        uw[a] = u[a];
+      }
+    }
+    for (int a = 0; a < DIM; ++a) v[a] = double(Kd * u[a]);
+    const Real Ts = P.Ts_field ? S.Ts_in[c] : P.Ts_uniform;
+    const bool fluid_on = phif >= P.phi_min;
+    const bool solid_on = P.Ts_field ? (phis >= P.phi_min) : true;
+    if (fluid_on && solid_on)
+      v[3] = double(phif * (P.AT_eta2 * (mu * cp * P.inv_Pr) * phif * phis * phis * (Ts - T)));
+    v[4] = double(phif * rho);
+    if (outlet_cell) {
+      v[5] = double(rho * u[0] * cp * T);
+      v[6] = double(rho * u[0] * cp);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NDIAG; ++k) {
+    const double s = block_sum<double>(v[k], red_sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * NDIAG + k] = s;
+  }
+}
+
+// Fixed-order sum of the block partials (one warp).
+static __global__ void diag_combine_kernel(const double* __restrict__ part, int nb,
+                                           double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < NDIAG; ++k) {
+    double s = 0;
+    for (int b = lane; b < nb; b += 32) s += part[(size_t)b * NDIAG + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[k] = s;
+  }
 }
 
 }  // namespace pflb

@@ -117,6 +117,11 @@ struct Launcher {
   virtual int batch_key() const = 0;
   // bound of the kernels' device waits (SM clock cycles)
   virtual void set_wait_limit(long long cycles) = 0;
+  // NDIAG diagnostic sums of the current state into out (device); part holds
+  // blocks() * NDIAG doubles
+  virtual cudaError_t diagnostics(const Buffers& B, int cur, double* part, double* out,
+                                  cudaStream_t st) = 0;
+  virtual int diag_blocks() const = 0;
 };
 
 constexpr double R_GAS = 8.314;  // J/(mol K), value printed in Sec. 3.1
@@ -590,6 +595,13 @@ struct LauncherImpl final : Launcher {
     return cudaGetLastError();
   }
   float g_scale() const override { return float(P.g_scale); }
+  int diag_blocks() const override { return blocks(); }
+  cudaError_t diagnostics(const Buffers& B, int cur, double* part, double* out,
+                          cudaStream_t st) override {
+    diag_kernel<DIM, K, Real, Store><<<blocks(), BLOCK, 0, st>>>(P, state(B, cur), part);
+    diag_combine_kernel<<<1, 32, 0, st>>>(part, blocks(), out);
+    return cudaGetLastError();
+  }
 };
 
 // factories, one per translation unit (compiled in parallel)

@@ -168,8 +168,7 @@ __device__ __forceinline__ bool march_prefetch(const Params<Real, K>& P,
   for (int i = 0; i < L::Q; ++i) {
     const int src =
         v[0][1 - L::c(i, 0)] + P.nx * (v[1][1 - L::c(i, 1)] + P.ny * v[2][1 - L::c(i, 2)]);
-    out[i] = Codec<Store, Real>::load(S.g_in + (size_t)i * P.N + src,
-                                      Real(L::w(i)) * P.g_inv_scale);
+    out[i] = Codec<Store, Real>::raw(S.g_in + (size_t)i * P.N + src);
   }
   return true;
 }
@@ -223,15 +222,13 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
                                 z_begin - 1, P0);
     march_stage<Real, Store, K>(P, S, planes + (z_begin % 3) * NF * HP, x0, y0, z_begin, P0);
     Real pre[L::Q], nxt[L::Q];
-    bool have = false, have_nxt = false;
     if constexpr (PRE) {
-      if (in_xy) have = march_prefetch<Real, Store, K>(P, S, x, y, z_begin, pre);
+      if (in_xy) march_prefetch<Real, Store, K>(P, S, x, y, z_begin, pre);
     }
     for (int z = z_begin; z < z_end; ++z) {
       march_stage<Real, Store, K>(P, S, planes + ((z + 1) % 3) * NF * HP, x0, y0, z + 1, P0);
       if constexpr (PRE) {
-        have_nxt = false;
-        if (in_xy && z + 1 < z_end) have_nxt = march_prefetch<Real, Store, K>(P, S, x, y, z + 1, nxt);
+        if (in_xy && z + 1 < z_end) march_prefetch<Real, Store, K>(P, S, x, y, z + 1, nxt);
       }
       __syncthreads();
       if (in_xy) {
@@ -246,14 +243,10 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
         const MarchAcc<Real, K, PRE> A{cen, planes + ((z + 2) % 3) * NF * HP,
                                        planes + ((z + 1) % 3) * NF * HP, h, viscosity(P, T0), fD,
                                        pre};
+        // a cell that prefetched nothing lies on a non-periodic face: the
+        // update takes its boundary path of the pull (edge) there
         Real fi, fo;
-        if (PRE && !have) {
-          // a cell on a non-periodic face: the boundary path of the pull
-          const MarchAcc<Real, K, false> B{A.cen, A.zm, A.zp, h, A.mu, A.fD, nullptr};
-          accI += cell_update<3, K, Real, Store>(P, S, B, c, xyz, P0, dlnP0, dP0r, fi, fo);
-        } else {
-          accI += cell_update<3, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
-        }
+        accI += cell_update<3, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
       }
@@ -261,7 +254,6 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
       if constexpr (PRE) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) pre[i] = nxt[i];
-        have = have_nxt;
       }
     }
   }

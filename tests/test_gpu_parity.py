@@ -74,6 +74,48 @@ def test_fp64_config1_channel_disc_full_size():
     assert_fp64(*run_pair(p, f, 400, chunks=2))
 
 
+def test_fp64_config1_5000_steps_drag_nusselt_mass_balance():
+    """The 128x64 channel with the heated disc over the configuration's 5000
+    steps: fields within 1e-10 of the oracle, and the diagnostics -- drag on
+    the disc, heat from the disc, fluid mass, summed boundary fluxes, outlet
+    mixing-cup temperature -- within 1e-10, hence the drag coefficient
+    Cd = 2 F_x / (rho u_mean^2 D), the Nusselt number Nu = Q / (pi lambda
+    (T_s - T_in)) and the mass-balance residual (mass change minus net
+    inflow) of the GPU run equal the oracle's."""
+    p = I.config1()
+    f = I.with_initial_u(p, I.config1_fields(p))
+    O.set_threads(0)
+    ora = O.OracleState(p, f["phi"], f["T"], u=f["u"])
+    dom = Domain(p, "fp64")
+    dom.set_phase_field(f["phi"])
+    dom.set_fields(f["T"], None, f["u"])
+    d0, o0 = dom.diagnostics(), ora.diagnostics()
+    for _ in range(5):
+        ora.step(1000)
+        dom.step(1000)
+    got = dom.get("T", "g", "u")
+    u, _, _ = ora.moments()
+    for k, ref in (("T", ora.T), ("g", ora.g.reshape(9, -1)), ("u", u)):
+        assert maxrel(got[k], ref) <= FP64_TOL, k
+    dg, do = dom.diagnostics(), ora.diagnostics()
+    assert dg["step"] == 5000
+    for k in ("heat", "mass", "outlet_Tm", "flux_in_total", "flux_out_total"):
+        assert abs(dg[k] - do[k]) <= FP64_TOL * abs(do[k]), k
+    assert np.max(np.abs(dg["drag"] - do["drag"])) <= FP64_TOL * np.max(np.abs(do["drag"]))
+    u_mean, D, lam = 2.0 / 3.0 * p["u_in"], 16.0, (p["mu_ref"] / p["rho_ref"]) * p["cp0"] / p["Pr"]
+    res = {}
+    for name, d, d_0 in (("gpu", dg, d0), ("oracle", do, o0)):
+        res[name] = {"Cd": 2.0 * d["drag"][0] / (u_mean ** 2 * D),
+                     "Nu": d["heat"] / (np.pi * lam * (p["Ts_uniform"] - p["T_in"])),
+                     "mass_residual": (d["mass"] - d_0["mass"]) -
+                                      (d["flux_in_total"] - d["flux_out_total"])}
+    print("config1 after 5000 steps:", res)
+    for k in ("Cd", "Nu"):
+        assert res["gpu"][k] > 0 and abs(res["gpu"][k] / res["oracle"][k] - 1) <= FP64_TOL
+    assert abs(res["gpu"]["mass_residual"] - res["oracle"]["mass_residual"]) <= \
+        FP64_TOL * do["mass"]
+
+
 def test_fp64_ragged_2d_walls_random_state():
     p = small_case(2, 61, 37, bc=["inlet", "outlet", "wall", "wall", "periodic", "periodic"],
                    A_u=80.0, A_T=60.0, eta=3.0, inlet_parabolic=1, u_in=0.03,
@@ -209,7 +251,8 @@ def test_fp16_storage_decodes_populations():
             st = d.get_state()
         d.close()
     N, Q = p["nx"] * p["ny"], 9
-    off = 64 + 104
+    # from the end: Ts, Y (5 species), T (floats), moments, residuals
+    off = st.nbytes - 4 * N * (1 + 5 + 1) - 4 * 3 * N - 2 * Q * N
     h = np.frombuffer(st[off:off + 2 * Q * N].tobytes(), dtype=np.float16).astype(np.float64)
     off += 2 * Q * N
     M = np.frombuffer(st[off:off + 4 * 3 * N].tobytes(), dtype=np.float32).astype(np.float64)

@@ -525,3 +525,65 @@ def test_species_diffusivity_power_law():
     for T0 in (300.0, 450.0, 600.0):
         D = _species_mode_D(T0)
         assert np.allclose(D, 0.02 * (T0 / 300.0) ** 1.7, rtol=1e-11, atol=0), (T0, D)
+
+
+# --------------------------------------------------------------- diagnostics
+def test_drag_diagnostic_balances_the_body_force():
+    """Periodic box with a uniform solid fraction driven by a body force: at
+    steady state the drag on the solid phase, sum K_d u, equals the total
+    body force N F_b (momentum balance), whatever K_d is."""
+    nx, ny = 6, 5
+    Fb = 2e-6
+    p = small(2, nx, ny, bc=["periodic"] * 6, nu=0.1, A_u=40.0, eta=2.0, Fb=[Fb, 0, 0])
+    phi = np.full(nx * ny, 0.3)
+    s = O.OracleState(p, phi, np.full(nx * ny, 300.0))
+    s.step(3000)
+    d = s.diagnostics()
+    assert abs(d["drag"][0] / (nx * ny * Fb) - 1) < 1e-9
+    assert abs(d["drag"][1]) < 1e-12 * nx * ny * Fb + 1e-20
+
+
+def test_heat_diagnostic_is_the_fluid_energy_change():
+    """At rest in a periodic box with the solid held at Ts (no species, fixed
+    P0), the conduction fluxes cancel in the sum, so one step changes the
+    fluid energy sum phi_f rho cp dT by exactly the heat diagnostic
+    sum phi_f S_I of the state before the step."""
+    nx, ny = 9, 7
+    p = small(2, nx, ny, bc=["periodic"] * 6, nu=0.05, A_T=60.0, eta=3.0, Ts_uniform=500.0)
+    rng = np.random.default_rng(8)
+    N = nx * ny
+    phi = rng.uniform(0.05, 0.9, N)
+    T = rng.uniform(300, 450, N)
+    s = O.OracleState(p, phi, T)
+    d = s.diagnostics()
+    Tn, _, _ = O.fd_phase(p, phi, T, None, None, np.zeros((2, N)), p["P0"], p["P0"])
+    rho = p["P0"] * p["M0"] / (8.314 * T * p["rho_ref"])
+    dE = np.sum((1 - phi) * rho * p["cp0"] * (Tn - T))
+    assert d["heat"] > 0 and abs(dE / d["heat"] - 1) < 1e-12
+
+
+def test_mass_diagnostic_is_conserved_in_a_closed_box():
+    """Closed box, heat release from a hot spot: P0 follows the closure
+    (Sec. 3.1), so the fluid mass sum phi_f rho stays at its initial value
+    while T and P0 change."""
+    nx, ny = 12, 8
+    p = small(2, nx, ny, bc=["periodic"] * 6, nu=0.05, A_T=20.0, eta=3.0, Ts_uniform=700.0,
+              p0_mode="closed")
+    rng = np.random.default_rng(9)
+    phi = 0.4 * rng.uniform(0, 1, nx * ny) ** 3
+    s = O.OracleState(p, phi, np.full(nx * ny, 300.0))
+    m0 = s.diagnostics()["mass"]
+    s.step(200)
+    assert abs(s.P0 / p["P0"] - 1) > 1e-4
+    assert abs(s.diagnostics()["mass"] / m0 - 1) < 1e-12
+
+
+def test_outlet_mixing_cup_temperature_of_a_uniform_stream():
+    """Sec. 4.2, eq. Tmean-def: a uniform-temperature stream has T_m = T."""
+    p = I.config1(nx=40, ny=20)
+    p["Ts_uniform"] = 300.0
+    phi = np.zeros(40 * 20)
+    f = I.with_initial_u(p, {"phi": phi, "T": np.full(800, 300.0), "Y": None, "Ts": None})
+    s = O.OracleState(p, phi, f["T"], u=f["u"])
+    s.step(20)
+    assert abs(s.diagnostics()["outlet_Tm"] - 300.0) < 1e-9
