@@ -3,7 +3,9 @@
 Headline workload: the 3-D reactive particle bed, 256 x 128 x 128 D3Q19,
 5 species with the one-step CH4 chemistry, transported solid temperature,
 138 seeded ellipsoids (synthetic stand-in for the paper's packed beds), FP32
-compute with the populations stored as selected by --precision.  A step is one
+compute and storage by default (--precision selects FP16-stored residuals or
+FP64); the step kernel is the one the library's autotuner picks for the
+domain.  A step is one
 pass of the whole hot path: pull collide-stream with drag, FD transport of
 T / Y / Ts, Arrhenius source, FP64 P0 / mass reduction -- one fused kernel
 launch.  The working set (>= 0.5 GB) is larger than the 129 MB L2, so no flush
@@ -40,8 +42,9 @@ sys.path.insert(0, ROOT)
 from paper_2310_17214_gb300 import inputs as I  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20
-KERNEL_SRC = os.path.join(ROOT, "paper_2310_17214_gb300", "csrc", "pflb_kernels.cuh")
-DEFAULT_PRECISION = "fp32_fp16"
+KERNEL_SRC = [os.path.join(ROOT, "paper_2310_17214_gb300", "csrc", f)
+              for f in ("pflb_kernels.cuh", "pflb_step3d.cuh")]
+DEFAULT_PRECISION = "fp32"
 METRIC = "MLUPS of the fused PF-LB-FD step (3-D D3Q19 reactive bed 256x128x128)"
 
 
@@ -69,11 +72,12 @@ def measured_peaks():
 
 
 def kernel_hash():
-    """Identity of the step kernel's build: its source and the compiler flags."""
+    """Identity of the step kernels' build: their sources and the compiler flags."""
     from paper_2310_17214_gb300 import build as B
     h = hashlib.sha256()
-    with open(KERNEL_SRC, "rb") as f:
-        h.update(f.read())
+    for src in KERNEL_SRC:
+        with open(src, "rb") as f:
+            h.update(f.read())
     h.update(" ".join(B.ARCH + B.FLAGS[:-2]).encode())  # the include path is machine-specific
     return h.hexdigest()[:16]
 
@@ -313,11 +317,23 @@ def crop_problem(prob, fields, ncols):
 
 
 # --------------------------------------------------------------------- GPU arm
-def make_domain(prob, fields, precision, dev, stream):
+KERNEL_FN = {"tiled": "step_kernel", "march": "step3d_march_kernel<prefetch=false>",
+             "march_prefetch": "step3d_march_kernel<prefetch=true>", "tma": "step_tma_kernel",
+             "persistent": "step_persistent_kernel<32x8>",
+             "persistent_32x16": "step_persistent_kernel<32x16>"}
+
+
+def make_domain(prob, fields, precision, dev, stream, tune=False):
+    """A domain of the workload with its fields set; with `tune`, the step
+    kernel the library's autotuner picks (state restored afterwards)."""
     from paper_2310_17214_gb300._native import Domain
     dom = Domain(prob, precision, stream=stream, device=dev.index)
     dom.set_phase_field(fields["phi"], fields["Ts"])
     dom.set_fields(fields["T"], fields["Y"])
+    dom.tuned = None
+    if tune:
+        chosen, table = dom.autotune(10)
+        dom.tuned = {"chosen": chosen, "us_per_step": table}
     return dom
 
 
@@ -386,7 +402,7 @@ def errors_vs_fp64(prob, fields, steps, dev, precisions):
     st = torch.cuda.current_stream(dev)
     out = {}
     for prec in ("fp64",) + tuple(precisions):
-        dom = make_domain(prob, fields, prec, dev, st.cuda_stream)
+        dom = make_domain(prob, fields, prec, dev, st.cuda_stream, tune=True)
         dom.step(steps)
         out[prec] = dom.get("T", "Y", "Ts", "u")
         dom.close()
@@ -575,7 +591,8 @@ def main():
     N = fields["phi"].size
     peaks, peak_kind = measured_peaks()
 
-    dom = make_domain(prob, fields, args.precision, dev, st.cuda_stream)
+    dom = make_domain(prob, fields, args.precision, dev, st.cuda_stream, tune=True)
+    tuned = dom.tuned
     ms, wall, clk = time_steps(dom, args.steps, args.warmup, dev, st, pg=pg, clocks=(rank == 0))
     final_step = dom.scalars()["step"]
     dom.close()
@@ -587,7 +604,7 @@ def main():
     achieved = bpc * N / per_launch / 1e9
     workload = workload_name(prob)
     kname = {"fp32": "float,float", "fp32_fp16": "float,__half", "fp64": "double,double"}
-    kernel = f"step_kernel<3,5,{kname[args.precision]}>"
+    kernel = f"{KERNEL_FN[tuned['chosen']]} (3-D, K=5, {kname[args.precision]})"
 
     extra = {}
     if not args.quick and rank == 0:
@@ -596,18 +613,19 @@ def main():
         for prec in ("fp32", "fp32_fp16", "fp64"):
             if prec == args.precision:
                 continue
-            d = make_domain(prob, fields, prec, dev, st.cuda_stream)
+            d = make_domain(prob, fields, prec, dev, st.cuda_stream, tune=True)
             n = 10 if prec == "fp64" else 50
             m, _, _ = time_steps(d, n, 3, dev, st)
+            tl = d.tuned
             d.close()
             t = sum(m) / len(m) / 1e3
             b = alg_bytes_per_cell(prob, prec)
             legs[prec] = {"ms_per_step": t * 1e3, "mlups": N / t / 1e6,
                           "alg_bytes_per_cell": b, "achieved_gbs": b * N / t / 1e9,
-                          "hbm_frac": b * N / t / 1e9 / peaks["hbm_gbs"]}
+                          "hbm_frac": b * N / t / 1e9 / peaks["hbm_gbs"], "autotune": tl}
         legs[args.precision] = {"ms_per_step": per_launch * 1e3, "mlups": N / per_launch / 1e6,
                                 "alg_bytes_per_cell": bpc, "achieved_gbs": achieved,
-                                "hbm_frac": achieved / peaks["hbm_gbs"]}
+                                "hbm_frac": achieved / peaks["hbm_gbs"], "autotune": tuned}
         # the FP64 step is bound by the FP64 pipe: its roofline is the probed FMA rate
         from paper_2310_17214_gb300._native import probe_fp64_tflops
         peak64 = probe_fp64_tflops(dev.index)

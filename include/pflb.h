@@ -281,8 +281,10 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where);
 #define PFLB_KERNEL_MARCH_PREFETCH 5
 #define PFLB_KERNELS 6
 
-/* Select the step kernel of a domain (after pflb_set_fields).  Returns
- * PFLB_ERR_UNSUPPORTED if the kernel cannot run this domain. */
+/* Select the step kernel of a domain (after pflb_set_fields).  The default is
+ * PFLB_KERNEL_MARCH for 3-D domains with FP32 storage, PFLB_KERNEL_TILED
+ * otherwise.  Returns PFLB_ERR_UNSUPPORTED if the kernel cannot run this
+ * domain. */
 int pflb_select_kernel(pflb_domain* d, int kernel);
 
 /* Bound, in SM clock cycles, of the device-side waits of this domain's

@@ -576,128 +576,132 @@ __device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, const int xyz[
   return u;
 }
 
-// Pull streaming of every population into the cell, with the boundary rules:
-// half-way bounce-back on walls (moving walls add 2 w rho c.u_w), the inlet
-// as a moving wall with the inlet velocity and inlet density, the outlet as
-// anti-bounce-back at P_h = 0 with wall velocity uw.
-// Lattice tables for the rolled boundary path of the pull (same order as
-// Lattice<DIM>).
-struct LatTab {
-  int c[19][3];
-  int opp[19];
-  float w[19];
-};
-template <int DIM>
-__host__ __device__ constexpr LatTab lat_tab() {
-  LatTab t{};
-  for (int i = 0; i < Lattice<DIM>::Q; ++i) {
-    for (int a = 0; a < 3; ++a) t.c[i][a] = Lattice<DIM>::c(i, a);
-    t.opp[i] = Lattice<DIM>::opp(i);
-    t.w[i] = float(Lattice<DIM>::w(i));
-  }
-  return t;
-}
-static __constant__ LatTab c_lat2 = lat_tab<2>();
-static __constant__ LatTab c_lat3 = lat_tab<3>();
-
-// First-order part of direction (cx, cy, cz) with weight w at runtime.
-template <int DIM, class Real, class MA>
-__device__ __forceinline__ Real first_order_rt(const MA& A, const int* cv, Real w, int src, int dx,
-                                               int dy, int dz) {
-  Real cj = 0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a)
-    if (cv[a] != 0) cj += Real(cv[a]) * A.mom(1 + a, src, dx, dy, dz);
-  return w * (A.mom(0, src, dx, dy, dz) + Real(3) * cj);
-}
-
-// Boundary path of the pull for one cell on a domain face: a rolled loop over
-// the directions (one copy of the code) writing ge[]; the rules: periodic
-// wrap; half-way bounce-back on walls (moving walls add 2 w rho c.u_w); the
-// inlet as a moving wall with the inlet velocity and inlet density; the
-// outlet as anti-bounce-back at P_h = 0 with wall velocity uw.
+// The cell's own post-collision population of direction ib (bounce-back).
 template <int DIM, class Real, class Store, int K, class MA>
-__device__ __noinline__ void pull_edge(const Params<Real, K>& P, const State<Real, Store>& S, int c,
-                                       const int* xyz, Real rho_c, Real rho_in, const Real* uw,
-                                       Real* ge, const MA& mom) {
-  constexpr bool FO = IsHalf<Store>::value;
-  const LatTab& L = DIM == 2 ? c_lat2 : c_lat3;
-  const Real u_inl = inlet_u(P, xyz, DIM);
-#pragma unroll 1
-  for (int i = 0; i < Lattice<DIM>::Q; ++i) {
-    const int* cv = L.c[i];
-    int sx[3] = {xyz[0] - cv[0], xyz[1] - cv[1], DIM == 3 ? xyz[2] - cv[2] : 0};
-    int wall = -1;
-    bool inlet = false, outlet = false;
+__device__ __forceinline__ Real own_pop(const Params<Real, K>& P, const State<Real, Store>& S,
+                                        int c, int ib, const MA& mom) {
+  const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)ib * P.N + c);
+  if constexpr (IsHalf<Store>::value)
+    return Codec<Store, Real>::dec(r, Real(Lattice<DIM>::w(ib)) * P.g_inv_scale,
+                                   first_order<DIM, Real>(mom, ib, c, 0, 0, 0));
+  else return r;
+}
+
+// Half-way bounce-back with the wall velocity for the directions entering
+// through face F, when the cell lies on it (on) and it is a wall.
+template <int DIM, int F, class Real, class Store, int K, class MA>
+__device__ __forceinline__ void wall_pops(const Params<Real, K>& P, const State<Real, Store>& S,
+                                          int c, bool on, Real rho_c, Real* gin, const MA& mom) {
+  using L = Lattice<DIM>;
+  constexpr int a = F >> 1, s = (F & 1) ? -1 : 1;
+  if (!(on && P.bc[F] == BC_WALL)) return;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
-      if (sx[a] < 0 || sx[a] >= n) {
-        const int face = 2 * a + (sx[a] >= n ? 1 : 0);
-        const int bc = P.bc[face];
-        if (bc == BC_PERIODIC) sx[a] = sx[a] < 0 ? sx[a] + n : sx[a] - n;
-        else if (bc == BC_WALL) { if (wall < 0) wall = face; }
-        else if (bc == BC_INLET) inlet = true;
-        else outlet = true;
-      }
-    }
-    const Real w = Real(L.w[i]);
-    if (wall >= 0 || inlet || outlet) {
-      const int ib = L.opp[i];
-      const Real wb = Real(L.w[ib]);
-      const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)ib * P.N + c);
-      Real own;
-      if constexpr (FO) own = Codec<Store, Real>::dec(r, wb * P.g_inv_scale,
-                                                      first_order_rt<DIM, Real>(mom, L.c[ib], wb, c, 0, 0, 0));
-      else own = r;
-      Real cu = 0, uu = 0;
+  for (int i = 0; i < L::Q; ++i) {
+    if (L::c(i, a) != s) continue;
+    Real cu = 0;
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const Real ub = wall >= 0 ? P.wall_u[wall][a] : (outlet ? uw[a] : (a == 0 ? u_inl : Real(0)));
-        cu += Real(cv[a]) * ub;
-        uu += ub * ub;
-      }
-      if (outlet) ge[i] = -own + w * rho_c * (Real(3) * cu * cu - uu);
-      else ge[i] = own + Real(2) * w * (inlet ? rho_in : rho_c) * cu;
-    } else {
-      const int src = sx[0] + P.nx * (sx[1] + P.ny * sx[2]);
-      const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)i * P.N + src);
-      // a periodic source: the staged halo holds its image at the same offset
-      if constexpr (FO)
-        ge[i] = Codec<Store, Real>::dec(r, w * P.g_inv_scale,
-                                        first_order_rt<DIM, Real>(mom, cv, w, src, -cv[0], -cv[1],
-                                                                  DIM == 3 ? -cv[2] : 0));
-      else ge[i] = r;
-    }
+    for (int b = 0; b < DIM; ++b) cu += Real(L::c(i, b)) * P.wall_u[F][b];
+    gin[i] = own_pop<DIM, Real, Store>(P, S, c, L::opp(i), mom) +
+             Real(2) * Real(L::w(i)) * rho_c * cu;
   }
 }
 
-// Pull streaming of every population into the cell: interior cells read the
-// 19 (9) upstream neighbours; cells on a domain face take the boundary path.
+// Pull streaming of every population into the cell.  A cell off every face
+// reads its upstream neighbours at fixed offsets.  On a face, along each axis
+// the upstream neighbour coordinate wraps across a periodic face and is
+// clamped to the cell itself across any other face; every direction is read
+// from there.  Directions that cross a non-periodic face are then replaced by the
+// boundary rules, in the order outlet, inlet, walls (the wall of the lowest
+// axis last, so it wins on edges and corners): half-way bounce-back on walls
+// (moving walls add 2 w rho c.u_w), the inlet as a moving wall with the inlet
+// velocity and inlet density, the outlet as anti-bounce-back at P_h = 0 with
+// wall velocity uw.
 template <int DIM, class Real, class Store, int K, class MA>
 __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real, Store>& S, int c,
-                                     const int xyz[3], bool edge, Real rho_c, Real rho_in,
-                                     const Real* uw, Real* gin, const MA& mom) {
+                                     const int xyz[3], Real rho_c, Real rho_in, const Real* uw,
+                                     Real* gin, const MA& mom) {
   using L = Lattice<DIM>;
   constexpr bool FO = IsHalf<Store>::value;  // residual storage: add the first-order part
-  if (edge) {
-    Real ge[L::Q];
-    pull_edge<DIM, Real, Store, K>(P, S, c, xyz, rho_c, rho_in, uw, ge, mom);
+  // cells off every domain face: fixed offsets from the cell (the common case)
+  const bool inner = xyz[0] > 0 && xyz[0] < P.nx - 1 && xyz[1] > 0 && xyz[1] < P.ny - 1 &&
+                     (DIM == 2 || (xyz[2] > 0 && xyz[2] < P.nz - 1));
+  if (inner) {
+    const int sy = P.nx, sz = P.nx * P.ny;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) gin[i] = ge[i];
+    for (int i = 0; i < L::Q; ++i) {
+      const int cx = L::c(i, 0), cy = L::c(i, 1), cz = DIM == 3 ? L::c(i, 2) : 0;
+      const int src = c - cx - cy * sy - cz * sz;
+      const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)i * P.N + src);
+      if constexpr (FO)
+        gin[i] = Codec<Store, Real>::dec(r, Real(L::w(i)) * P.g_inv_scale,
+                                         first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz));
+      else gin[i] = r;
+    }
     return;
   }
-  const int sy = P.nx, sz = P.nx * P.ny;
+  // upstream neighbour coordinates along each axis: m (coordinate - 1) and
+  // p (coordinate + 1), wrapped across periodic faces, clamped otherwise
+  const int x = xyz[0], y = xyz[1], z = DIM == 3 ? xyz[2] : 0;
+  const bool per0 = P.bc[0] == BC_PERIODIC, per1 = P.bc[1] == BC_PERIODIC;
+  const bool per2 = P.bc[2] == BC_PERIODIC, per3 = P.bc[3] == BC_PERIODIC;
+  const bool per4 = P.bc[4] == BC_PERIODIC, per5 = P.bc[5] == BC_PERIODIC;
+  const int xm = x > 0 ? x - 1 : (per0 ? P.nx - 1 : x);
+  const int xp = x < P.nx - 1 ? x + 1 : (per1 ? 0 : x);
+  const int ym = y > 0 ? y - 1 : (per2 ? P.ny - 1 : y);
+  const int yp = y < P.ny - 1 ? y + 1 : (per3 ? 0 : y);
+  const int zm = DIM == 3 ? (z > 0 ? z - 1 : (per4 ? P.nz - 1 : z)) : 0;
+  const int zp = DIM == 3 ? (z < P.nz - 1 ? z + 1 : (per5 ? 0 : z)) : 0;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = DIM == 3 ? L::c(i, 2) : 0;
-    const int src = c - cx - cy * sy - cz * sz;
+    const int sx = cx > 0 ? xm : (cx < 0 ? xp : x);
+    const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
+    const int sz = cz > 0 ? zm : (cz < 0 ? zp : z);
+    const int src = sx + P.nx * (sy + P.ny * sz);
     const Real r = Codec<Store, Real>::raw(S.g_in + (size_t)i * P.N + src);
+    // a periodic source: the staged halo holds its image at the same offset
     if constexpr (FO)
       gin[i] = Codec<Store, Real>::dec(r, Real(L::w(i)) * P.g_inv_scale,
                                        first_order<DIM, Real>(mom, i, src, -cx, -cy, -cz));
     else gin[i] = r;
   }
+  // non-periodic faces the cell lies on
+  const bool f0 = x == 0 && !per0, f1 = x == P.nx - 1 && !per1;
+  const bool f2 = y == 0 && !per2, f3 = y == P.ny - 1 && !per3;
+  const bool f4 = DIM == 3 && z == 0 && !per4, f5 = DIM == 3 && z == P.nz - 1 && !per5;
+  if (!(f0 || f1 || f2 || f3 || f4 || f5)) return;
+  if (f1 && P.bc[1] == BC_OUTLET) {
+    Real uu = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) uu += uw[a] * uw[a];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (L::c(i, 0) != -1) continue;
+      Real cu = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) cu += Real(L::c(i, a)) * uw[a];
+      gin[i] = -own_pop<DIM, Real, Store>(P, S, c, L::opp(i), mom) +
+               Real(L::w(i)) * rho_c * (Real(3) * cu * cu - uu);
+    }
+  }
+  if (f0 && P.bc[0] == BC_INLET) {
+    const Real ui = inlet_u(P, xyz, DIM);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+      if (L::c(i, 0) != 1) continue;
+      gin[i] = own_pop<DIM, Real, Store>(P, S, c, L::opp(i), mom) +
+               Real(2) * Real(L::w(i)) * rho_in * ui;
+    }
+  }
+  // walls, the highest axis first so that the lowest axis wins on edges
+  if (DIM == 3) {
+    wall_pops<DIM, 5>(P, S, c, f5, rho_c, gin, mom);
+    wall_pops<DIM, 4>(P, S, c, f4, rho_c, gin, mom);
+  }
+  wall_pops<DIM, 3>(P, S, c, f3, rho_c, gin, mom);
+  wall_pops<DIM, 2>(P, S, c, f2, rho_c, gin, mom);
+  wall_pops<DIM, 1>(P, S, c, f1, rho_c, gin, mom);
+  wall_pops<DIM, 0>(P, S, c, f0, rho_c, gin, mom);
 }
 
 // ----------------------------------------------------------- reductions
@@ -1003,16 +1007,19 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
 
 // Staged-plane accessor: own and neighbour values of the staged fields and
 // properties (the populations come from global memory).
-template <int DIM, class Real, bool PRE = false, class TL = Tile<DIM>, int MF = 0>
+template <int DIM, class Real, bool PRE = false, class TL = Tile<DIM>, int MF = 0,
+          bool STASH = false>
 struct PlaneAcc {
   static constexpr int HP = TL::HP;
   static constexpr bool has_pops = PRE;  // populations prefetched into registers
-  static constexpr bool wrap_pops = false;  // ... for cells off every domain face only
+  static constexpr bool kStash = STASH;  // pulled populations wait in shared memory
   const Real* __restrict__ cen;
   const Real* __restrict__ zm;
   const Real* __restrict__ zp;
   int h;
   const Real* pre;
+  bool pv;  // pre holds this cell's populations
+  Real* st; // stash, [Q][BLOCK] (STASH)
   __device__ __forceinline__ Real c(int f) const { return cen[f * HP + h]; }
   __device__ __forceinline__ Real n(int f, int a, int s) const {
     if (a == 0) return cen[f * HP + h + s];
@@ -1060,19 +1067,12 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const Real Kd = P.Au_eta2 * mu * phif * phis * phis;
   const Real invT = fdiv(Real(1), T0);
 
-  // cells whose pull needs the boundary rules; with pops prefetched across
-  // periodic faces (Acc::wrap_pops) only the non-periodic faces count
-  bool edge;
-  if constexpr (Acc::wrap_pops) {
-    edge = (xyz[0] == 0 && P.bc[0] != BC_PERIODIC) || (xyz[0] == P.nx - 1 && P.bc[1] != BC_PERIODIC) ||
-           (xyz[1] == 0 && P.bc[2] != BC_PERIODIC) || (xyz[1] == P.ny - 1 && P.bc[3] != BC_PERIODIC);
-    if (DIM == 3)
-      edge = edge || (xyz[2] == 0 && P.bc[4] != BC_PERIODIC) ||
-             (xyz[2] == P.nz - 1 && P.bc[5] != BC_PERIODIC);
-  } else {
-    edge = xyz[0] == 0 || xyz[0] == P.nx - 1 || xyz[1] == 0 || xyz[1] == P.ny - 1;
-    if (DIM == 3) edge = edge || xyz[2] == 0 || xyz[2] == P.nz - 1;
-  }
+  // cells on a non-periodic face (their pull takes the boundary rules)
+  bool edge = (xyz[0] == 0 && P.bc[0] != BC_PERIODIC) || (xyz[0] == P.nx - 1 && P.bc[1] != BC_PERIODIC) ||
+              (xyz[1] == 0 && P.bc[2] != BC_PERIODIC) || (xyz[1] == P.ny - 1 && P.bc[3] != BC_PERIODIC);
+  if (DIM == 3)
+    edge = edge || (xyz[2] == 0 && P.bc[4] != BC_PERIODIC) ||
+           (xyz[2] == P.nz - 1 && P.bc[5] != BC_PERIODIC);
 
   // (a1) pull streaming, moments, implicit drag
   Real rho_in = 0;
@@ -1088,7 +1088,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
   const Real inv_rk = fdiv(Real(1), rho + Real(0.5) * Kd);
   for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
-    if (Acc::has_pops && !edge) {
+    if (Acc::has_pops && A.pv) {  // populations prefetched for this cell
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         // prefetched values are raw stored numbers (scaled residuals with FP16)
@@ -1099,7 +1099,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
                                                                   DIM == 3 ? -L::c(i, 2) : 0));
       }
     } else {
-      pull<DIM>(P, S, c, xyz, edge, rho, rho_in, uw, gin, A);
+      pull<DIM>(P, S, c, xyz, rho, rho_in, uw, gin, A);
     }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -1111,6 +1111,16 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
       u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) * inv_rk;
       uw[a] = u[a];
     }
+  }
+  Real sg = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) sg += gin[i];
+
+  // the pulled populations are needed again only by the collision: with a
+  // stash they wait in shared memory instead of 9 / 19 registers
+  if constexpr (Acc::kStash) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) A.st[i * BLOCK + threadIdx.x] = gin[i];
   }
 
   const bool fluid_on = phif >= P.phi_min;
@@ -1218,9 +1228,6 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     G[a] = CS2 * Real(0.5) * (at(F_RHO, a, +1) - at(F_RHO, a, -1));
     F[a] = P.Fb[a] - Kd * u[a];
   }
-  Real sg = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) sg += gin[i];
   const Real Ph = sg + Real(0.5) * rho * CS2 * D;
   const Real omega = fdiv(Real(2) * rho, rho + Real(6) * mu);
   const Real src_w = Real(1) - Real(0.5) * omega;
@@ -1265,7 +1272,9 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     }
     const Real e = cu * (Real(3) + Real(4.5) * cu) - uu15;
     const Real x = (cH - uH) * e + (cF - uF);
-    Real g = keep * gin[i] + w * (A0 + B * e + src_w * x);
+    Real gi = gin[i];
+    if constexpr (Acc::kStash) gi = A.st[i * BLOCK + threadIdx.x];
+    Real g = keep * gi + w * (A0 + B * e + src_w * x);
     if constexpr (FO) g -= w * (Pst + Real(3) * cj);
     Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g, P.g_scale * Real(1.0 / L::w(i)));
   }
@@ -1326,11 +1335,15 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
     constexpr int RS = T_::TY / RPT;  // row stride between a thread's cells
     // population loads of the thread's interior cells, issued before staging
     Real pre[RPT][L::Q];
+    bool pv[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) pv[r] = false;
     if constexpr (T_::PREFETCH) {
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const int yr = y0 + ty + r * RS;
         const bool inner = x > 0 && x < P.nx - 1 && yr > 0 && yr < P.ny - 1;
+        pv[r] = inner;
         if (inner) {
           const int c = x + P.nx * yr;
 #pragma unroll
@@ -1351,7 +1364,8 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
         const int hr = (ty + r * RS + 1) * T_::HX + (tx + 1);
         Real fi, fo;
         const PlaneAcc<DIM, Real, T_::PREFETCH, T_, F_Y0 + K> A{&planes[0].f[0][0], nullptr,
-                                                                nullptr, hr, pre[r]};
+                                                                nullptr, hr, pre[r], pv[r],
+                                                                nullptr};
         accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
@@ -1369,9 +1383,10 @@ __device__ __forceinline__ void step_tile(const Params<Real, K>& P, const State<
         const int c = x + P.nx * (y + P.ny * z);
         const int xyz[3] = {x, y, z};
         Real fi, fo;
-        const PlaneAcc<DIM, Real, false, T_, F_Y0 + K> A{&planes[z % 3].f[0][0],
-                                               &planes[(z + 2) % 3].f[0][0],
-                                               &planes[(z + 1) % 3].f[0][0], h, nullptr};
+        const PlaneAcc<DIM, Real, false, T_, F_Y0 + K, true> A{
+            &planes[z % 3].f[0][0], &planes[(z + 2) % 3].f[0][0],
+            &planes[(z + 1) % 3].f[0][0], h, nullptr, false,
+            reinterpret_cast<Real*>(planes + T_::NPL)};
         accI += cell_update<DIM, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
         accOut += fo;
@@ -1449,9 +1464,11 @@ step_persistent_kernel(const Params<Real, K> P, const State<Real, Store> S, int 
   }
 }
 
+// staged planes, and in 3-D the stash of the pulled populations
 template <int DIM, int K, class Real, class Store, class T_ = Tile<DIM>>
 constexpr size_t step_smem_bytes() {
-  return sizeof(Plane<Real, K, T_::HP, n_mom<DIM, Store>()>) * T_::NPL;
+  return sizeof(Plane<Real, K, T_::HP, n_mom<DIM, Store>()>) * T_::NPL +
+         (DIM == 3 ? sizeof(Real) * Lattice<DIM>::Q * BLOCK : 0);
 }
 
 // ------------------------------------------- chemistry pre-pass (implicit)
@@ -1562,7 +1579,7 @@ moments_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __re
   const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
   Real gin[Q], u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
   for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
-    pull<DIM>(P, S, c, xyz, true, rho, rho_in, uw, gin, GlobalMom<Real>{S.M_in, P.N});
+    pull<DIM>(P, S, c, xyz, rho, rho_in, uw, gin, GlobalMom<Real>{S.M_in, P.N});
     for (int a = 0; a < DIM; ++a) {
       Real m = 0;
       for (int i = 0; i < Q; ++i) m += Real(L::c(i, a)) * gin[i];
@@ -1615,7 +1632,7 @@ diag_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __restr
     const bool outlet_cell = P.bc[1] == BC_OUTLET && xyz[0] == P.nx - 1;
     Real gin[Q], u[3] = {0, 0, 0}, uw[3] = {0, 0, 0};
     for (int pass = 0; pass < (outlet_cell ? 2 : 1); ++pass) {
-      pull<DIM>(P, S, c, xyz, true, rho, rho_in, uw, gin, GlobalMom<Real>{S.M_in, P.N});
+      pull<DIM>(P, S, c, xyz, rho, rho_in, uw, gin, GlobalMom<Real>{S.M_in, P.N});
       for (int a = 0; a < DIM; ++a) {
         Real m = 0;
         for (int i = 0; i < Q; ++i) m += Real(L::c(i, a)) * gin[i];

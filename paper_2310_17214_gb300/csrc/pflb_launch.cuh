@@ -298,7 +298,9 @@ struct LauncherImpl final : Launcher {
   const void* map_key[2][5] = {};
   int tma_state = 0;  // 0 unknown, 1 usable, -1 not usable
   int tma_grid = 0;
-  int kernel_sel = 0;
+  // default step kernel: the z-march for 3-D FP32 storage (fastest measured on
+  // the 3-D bed), the staged-tile kernel otherwise
+  int kernel_sel = (DIM == 3 && MODE == MODE_FP32) ? 4 : 0;
   long long wait_limit = kDefaultWaitCycles;
   void set_wait_limit(long long cycles) override { wait_limit = cycles; }
   SurrArgs surr;

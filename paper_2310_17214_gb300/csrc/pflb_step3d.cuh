@@ -35,7 +35,7 @@ __host__ __device__ constexpr int march_nf() { return G_Y0 + K + n_mom<3, Store>
 
 template <int K, class Real, class Store>
 constexpr size_t march_smem_bytes() {
-  return sizeof(Real) * 3 * march_nf<K, Store>() * Tile<3>::HP;
+  return sizeof(Real) * (3 * march_nf<K, Store>() * Tile<3>::HP + Lattice<3>::Q * BLOCK);
 }
 
 // Accessor of cell_update over the march's staged planes; mu and f_D are the
@@ -45,13 +45,15 @@ struct MarchAcc {
   using TL = Tile<3>;
   static constexpr int HP = TL::HP;
   static constexpr bool has_pops = PRE;
-  static constexpr bool wrap_pops = PRE;
+  static constexpr bool kStash = true;  // pulled populations wait in shared memory
   const Real* __restrict__ cen;
   const Real* __restrict__ zm;
   const Real* __restrict__ zp;
   int h;
   Real mu, fD;
   const Real* pre;
+  bool pv;  // pre holds this cell's populations
+  Real* st; // stash [Q][BLOCK]
   __device__ __forceinline__ Real c(int f) const {
     if (f == F_MU) return mu;
     if (f == F_FD) return fD;
@@ -222,13 +224,15 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
                                 z_begin - 1, P0);
     march_stage<Real, Store, K>(P, S, planes + (z_begin % 3) * NF * HP, x0, y0, z_begin, P0);
     Real pre[L::Q], nxt[L::Q];
+    bool have = false, have_nxt = false;
     if constexpr (PRE) {
-      if (in_xy) march_prefetch<Real, Store, K>(P, S, x, y, z_begin, pre);
+      if (in_xy) have = march_prefetch<Real, Store, K>(P, S, x, y, z_begin, pre);
     }
     for (int z = z_begin; z < z_end; ++z) {
       march_stage<Real, Store, K>(P, S, planes + ((z + 1) % 3) * NF * HP, x0, y0, z + 1, P0);
       if constexpr (PRE) {
-        if (in_xy && z + 1 < z_end) march_prefetch<Real, Store, K>(P, S, x, y, z + 1, nxt);
+        have_nxt = in_xy && z + 1 < z_end &&
+                   march_prefetch<Real, Store, K>(P, S, x, y, z + 1, nxt);
       }
       __syncthreads();
       if (in_xy) {
@@ -242,9 +246,9 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
         }
         const MarchAcc<Real, K, PRE> A{cen, planes + ((z + 2) % 3) * NF * HP,
                                        planes + ((z + 1) % 3) * NF * HP, h, viscosity(P, T0), fD,
-                                       pre};
+                                       pre, PRE && have, planes + 3 * NF * HP};
         // a cell that prefetched nothing lies on a non-periodic face: the
-        // update takes its boundary path of the pull (edge) there
+        // update pulls with the boundary rules there
         Real fi, fo;
         accI += cell_update<3, K, Real, Store>(P, S, A, c, xyz, P0, dlnP0, dP0r, fi, fo);
         accIn += fi;
@@ -254,6 +258,7 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
       if constexpr (PRE) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) pre[i] = nxt[i];
+        have = have_nxt;
       }
     }
   }

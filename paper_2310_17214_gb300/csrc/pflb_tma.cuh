@@ -138,11 +138,12 @@ template <int K, class Store>
 struct TmaAcc {
   using LY = TmaLayout<K, Store>;
   static constexpr bool has_pops = true;
-  static constexpr bool wrap_pops = false;
+  static constexpr bool kStash = false;
   const float* __restrict__ raw;
   const Store* __restrict__ pops;
   const float* __restrict__ der;
   int lx, ly;
+  bool pv;  // the stage's population windows are valid for this cell (off every face)
   __device__ __forceinline__ int ridx(int dx, int dy) const {
     return (ly + 1 + dy) * LY::FW + lx + LY::XL + dx;
   }
@@ -364,7 +365,7 @@ step_tma_kernel(const Params<float, K> P, const State<float, Store> S, int p0_cl
     const int x = x0 + lx, y = y0 + ly;
     if (x < P.nx && y < P.ny) {
       const TmaAcc<K, Store> A{raw, reinterpret_cast<const Store*>(stage[s] + LY::raw_bytes), der,
-                               lx, ly};
+                               lx, ly, x > 0 && x < P.nx - 1 && y > 0 && y < P.ny - 1};
       const int c = x + P.nx * y;
       const int xyz[3] = {x, y, 0};
       float fi, fo;
