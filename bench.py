@@ -216,8 +216,9 @@ def workload_name(prob):
     return f"reactive_bed_{prob['nx']}x{prob['ny']}_d2q9_k{prob['K']}"
 
 
-def config_of(prob, fields, precision):
-    return {"workload": workload_name(prob), "nx": prob["nx"], "ny": prob["ny"],
+def config_of(prob, fields, precision, world=1):
+    """The workload's config, identical in both arms of the benchmark."""
+    return {"parallelism": f"replicas x{world}" if world > 1 else "single device","workload": workload_name(prob), "nx": prob["nx"], "ny": prob["ny"],
             "nz": prob.get("nz", 1), "lattice": "D3Q19" if prob["dim"] == 3 else "D2Q9",
             "species": prob["K"], "particles": fields["info"]["placed"],
             "porosity_bed": round(fields["info"]["porosity_bed"], 3),
@@ -291,7 +292,7 @@ def run_reference(args, prob, fields, world, rank, pg):
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(prob, fields, args.precision),
+            "config": config_of(prob, fields, args.precision, world),
             "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -656,8 +657,7 @@ def main():
 
     if rank != 0:
         return
-    cfg = config_of(prob, fields, args.precision)
-    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    cfg = config_of(prob, fields, args.precision, world)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,

@@ -144,7 +144,20 @@ typedef struct pflb_mechanism {
   double dH[PFLB_JMAX], dS[PFLB_JMAX];    /* standard reaction enthalpy (J/mol), entropy (J/mol/K) */
   double rorder[PFLB_JMAX][PFLB_KMAX];    /* reverse orders */
   double p_ref;            /* standard pressure of K_c (Pa) */
+  /* Transport.  PFLB_TRANSPORT_SINGLE: the description's viscosity law
+   * (mu_ref, Sutherland) and lambda = mu cp / Pr for the whole mixture.
+   * PFLB_TRANSPORT_MIXTURE: mixture-averaged values (Sec. 4.4, eqs. muT_mix,
+   * phi_mix, conduct_mix) -- mu = sum_k mu_k X_k / sum_j Phi_kj X_j with
+   * Wilke's Phi_kj, lambda = (sum_k X_k lambda_k + 1 / sum_k X_k / lambda_k) / 2 --
+   * from the species' Sutherland laws mu_k(T) = mu_k (T / suth_Tk)^1.5
+   * (suth_Tk + suth_Sk) / (T + suth_Sk) and the modified Eucken relation
+   * lambda_k = mu_k (1.32 cv_k + 1.77 R / M_k), cv_k = cp_k - R / M_k. */
+  int transport;
+  double mu_k[PFLB_KMAX], suth_Tk[PFLB_KMAX], suth_Sk[PFLB_KMAX];
 } pflb_mechanism;
+
+#define PFLB_TRANSPORT_SINGLE 0
+#define PFLB_TRANSPORT_MIXTURE 1
 
 typedef struct pflb_scalars {
   double P0;               /* thermodynamic pressure at the current step (Pa) */

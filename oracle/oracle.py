@@ -54,6 +54,8 @@ class OrcParams(C.Structure):
         ("order", (C.c_double * KMAX) * JMAX), ("stoich", (C.c_double * KMAX) * JMAX),
         ("rev", C.c_int * JMAX), ("dH", C.c_double * JMAX), ("dS", C.c_double * JMAX),
         ("rorder", (C.c_double * KMAX) * JMAX), ("p_ref", C.c_double),
+        ("transport_mix", C.c_int), ("mu_k", C.c_double * KMAX),
+        ("suth_Tk", C.c_double * KMAX), ("suth_Sk", C.c_double * KMAX),
     ]
 
 
@@ -94,6 +96,8 @@ def lib():
         L.orc_step.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_void_p]
         L.orc_run.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_int]
         L.orc_diagnostics.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, dp]
+        L.orc_mixture_transport.argtypes = [P, C.c_double, dp, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_set_threads.restype = C.c_int
         _lib = L
@@ -161,6 +165,11 @@ def make_params(prob: dict) -> OrcParams:
             for k in range(K):
                 p.rorder[j][k] = r["reverse"]["order"][k]
     p.p_ref = prob.get("p_ref", 101325.0)
+    if prob.get("transport") == "mixture":
+        p.transport_mix = 1
+        for k in range(K):
+            p.mu_k[k], p.suth_Tk[k], p.suth_Sk[k] = prob["mu_k"][k], prob["suth_Tk"][k], \
+                prob["suth_Sk"][k]
     return p
 
 
@@ -279,6 +288,16 @@ def fd_phase(prob, phi, T, Y, Ts, u, P0, P0prev):
     lib().orc_fd_phase(C.byref(p), f64(phi), f64(T), Yin, _ptr(None if Ts is None else f64(Ts)),
                        f64(u), float(P0), float(P0prev), Tn, Yn, _ptr(Tsn))
     return Tn, (Yn[: K * N] if K > 0 else None), Tsn
+
+
+def mixture_transport(prob, T, Y):
+    """(mu, lambda) in SI units of a gas of composition Y at T, mixture rules."""
+    p = make_params(prob)
+    mu, lam = C.c_double(), C.c_double()
+    Yp = np.zeros(KMAX)
+    Yp[: prob["K"]] = Y
+    lib().orc_mixture_transport(C.byref(p), float(T), Yp, C.byref(mu), C.byref(lam))
+    return mu.value, lam.value
 
 
 def chem_implicit(prob, T, Y, rho_lat):

@@ -89,6 +89,13 @@ typedef struct {
   int rev[ORC_JMAX];
   double dH[ORC_JMAX], dS[ORC_JMAX], rorder[ORC_JMAX][ORC_KMAX];
   double p_ref;
+  /* mixture-averaged transport (Sec. 4.4, eqs. muT_mix, phi_mix, conduct_mix):
+   * species viscosities from Sutherland laws mu_k(T) = mu_k (T / Tk)^1.5
+   * (Tk + Sk) / (T + Sk), species conductivities from the modified Eucken
+   * relation lambda_k = mu_k (1.32 cv_k + 1.77 R / M_k), cv_k = cp_k - R / M_k;
+   * 0 = single gas (mu_ref, Pr) */
+  int transport_mix;
+  double mu_k[ORC_KMAX], suth_Tk[ORC_KMAX], suth_Sk[ORC_KMAX];
 } orc_params;
 
 /* ---------------------------------------------------------------- lattices */
@@ -191,12 +198,60 @@ static double visc(const orc_params* p, double T) {
   return mu * p->dt / (p->rho_ref * p->dx * p->dx);
 }
 
+/* Mixture-averaged viscosity and conductivity (physical units) of a gas of
+ * composition Y at T (Sec. 4.4): mole fractions X_k = Y_k Mw / M_k;
+ * mu = sum_k mu_k X_k / sum_j Phi_kj X_j with
+ * Phi_kj = (1 + sqrt(mu_k / mu_j sqrt(M_j / M_k)))^2 / (sqrt(8) sqrt(1 + M_k / M_j))
+ * (eqs. muT_mix, phi_mix); lambda = (sum_k X_k lambda_k + 1 / sum_k X_k / lambda_k) / 2
+ * (eq. conduct_mix). */
+void orc_mixture_transport(const orc_params* p, double T, const double* Y, double* mu_out,
+                           double* lam_out) {
+  int K = p->K;
+  double Mw = mixture_Mw(p, Y);
+  double X[ORC_KMAX], mu[ORC_KMAX], lam[ORC_KMAX];
+  for (int k = 0; k < K; ++k) {
+    X[k] = Y[k] * Mw / p->M[k];
+    mu[k] = p->mu_k[k] * pow(T / p->suth_Tk[k], 1.5) * (p->suth_Tk[k] + p->suth_Sk[k]) /
+            (T + p->suth_Sk[k]);
+    lam[k] = mu[k] * (1.32 * (p->cp[k] - ORC_R / p->M[k]) + 1.77 * ORC_R / p->M[k]);
+  }
+  double m = 0, l1 = 0, l2 = 0;
+  for (int k = 0; k < K; ++k) {
+    double den = 0;
+    for (int j = 0; j < K; ++j) {
+      double a = 1.0 + sqrt(mu[k] / mu[j] * sqrt(p->M[j] / p->M[k]));
+      double phi = a * a / (sqrt(8.0) * sqrt(1.0 + p->M[k] / p->M[j]));
+      den += phi * X[j];
+    }
+    m += mu[k] * X[k] / den;
+    l1 += X[k] * lam[k];
+    l2 += X[k] / lam[k];
+  }
+  *mu_out = m;
+  *lam_out = 0.5 * (l1 + 1.0 / l2);
+}
+
+/* lattice viscosity of a gas of composition Y at T */
+static double visc_of(const orc_params* p, double T, const double* Y) {
+  if (!(p->transport_mix && p->K > 0)) return visc(p, T);
+  double mu, lam;
+  orc_mixture_transport(p, T, Y, &mu, &lam);
+  return mu * p->dt / (p->rho_ref * p->dx * p->dx);
+}
+
 static void derive(const orc_params* p, const cellv* v, double P0, derv* d) {
   d->Mw = mixture_Mw(p, v->Y);
   d->rho = eos_rho(p, P0, d->Mw, v->T);
   d->cp = mixture_cp(p, v->Y);
-  d->mu = visc(p, v->T);
-  d->lam = d->mu * d->cp / p->Pr; /* Sec. 4, eq. lambdaT (lattice units) */
+  if (p->transport_mix && p->K > 0) {
+    double mu, lam, s = p->dt / (p->rho_ref * p->dx * p->dx);
+    orc_mixture_transport(p, v->T, v->Y, &mu, &lam);
+    d->mu = mu * s;
+    d->lam = lam * s;
+  } else {
+    d->mu = visc(p, v->T);
+    d->lam = d->mu * d->cp / p->Pr; /* Sec. 4, eq. lambdaT (lattice units) */
+  }
   for (int k = 0; k < p->K; ++k) {
     double D = p->Dref[k];
     if (p->D_exp != 0.0) D = p->Dref[k] * pow(v->T / p->D_Tref, p->D_exp);
@@ -633,7 +688,7 @@ static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, 
     double Yc[ORC_KMAX];
     for (int k = 0; k < p->K; ++k) Yc[k] = Y[(size_t)k * N + c];
     double r = eos_rho(p, P0, mixture_Mw(p, Yc), T[c]);
-    double mu = visc(p, T[c]);
+    double mu = visc_of(p, T[c], Yc);
     double phis = phi[c], phif = 1.0 - phis;
     double kd = p->A_u * mu * phif * phis * phis / eta2;
     double gin[ORC_QMAX], uw[3] = {0, 0, 0}, uc[3] = {0, 0, 0};

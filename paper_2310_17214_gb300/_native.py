@@ -51,6 +51,8 @@ class Mechanism(C.Structure):
         ("order", (C.c_double * KMAX) * JMAX), ("stoich", (C.c_double * KMAX) * JMAX),
         ("rev", C.c_int * JMAX), ("dH", C.c_double * JMAX), ("dS", C.c_double * JMAX),
         ("rorder", (C.c_double * KMAX) * JMAX), ("p_ref", C.c_double),
+        ("transport", C.c_int), ("mu_k", C.c_double * KMAX), ("suth_Tk", C.c_double * KMAX),
+        ("suth_Sk", C.c_double * KMAX),
     ]
 
 
@@ -206,6 +208,11 @@ def make_mechanism(prob: dict) -> Mechanism:
             for k in range(K):
                 m.rorder[j][k] = r["reverse"]["order"][k]
     m.p_ref = prob.get("p_ref", 101325.0)
+    if K and prob.get("transport") == "mixture":
+        m.transport = 1
+        for k in range(K):
+            m.mu_k[k], m.suth_Tk[k], m.suth_Sk[k] = prob["mu_k"][k], prob["suth_Tk"][k], \
+                prob["suth_Sk"][k]
     return m
 
 

@@ -208,7 +208,41 @@ int validate_mech(const pflb_mechanism& m, std::string& msg) {
     if (!(m.M[k] > 0 && m.cp[k] > 0 && m.Dref[k] >= 0))
       return bad(PFLB_ERR_ARG, "species data must be positive");
   if (m.K > 0 && m.D_exp != 0.0 && !(m.D_Tref > 0)) return bad(PFLB_ERR_ARG, "D_Tref must be > 0");
+  if (m.transport != PFLB_TRANSPORT_SINGLE && m.transport != PFLB_TRANSPORT_MIXTURE)
+    return bad(PFLB_ERR_ARG, "bad transport mode");
+  if (m.transport == PFLB_TRANSPORT_MIXTURE)
+    for (int k = 0; k < m.K; ++k)
+      if (!(m.mu_k[k] > 0 && m.suth_Tk[k] > 0 && m.suth_Sk[k] >= 0))
+        return bad(PFLB_ERR_ARG, "species viscosity laws must be positive");
   return PFLB_OK;
+}
+
+// Mixture-averaged viscosity and conductivity (SI) of composition Y at T, the
+// rules of the device's transport() in double precision.
+static void mixture_mu_lam(const pflb_mechanism& m, double T, const double* Y, double& mu,
+                           double& lam) {
+  double invMw = 0, X[PFLB_KMAX], mk[PFLB_KMAX], lk[PFLB_KMAX];
+  for (int k = 0; k < m.K; ++k) invMw += Y[k] / m.M[k];
+  for (int k = 0; k < m.K; ++k) {
+    X[k] = Y[k] / m.M[k] / invMw;
+    mk[k] = m.mu_k[k] * std::pow(T / m.suth_Tk[k], 1.5) * (m.suth_Tk[k] + m.suth_Sk[k]) /
+            (T + m.suth_Sk[k]);
+    const double RM = 8.314 / m.M[k];
+    lk[k] = mk[k] * (1.32 * (m.cp[k] - RM) + 1.77 * RM);
+  }
+  double s = 0, l1 = 0, l2 = 0;
+  for (int k = 0; k < m.K; ++k) {
+    double den = 0;
+    for (int j = 0; j < m.K; ++j) {
+      const double q = 1.0 + std::sqrt(mk[k] / mk[j]) * std::pow(m.M[j] / m.M[k], 0.25);
+      den += q * q / (std::sqrt(8.0) * std::sqrt(1.0 + m.M[k] / m.M[j])) * X[j];
+    }
+    s += mk[k] * X[k] / den;
+    l1 += X[k] * lk[k];
+    l2 += X[k] / lk[k];
+  }
+  mu = s;
+  lam = 0.5 * (l1 + 1.0 / l2);
 }
 
 int check_stability(const pflb_domain_desc& D, const pflb_mechanism* m, std::string& msg) {
@@ -233,10 +267,18 @@ int check_stability(const pflb_domain_desc& D, const pflb_mechanism* m, std::str
     const double T = temps[i];
     double mu = D.mu_ref;
     if (D.sutherland) mu *= std::pow(T / D.suth_T, 1.5) * (D.suth_T + D.suth_S) / (T + D.suth_S);
-    const double mu_lat = mu * h2 / D.rho_ref;
     const double rho_lat = D.P0 / (8.314 * T * invMw * D.rho_ref);
+    double a;  // lambda / (rho cp), lattice units
+    if (mix && m->transport == PFLB_TRANSPORT_MIXTURE) {
+      double lam, cp = 0;
+      mixture_mu_lam(*m, T, m->Y_in, mu, lam);
+      for (int k = 0; k < m->K; ++k) cp += m->Y_in[k] * m->cp[k];
+      a = lam * h2 / D.rho_ref / (rho_lat * cp);
+    } else {
+      a = mu * h2 / D.rho_ref / (rho_lat * D.Pr);
+    }
+    const double mu_lat = mu * h2 / D.rho_ref;
     const double tau = 0.5 + 3.0 * mu_lat / rho_lat;  // tau = 1/2 + nu / cs^2
-    const double a = mu_lat / (rho_lat * D.Pr);       // lambda / (rho cp), lattice units
     if (!(tau > 0.5) || !std::isfinite(tau)) {
       std::snprintf(buf, sizeof(buf), "relaxation time tau = %.6g <= 1/2 at T = %g K", tau, T);
       msg = buf;

@@ -146,6 +146,12 @@ struct Params {
   // FP64 copy of the chemistry for the implicit Newton integrator (FP64 in
   // every precision mode: the stiff chemistry keeps double precision)
   Chem64<K> c64;
+  // mixture-averaged transport (Sec. 4.4): species Sutherland laws (lattice
+  // units), modified Eucken factors, Wilke's constant factors
+  int mix;
+  Real mu_lat_k[KK], inv_suth_Tk[KK], suth_Sk[KK], suth_TSk[KK], eucken_k[KK];
+  Real wA[KK][KK];         // (M_j / M_k)^(1/4)
+  Real wB[KK][KK];         // 1 / (sqrt(8) sqrt(1 + M_k / M_j))
 };
 
 // Scalar state on the device.  The per-step quantities the cells need (P0,
@@ -255,6 +261,52 @@ __device__ __forceinline__ Real viscosity(const Params<Real, K>& P, Real T) {
   if (!P.sutherland) return P.mu_lat;
   Real t = T * P.inv_suth_T;
   return P.mu_lat * t * sqrt(t) * fdiv(P.suth_TS, T + P.suth_S);
+}
+
+// Viscosity and conductivity of the gas of composition Y at T (lattice
+// units).  Single-gas mode: the viscosity law above and lambda = mu cp / Pr.
+// Mixture mode (Sec. 4.4, eqs. muT_mix, phi_mix, conduct_mix): mole fractions
+// X_k = Y_k Mw / M_k, species viscosities from their Sutherland laws,
+// mu = sum_k mu_k X_k / sum_j Phi_kj X_j with
+// Phi_kj = (1 + sqrt(mu_k / mu_j) (M_j / M_k)^(1/4))^2 / (sqrt(8) sqrt(1 + M_k / M_j)),
+// lambda = (sum_k X_k lambda_k + 1 / sum_k X_k / lambda_k) / 2 with
+// lambda_k = mu_k (1.32 cv_k + 1.77 R / M_k).
+template <class Real, int K>
+__device__ __forceinline__ void transport(const Params<Real, K>& P, Real T, const Real* Y,
+                                          Real invMw, Real cp, Real& mu, Real& lam) {
+  if constexpr (K > 0) {
+    if (P.mix) {
+      Real X[K], m[K], sm[K], ism[K];
+      const Real Mw = fdiv(Real(1), invMw);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        X[k] = Y[k] * P.invM[k] * Mw;
+        const Real t = T * P.inv_suth_Tk[k];
+        m[k] = P.mu_lat_k[k] * t * sqrt(t) * fdiv(P.suth_TSk[k], T + P.suth_Sk[k]);
+        sm[k] = sqrt(m[k]);
+        ism[k] = fdiv(Real(1), sm[k]);
+      }
+      Real mm = 0, l1 = 0, l2 = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        Real den = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const Real a = Real(1) + sm[k] * ism[j] * P.wA[k][j];
+          den += a * a * P.wB[k][j] * X[j];
+        }
+        mm += m[k] * X[k] * fdiv(Real(1), den);
+        const Real lk = m[k] * P.eucken_k[k];
+        l1 += X[k] * lk;
+        l2 += X[k] * fdiv(Real(1), lk);
+      }
+      mu = mm;
+      lam = Real(0.5) * (l1 + fdiv(Real(1), l2));
+      return;
+    }
+  }
+  mu = viscosity(P, T);
+  lam = mu * cp * P.inv_Pr;
 }
 
 template <class Real, int K>
@@ -981,9 +1033,11 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
       }
     }
     const Real phif = Real(1) - phis;
-    const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
-    const Real mu = viscosity(P, T);
+    const Real invMw = mixture_invMw(P, Y);
+    const Real rho = fdiv(P0 * P.eos_cr, T * invMw);
     const Real cp = mixture_cp(P, Y);
+    Real mu, lam;
+    transport(P, T, Y, invMw, cp, mu, lam);
     Real fD = Real(1);
     if constexpr (K > 0) {
       if (P.D_Tdep) fD = fpow(T * P.inv_DTref, P.D_exp);
@@ -991,7 +1045,7 @@ __device__ __forceinline__ void stage_plane(const Params<Real, K>& P, const Stat
     pl.f[F_T][h] = T;
     pl.f[F_PHI][h] = phis;
     pl.f[F_RHO][h] = rho;
-    pl.f[F_KT][h] = phif * (mu * cp * P.inv_Pr);
+    pl.f[F_KT][h] = phif * lam;
     pl.f[F_MU][h] = mu;
     pl.f[F_FD][h] = fD;
     pl.f[F_TS][h] = Ts;
@@ -1126,7 +1180,9 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   const bool fluid_on = phif >= P.phi_min;
   const bool solid_on = P.Ts_field ? (phis >= P.phi_min) : true;
   Real SI = 0;
-  if (fluid_on && solid_on) SI = P.AT_eta2 * lam * phif * phis * phis * (Ts0 - T0);
+  if (fluid_on && solid_on)
+    SI = P.mix ? P.AT_eta2 * A.c(F_KT) * phis * phis * (Ts0 - T0)  // staged phi_f lambda
+               : P.AT_eta2 * lam * phif * phis * phis * (Ts0 - T0);
 
   // (c) reaction source
   Real om[KK], omT = 0;
@@ -1571,7 +1627,9 @@ moments_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __re
   for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
   const Real rho = P0 * Real(P.eos_c) / (T * mixture_invMw(P, Y));
   const Real phis = S.phi[c];
-  const Real Kd = P.Au_eta2 * viscosity(P, T) * (Real(1) - phis) * phis * phis;
+  Real mu_c, lam_c;
+  transport(P, T, Y, mixture_invMw(P, Y), mixture_cp(P, Y), mu_c, lam_c);
+  const Real Kd = P.Au_eta2 * mu_c * (Real(1) - phis) * phis * phis;
   Real Yin[KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) Yin[k] = P.Y_in[k];
@@ -1622,8 +1680,9 @@ diag_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __restr
     for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
     const Real rho = P0 * Real(P.eos_c) / (T * mixture_invMw(P, Y));
     const Real phis = S.phi[c], phif = Real(1) - phis;
-    const Real mu = viscosity(P, T);
     const Real cp = mixture_cp(P, Y);
+    Real mu, lam;
+    transport(P, T, Y, mixture_invMw(P, Y), cp, mu, lam);
     const Real Kd = P.Au_eta2 * mu * phif * phis * phis;
     Real Yin[KK];
 #pragma unroll
@@ -1645,7 +1704,7 @@ diag_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __restr
     const bool fluid_on = phif >= P.phi_min;
     const bool solid_on = P.Ts_field ? (phis >= P.phi_min) : true;
     if (fluid_on && solid_on)
-      v[3] = double(phif * (P.AT_eta2 * (mu * cp * P.inv_Pr) * phif * phis * phis * (Ts - T)));
+      v[3] = double(phif * (P.AT_eta2 * lam * phif * phis * phis * (Ts - T)));
     v[4] = double(phif * rho);
     if (outlet_cell) {
       v[5] = double(rho * u[0] * cp * T);

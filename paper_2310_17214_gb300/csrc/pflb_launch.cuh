@@ -226,6 +226,20 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
   // FP16 residual scale: residuals |r / w| from 4 down to 3.7e-9 (lattice
   // units) stay in the normal FP16 range; smaller ones keep an absolute
   // resolution of 3.6e-12 as subnormals
+  P.mix = (K > 0 && m.transport == PFLB_TRANSPORT_MIXTURE) ? 1 : 0;
+  for (int k = 0; k < K; ++k) {
+    const double sT = m.suth_Tk[k] > 0 ? m.suth_Tk[k] : 1.0;
+    P.mu_lat_k[k] = Real(m.mu_k[k] * h2 / d.rho_ref);
+    P.inv_suth_Tk[k] = Real(1.0 / sT);
+    P.suth_Sk[k] = Real(m.suth_Sk[k]);
+    P.suth_TSk[k] = Real(sT + m.suth_Sk[k]);
+    const double RM = R_GAS / m.M[k];
+    P.eucken_k[k] = Real(1.32 * (m.cp[k] - RM) + 1.77 * RM);
+    for (int j = 0; j < K; ++j) {
+      P.wA[k][j] = Real(std::pow(m.M[j] / m.M[k], 0.25));
+      P.wB[k][j] = Real(1.0 / (std::sqrt(8.0) * std::sqrt(1.0 + m.M[k] / m.M[j])));
+    }
+  }
   const float s = mode == MODE_FP16 ? 16384.0f : 1.0f;
   P.g_scale = Real(s);
   P.g_inv_scale = Real(1.0f / s);

@@ -123,9 +123,11 @@ __device__ __forceinline__ void march_stage(const Params<Real, K>& P, const Stat
       }
     }
     const Real phif = Real(1) - phis;
-    const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
-    const Real mu = viscosity(P, T);
+    const Real invMw = mixture_invMw(P, Y);
+    const Real rho = fdiv(P0 * P.eos_cr, T * invMw);
     const Real cp = mixture_cp(P, Y);
+    Real mu, lam;
+    transport(P, T, Y, invMw, cp, mu, lam);
     Real fD = Real(1);
     if constexpr (K > 0) {
       if (P.D_Tdep) fD = fpow(T * P.inv_DTref, P.D_exp);
@@ -133,7 +135,7 @@ __device__ __forceinline__ void march_stage(const Params<Real, K>& P, const Stat
     pl[G_T * HP + h] = T;
     pl[G_PHI * HP + h] = phis;
     pl[G_RHO * HP + h] = rho;
-    pl[G_KT * HP + h] = phif * (mu * cp * P.inv_Pr);
+    pl[G_KT * HP + h] = phif * lam;
     pl[G_TS * HP + h] = Ts;
     pl[G_RF * HP + h] = phif * rho * fD;
 #pragma unroll
@@ -244,8 +246,17 @@ step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_
         if constexpr (K > 0) {
           if (P.D_Tdep) fD = fpow(T0 * P.inv_DTref, P.D_exp);
         }
+        Real mu0 = viscosity(P, T0);
+        if constexpr (K > 0) {
+          if (P.mix) {  // mixture-averaged viscosity of the cell's own composition
+            Real Yo[K], lam0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) Yo[k] = cen[(G_Y0 + k) * HP + h];
+            transport(P, T0, Yo, mixture_invMw(P, Yo), mixture_cp(P, Yo), mu0, lam0);
+          }
+        }
         const MarchAcc<Real, K, PRE> A{cen, planes + ((z + 2) % 3) * NF * HP,
-                                       planes + ((z + 1) % 3) * NF * HP, h, viscosity(P, T0), fD,
+                                       planes + ((z + 1) % 3) * NF * HP, h, mu0, fD,
                                        pre, PRE && have, planes + 3 * NF * HP};
         // a cell that prefetched nothing lies on a non-periodic face: the
         // update pulls with the boundary rules there

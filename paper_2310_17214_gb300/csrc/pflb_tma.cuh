@@ -244,15 +244,17 @@ __device__ __forceinline__ void derive_plane(const Params<float, K>& P, float* r
 #pragma unroll
     for (int k = 0; k < K; ++k) Y[k] = raw[LY::OFF_Y + k * LY::FBOX + r];
     const float phif = 1.f - phis;
-    const float rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
-    const float mu = viscosity(P, T);
+    const float invMw = mixture_invMw(P, Y);
+    const float rho = fdiv(P0 * P.eos_cr, T * invMw);
     const float cp = mixture_cp(P, Y);
+    float mu, lam;
+    transport(P, T, Y, invMw, cp, mu, lam);
     float fD = 1.f;
     if constexpr (K > 0) {
       if (P.D_Tdep) fD = fpow(T * P.inv_DTref, P.D_exp);
     }
     der[0 * LY::HP + h] = rho;
-    der[1 * LY::HP + h] = phif * (mu * cp * P.inv_Pr);
+    der[1 * LY::HP + h] = phif * lam;
     der[2 * LY::HP + h] = mu;
     der[3 * LY::HP + h] = fD;
     der[4 * LY::HP + h] = phif * rho * fD;

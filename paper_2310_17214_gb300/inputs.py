@@ -42,6 +42,26 @@ def element_matrix(species, elements=("C", "H", "O", "N")):
             [_AW[e] for e in elements])
 
 
+# Sutherland laws of the pure gases (mu_ref in Pa s at T_ref, T_ref, S in K):
+# values of the standard viscosity tables, used by the mixture-averaged
+# transport option; steam is referred to 350 K.
+SUTHERLAND = {"N2": (1.663e-5, 273.0, 107.0), "O2": (1.919e-5, 273.0, 139.0),
+              "CO2": (1.370e-5, 273.0, 222.0), "CO": (1.657e-5, 273.0, 136.0),
+              "CH4": (1.030e-5, 273.0, 198.0), "H2O": (1.120e-5, 350.0, 1064.0)}
+
+
+def mixture_transport(p):
+    """Switch a reactive problem to mixture-averaged viscosity and
+    conductivity (Sec. 4.4, eqs. muT_mix, phi_mix, conduct_mix) with the
+    species' Sutherland laws; the single-gas mu_ref, Sutherland constants and
+    Pr are then unused."""
+    p["transport"] = "mixture"
+    p["mu_k"] = [SUTHERLAND[s][0] for s in p["species"]]
+    p["suth_Tk"] = [SUTHERLAND[s][1] for s in p["species"]]
+    p["suth_Sk"] = [SUTHERLAND[s][2] for s in p["species"]]
+    return p
+
+
 # one-step CH4 mechanism species order
 SPECIES5 = ["CH4", "O2", "CO2", "H2O", "N2"]
 M5 = [molar_mass(s) for s in SPECIES5]

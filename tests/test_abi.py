@@ -90,7 +90,8 @@ def test_every_workload_passes_the_stability_checks():
     pass the create / set_mechanism checks, including T_max."""
     from paper_2310_17214_gb300 import inputs as I
     probs = [I.config1(), I.config2(), I.config2(precision="fp32"), I.config3(),
-             I.config3_crop(64), I.config4(), I.config4(chem="surrogate")] + I.config5()
+             I.config3_crop(64), I.config4(), I.config4(chem="surrogate"),
+             I.mixture_transport(I.config2()), I.mixture_transport(I.config3())] + I.config5()
     for p in probs:
         rc, msg = nat.validate(p, p.get("precision", "fp64"))
         assert rc == 0, (p.get("name"), rc, msg)

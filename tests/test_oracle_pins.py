@@ -587,3 +587,83 @@ def test_outlet_mixing_cup_temperature_of_a_uniform_stream():
     s = O.OracleState(p, phi, f["T"], u=f["u"])
     s.step(20)
     assert abs(s.diagnostics()["outlet_Tm"] - 300.0) < 1e-9
+
+
+# ---------------------------------------------- mixture-averaged transport
+def _air_like(T=300.0):
+    """N2 / O2 with the cp of air's constituents, for checks against tables."""
+    p = small(2, 4, 4, bc=["periodic"] * 6, nu=0.05)
+    p["K"], p["species"] = 2, ["N2", "O2"]
+    p["M"] = [I.molar_mass("N2"), I.molar_mass("O2")]
+    p["cp"], p["hf"], p["Dref"] = [1040.0, 918.0], [0.0, 0.0], [2e-5, 2e-5]
+    p["Y_in"] = [0.767, 0.233]
+    return I.mixture_transport(p)
+
+
+# Air at 1 atm from standard property tables: mu (Pa s), lambda (W/m/K).
+AIR_LAMBDA_TABLE = {300.0: 0.0263, 600.0: 0.0469}
+
+
+def test_mixture_transport_of_air_against_tables():
+    """Sec. 4.4, eqs. muT_mix, phi_mix, conduct_mix with the pure-gas
+    Sutherland laws of N2 and O2 and the modified Eucken conductivity: air
+    (23.3 % O2 by mass) matches tabulated viscosity within 3 % and
+    conductivity within 7 % (the Eucken relation is a correlation) at 300 and
+    600 K."""
+    p = _air_like()
+    for T in (300.0, 600.0):
+        mu, lam = O.mixture_transport(p, T, p["Y_in"])
+        assert abs(mu / AIR_MU_TABLE[T] - 1) < 0.03, (T, mu)
+        assert abs(lam / AIR_LAMBDA_TABLE[T] - 1) < 0.07, (T, lam)
+
+
+def test_mixture_transport_limits():
+    """A pure species gives its own viscosity and conductivity; a mixture of
+    two copies of one gas (same molar mass and law) gives that gas's values
+    at every composition (Phi_kj = 1); the mixture viscosity lies between
+    the pure values of N2 and O2."""
+    p = _air_like()
+    T = 450.0
+    mu_k = [p["mu_k"][k] * (T / p["suth_Tk"][k]) ** 1.5 * (p["suth_Tk"][k] + p["suth_Sk"][k]) /
+            (T + p["suth_Sk"][k]) for k in range(2)]
+    for k in range(2):
+        Y = [0.0, 0.0]
+        Y[k] = 1.0
+        mu, lam = O.mixture_transport(p, T, Y)
+        assert abs(mu / mu_k[k] - 1) < 1e-14
+        eucken = 1.32 * (p["cp"][k] - 8.314 / p["M"][k]) + 1.77 * 8.314 / p["M"][k]
+        assert abs(lam / (mu_k[k] * eucken) - 1) < 1e-14
+    q = dict(p)
+    q["M"] = [p["M"][0]] * 2
+    q["mu_k"], q["suth_Tk"], q["suth_Sk"] = [p["mu_k"][0]] * 2, [p["suth_Tk"][0]] * 2, \
+        [p["suth_Sk"][0]] * 2
+    q["cp"] = [p["cp"][0]] * 2
+    for y in (0.1, 0.5, 0.83):
+        mu, lam = O.mixture_transport(q, T, [y, 1 - y])
+        assert abs(mu / mu_k[0] - 1) < 1e-14
+        eucken = 1.32 * (q["cp"][0] - 8.314 / q["M"][0]) + 1.77 * 8.314 / q["M"][0]
+        assert abs(lam / (mu_k[0] * eucken) - 1) < 1e-14
+    mu, _ = O.mixture_transport(p, T, p["Y_in"])
+    assert min(mu_k) < mu < max(mu_k)
+
+
+def test_mixture_conductivity_is_what_the_step_conducts_with():
+    """The temperature step uses the mixture conductivity: a small conduction
+    mode in uniform air decays by G = 1 - 2 lambda dt / (rho cp dx^2)
+    (1 - cos th) with lambda from the mixture rule."""
+    nx, k, amp, T0 = 16, 2, 1e-3, 500.0
+    p = _air_like()
+    p.update(nx=nx, ny=1, dx=2.5e-5, dt=2.5e-7, rho_ref=1.2)
+    x = np.arange(nx)
+    th = 2 * math.pi * k / nx
+    T = T0 + amp * np.cos(th * x)
+    Y = np.repeat(np.asarray(p["Y_in"])[:, None], nx, axis=1).reshape(-1)
+    Tn, _, _ = O.fd_phase(p, np.zeros(nx), T, Y, None, np.zeros((2, nx)), p["P0"], p["P0"])
+    A = 2.0 / nx * np.sum((Tn - Tn.mean()) * np.cos(th * x))
+    G = A / amp
+    Mw = 1.0 / (p["Y_in"][0] / p["M"][0] + p["Y_in"][1] / p["M"][1])
+    rho = p["P0"] * Mw / (8.314 * T0)
+    cp = p["Y_in"][0] * p["cp"][0] + p["Y_in"][1] * p["cp"][1]
+    _, lam = O.mixture_transport(p, T0, p["Y_in"])
+    ref = 1 - 2 * lam * p["dt"] / (rho * cp * p["dx"] ** 2) * (1 - math.cos(th))
+    assert abs(G - ref) < 1e-9
