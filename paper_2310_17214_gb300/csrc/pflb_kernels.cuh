@@ -1353,11 +1353,13 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   return phif * fdiv(Real(1), Tn * mixture_invMw(P, Yn)) + Real(0) * Ph;
 }
 
-// Resident blocks per SM requested from the register allocator (measured on
-// GB300: FP32/FP16 2-D and FP16 3-D run best at <= 64 registers, FP32 3-D at
-// <= 85; FP64 is FP64-pipe bound and keeps the registers it needs).
+// Resident blocks per SM requested from the register allocator: 2-D FP32 /
+// FP16 storage at <= 64 registers (4 blocks), 3-D FP32 at <= 80 (3 blocks),
+// 3-D FP16 storage, whose decode holds the source cells' moments, at <= 128
+// (2 blocks); FP64 is bound by the FP64 pipe and keeps the registers it needs.
 template <int DIM, class Real, class Store> struct MinBlocks {
-  static constexpr int value = sizeof(Real) == 8 ? (DIM == 3 ? 1 : 2) : (DIM == 2 ? 4 : 3);
+  static constexpr int value =
+      sizeof(Real) == 8 ? (DIM == 3 ? 1 : 2) : (DIM == 2 ? 4 : (IsHalf<Store>::value ? 2 : 3));
 };
 
 // One tile of the fused step (tile (bx, by) of the xy grid, z-chunk bz in

@@ -177,13 +177,15 @@ __device__ __forceinline__ bool march_prefetch(const Params<Real, K>& P,
   return true;
 }
 
-template <class Real, class Store> struct MarchMinBlocks {
-  static constexpr int value = sizeof(Real) == 8 ? 1 : 2;
+// Resident blocks per SM asked of the register allocator: FP32 storage fits
+// 80 registers (3 blocks); the FP16 decode needs more (2 blocks, no spills).
+template <class Real, class Store, bool PRE> struct MarchBlocks {
+  static constexpr int value =
+      sizeof(Real) == 8 ? 1 : ((PRE || IsHalf<Store>::value) ? 2 : 3);
 };
 
 template <int K, class Real, class Store, bool PRE>
-__global__ void __launch_bounds__(BLOCK, (PRE ? MarchMinBlocks<Real, Store>::value
-                                              : (sizeof(Real) == 8 ? 1 : 3)))
+__global__ void __launch_bounds__(BLOCK, (MarchBlocks<Real, Store, PRE>::value))
 step3d_march_kernel(const Params<Real, K> P, const State<Real, Store> S, int p0_closed,
                     const double* __restrict__ prev_partials, unsigned prev_nb) {
   using T_ = Tile<3>;
