@@ -56,6 +56,7 @@ class OrcParams(C.Structure):
         ("rorder", (C.c_double * KMAX) * JMAX), ("p_ref", C.c_double),
         ("transport_mix", C.c_int), ("mu_k", C.c_double * KMAX),
         ("suth_Tk", C.c_double * KMAX), ("suth_Sk", C.c_double * KMAX),
+        ("feedback", C.c_int), ("fb_k", C.c_int),
     ]
 
 
@@ -90,7 +91,7 @@ def lib():
                                         C.POINTER(C.c_double)]
         L.orc_chem_implicit.restype = C.c_int
         L.orc_fd_phase.argtypes = [P, dp, dp, dp, C.c_void_p, dp, C.c_double, C.c_double,
-                                   dp, dp, C.c_void_p]
+                                   dp, dp, C.c_void_p, C.c_void_p]
         L.orc_init.argtypes = [P, dp, dp, dp, dp, C.c_void_p, C.c_void_p, C.c_double, dp]
         L.orc_moments.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_step.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_void_p]
@@ -165,6 +166,8 @@ def make_params(prob: dict) -> OrcParams:
             for k in range(K):
                 p.rorder[j][k] = r["reverse"]["order"][k]
     p.p_ref = prob.get("p_ref", 101325.0)
+    if prob.get("inlet_feedback") is not None:
+        p.feedback, p.fb_k = 1, int(prob["inlet_feedback"])
     if prob.get("transport") == "mixture":
         p.transport_mix = 1
         for k in range(K):
@@ -196,7 +199,7 @@ class OracleState:
         self.Ts = (np.ascontiguousarray(Ts, dtype=np.float64).reshape(N).copy()
                    if Ts is not None else None)
         self.g = np.zeros(Q * N)
-        self.scal = np.zeros(10)
+        self.scal = np.zeros(12)
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
         pp = None if Ph is None else np.ascontiguousarray(Ph, dtype=np.float64).reshape(-1)
         lib().orc_init(C.byref(self.p), self.phi, self.g, self.T, self.Y, _ptr(uu), _ptr(pp),
@@ -244,6 +247,11 @@ class OracleState:
     def P0(self):
         return self.scal[0]
 
+    @property
+    def u_in(self):
+        """Inlet peak speed of the next step (lattice units)."""
+        return self.scal[9]
+
 
 def lattice(dim):
     c = np.zeros(19 * 3, dtype=np.int32)
@@ -286,7 +294,7 @@ def fd_phase(prob, phi, T, Y, Ts, u, P0, P0prev):
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
     Yin = f64(Y) if K > 0 else np.zeros(1)
     lib().orc_fd_phase(C.byref(p), f64(phi), f64(T), Yin, _ptr(None if Ts is None else f64(Ts)),
-                       f64(u), float(P0), float(P0prev), Tn, Yn, _ptr(Tsn))
+                       f64(u), float(P0), float(P0prev), Tn, Yn, _ptr(Tsn), None)
     return Tn, (Yn[: K * N] if K > 0 else None), Tsn
 
 

@@ -96,6 +96,11 @@ typedef struct {
    * 0 = single gas (mu_ref, Pr) */
   int transport_mix;
   double mu_k[ORC_KMAX], suth_Tk[ORC_KMAX], suth_Sk[ORC_KMAX];
+  /* inlet mass-flow feedback (Sec. 4.4.1): after each step the inlet speed is
+   * set so that the fuel (species fb_k) entering through the inlet equals
+   * the fuel the step consumed, u_in = sum phi_f (-omega_F) / (rho_in Y_F,in A),
+   * A = sum over the inlet cells of the inlet profile; held in [0, 0.3] */
+  int feedback, fb_k;
 } orc_params;
 
 /* ---------------------------------------------------------------- lattices */
@@ -531,10 +536,14 @@ static double inlet_u(const orc_params* p, const int xyz[3]) {
  * cell velocity, central diffusion with arithmetic-mean face coefficients, the
  * species-enthalpy term -(sum cp_k j_k).grad T with central gradients, the
  * lagged dP0/dt, omega_T and S_I = A_T lambda phi_f phi_s^2 / eta^2 (Ts - T).
- * u is the lattice velocity field u[a*N + c]; Tn/Yn/Tsn receive step n+1. */
+ * u is the lattice velocity field u[a*N + c]; Tn/Yn/Tsn receive step n+1.
+ * DTm (nullable) receives the material increments of the step that the
+ * divergence needs, (1/T) DT/Dt + Mw sum_k (1/M_k) DY_k/Dt, each formed as
+ * the step's increment plus u.grad of the field with central differences
+ * (the gradient the LB source takes of rho); frozen cells: (T^{n+1} - T^n)/T. */
 int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const double* Y,
                  const double* Ts, const double* u, double P0, double P0prev,
-                 double* Tn, double* Yn, double* Tsn) {
+                 double* Tn, double* Yn, double* Tsn, double* DTm) {
   int N = ncell(p), K = p->K, dim = p->dim;
   double eta2 = p->eta * p->eta;
   double Cs = p->rhocp_s / p->rho_ref;
@@ -571,6 +580,7 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
       for (int k = 0; k < K; ++k) omega[k] = d0.rho * dY[k];
       omegaT = d0.rho * d0.cp * dT;
     }
+    double sYm = 0; /* sum_k (1/M_k) DY_k/Dt dt */
     for (int k = 0; k < K; ++k) {
       if (!fluid_on) { Yn[(size_t)k * N + c] = v0.Y[k]; continue; }
       double adv = 0, dif = 0;
@@ -585,6 +595,9 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
       }
       double rhs = -phif * d0.rho * adv + dif + phif * omega[k];
       Yn[(size_t)k * N + c] = v0.Y[k] + rhs / (phif * d0.rho);
+      double advc = 0; /* u.grad Y_k, central */
+      for (int a = 0; a < dim; ++a) advc += u[(size_t)a * N + c] * 0.5 * (vp[a].Y[k] - vm[a].Y[k]);
+      sYm += (Yn[(size_t)k * N + c] - v0.Y[k] + advc) / p->M[k];
     }
 
     /* temperature */
@@ -605,8 +618,12 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
       double rhs = -phif * d0.rho * d0.cp * adv + dif +
                    phif * (d0.rho * cross + (P0 - P0prev) / p->rho_ref + omegaT + SI);
       Tn[c] = v0.T + rhs / (phif * d0.rho * d0.cp);
+      double advc = 0; /* u.grad T, central */
+      for (int a = 0; a < dim; ++a) advc += u[(size_t)a * N + c] * 0.5 * (vp[a].T - vm[a].T);
+      if (DTm) DTm[c] = (Tn[c] - v0.T + advc) / v0.T + d0.Mw * sYm;
     } else {
       Tn[c] = v0.Ts;
+      if (DTm) DTm[c] = (v0.Ts - v0.T) / v0.T;
     }
 
     /* solid temperature (field mode) */
@@ -714,7 +731,8 @@ static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, 
 /* ----------------------------------------------------------- public API */
 /* scal: [0] P0, [1] P0 of the previous step, [2] fluid mass m (lattice),
  * [3] I = sum phi_f Mw / T, [4] inlet mass flux, [5] outlet mass flux,
- * [6] step counter, [7] / [8] inlet / outlet mass flux summed over the steps. */
+ * [6] step counter, [7] / [8] inlet / outlet mass flux summed over the steps,
+ * [9] inlet peak speed of the next step, [10] fuel consumed in the last step. */
 static double reduce_I(const orc_params* p, const double* phi, const double* T, const double* Y) {
   int N = ncell(p);
   double I = 0;
@@ -750,6 +768,8 @@ int orc_init(const orc_params* p, const double* phi, double* g, const double* T,
   scal[4] = scal[5] = 0;
   scal[6] = 0;
   scal[7] = scal[8] = 0; /* inlet / outlet mass flux summed over the steps */
+  scal[9] = p->u_in;     /* inlet peak speed of the next step */
+  scal[10] = 0;          /* fuel consumed in the last step (feedback) */
   return 0;
 }
 
@@ -774,8 +794,53 @@ int orc_moments(const orc_params* p, const double* phi, const double* g, const d
 
 /* One full time step n -> n+1 (in place on g, T, Y, Ts, scal).  diag
  * (nullable) receives u (dim*N), rho (N), P_h (N), D (N) of step n. */
-int orc_step(const orc_params* p, const double* phi, double* g, double* T, double* Y, double* Ts,
-             double* scal, double* diag) {
+/* Fuel (species fb_k) consumed over one step by the chemistry of the state
+ * (T, Y) at pressure P0: sum over fluid cells of phi_f (-omega_F) in lattice
+ * units (explicit rates, or the implicit increments times rho). */
+static double fuel_consumed(const orc_params* p, const double* phi, const double* T,
+                            const double* Y, double P0) {
+  int N = ncell(p), K = p->K;
+  double s = 0;
+  for (int c = 0; c < N; ++c) {
+    double phif = 1.0 - phi[c];
+    if (!(phif >= p->phi_min)) continue;
+    double Yc[ORC_KMAX];
+    for (int k = 0; k < K; ++k) Yc[k] = Y[(size_t)k * N + c];
+    double rho = eos_rho(p, P0, mixture_Mw(p, Yc), T[c]);
+    double om[ORC_KMAX] = {0}, omT = 0;
+    if (p->chem_mode == ORC_CHEM_EXPLICIT) {
+      orc_chem_rates(p, T[c], Yc, rho, om, &omT);
+    } else if (p->chem_mode == ORC_CHEM_IMPLICIT) {
+      double dY[ORC_KMAX], dT;
+      orc_chem_implicit(p, T[c], Yc, rho, dY, &dT);
+      for (int k = 0; k < K; ++k) om[k] = rho * dY[k];
+    }
+    s += phif * (-om[p->fb_k]);
+  }
+  return s;
+}
+
+/* the inlet profile summed over the inlet face (the area of the feedback) */
+static double inlet_area(const orc_params* p) {
+  orc_params q = *p;
+  q.u_in = 1.0;
+  double a = 0;
+  int nz = p->dim == 3 ? p->nz : 1;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < p->ny; ++y) {
+      int xyz[3] = {0, y, z};
+      a += inlet_u(&q, xyz);
+    }
+  return a;
+}
+
+int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, double* Y,
+             double* Ts, double* scal, double* diag) {
+  /* the inlet speed of this step is scal[9] (the feedback moves it) */
+  orc_params pc = *p_in;
+  pc.u_in = scal[9];
+  const orc_params* p = &pc;
+  double fuel = p->feedback ? fuel_consumed(p, phi, T, Y, scal[0]) : 0.0;
   lat_t L = lattice_of(p->dim);
   int N = ncell(p), dim = p->dim, K = p->K;
   double P0 = scal[0], P0prev = scal[1];
@@ -792,21 +857,18 @@ int orc_step(const orc_params* p, const double* phi, double* g, double* T, doubl
   stream_and_moments(p, L, phi, g, T, Y, P0, gin, u, rho, Kd, mu);
 
   /* 3: FD transport of T, Y (and Ts) with u^n, rho^n, explicit chemistry */
-  orc_fd_phase(p, phi, T, Y, p->Ts_field ? Ts : NULL, u, P0, P0prev, Tn, Yn, Tsn);
+  double* DTm = malloc(sizeof(double) * N);
+  orc_fd_phase(p, phi, T, Y, p->Ts_field ? Ts : NULL, u, P0, P0prev, Tn, Yn, Tsn, DTm);
 
   /* 4-5: divergence from the low-Mach constraint, source, collision */
   #pragma omp parallel for schedule(static)
   for (int c = 0; c < N; ++c) {
     int xyz[3];
     coords(p, c, xyz);
-    double Yc[ORC_KMAX];
-    for (int k = 0; k < K; ++k) Yc[k] = Y[(size_t)k * N + c];
-    double Mw = mixture_Mw(p, Yc);
-    double D = (Tn[c] - T[c]) / T[c];
-    double sY = 0;
-    for (int k = 0; k < K; ++k) sY += (Yn[(size_t)k * N + c] - Yc[k]) / p->M[k];
-    D += Mw * sY;
-    D -= (P0 - P0prev) / P0;
+    /* D = (1/T) DT/Dt + Mw sum_k (1/M_k) DY_k/Dt - (1/P0) dP0/dt: the
+     * continuity equation with the EOS (Sec. 3, eq. rho-in-terms-of-P0-and-T)
+     * at uniform P0, with the material increments of this step */
+    double D = DTm[c] - (P0 - P0prev) / P0;
 
     double r = rho[c], uc[3] = {0, 0, 0}, G[3] = {0, 0, 0}, F[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) uc[a] = u[(size_t)a * N + c];
@@ -821,7 +883,11 @@ int orc_step(const orc_params* p, const double* phi, double* g, double* T, doubl
     }
     double sg = 0;
     for (int i = 0; i < L.Q; ++i) sg += gin[(size_t)i * N + c];
-    double Ph = sg + 0.5 * r * CS2 * D;
+    /* P_h = sum g + half the zeroth moment of Xi, sum_i Xi_i = u.G + rho cs^2 D,
+     * so that each step adds the whole source to sum g */
+    double uG = 0;
+    for (int a = 0; a < dim; ++a) uG += uc[a] * G[a];
+    double Ph = sg + 0.5 * (r * CS2 * D + uG);
     double geq[ORC_QMAX], xi[ORC_QMAX];
     orc_equilibrium(dim, Ph, r, uc, geq);
     orc_source(dim, r, G, uc, F, D, xi);
@@ -864,8 +930,15 @@ int orc_step(const orc_params* p, const double* phi, double* g, double* T, doubl
   scal[6] += 1;
   scal[7] += fin;
   scal[8] += fout;
+  scal[10] = fuel;
+  if (p->feedback) {
+    /* inflow of fuel rho_in Y_F,in u_in A equals the fuel the step consumed */
+    double rho_in = eos_rho(p, P0, mixture_Mw(p, p->Y_in), p->T_in);
+    double u = fuel / (rho_in * p->Y_in[p->fb_k] * inlet_area(p));
+    scal[9] = u < 0.0 ? 0.0 : (u > 0.3 ? 0.3 : u);
+  }
 
-  free(gin); free(u); free(rho); free(Kd); free(mu); free(Tn); free(Yn);
+  free(gin); free(u); free(rho); free(Kd); free(mu); free(Tn); free(Yn); free(DTm);
   if (Tsn) free(Tsn);
   return 0;
 }

@@ -78,7 +78,7 @@ DREF6 = [2.2e-5, 2.1e-5, 2.0e-5, 1.6e-5, 2.5e-5, 2.0e-5]
 
 # one-step pre-exponential factor (m^3/(mol s)); Ea/R = 15000 K, first order
 # in CH4 and O2 (project-chosen, see the design notes for its calibration).
-A_ONE_STEP = 3.31e8
+A_ONE_STEP = 3.68e8
 
 
 def lean_ch4_air(phi_eq: float, species):
@@ -555,6 +555,50 @@ def config3_fields(p):
     f = reactive_fields(p, phi)
     f["info"] = info
     return f
+
+
+def adiabatic_temperature(p):
+    """Adiabatic flame temperature of the inlet mixture (complete combustion,
+    constant cp_k): T_in + q / cp_burnt."""
+    Yin = np.asarray(p["Y_in"])
+    Yb = np.asarray(burnt_composition(p["Y_in"], p["species"], p["M"]))
+    q = -float(np.dot(np.asarray(p["hf"]), Yb - Yin))
+    return p["T_in"] + q / float(np.dot(Yb, p["cp"]))
+
+
+def config6(nx=480, ny=120, precision="fp64", steps=20000, width=None):
+    """2-D wall-bounded flame (the straight-channel flame of Sec. 4.4.2): the
+    lean one-step CH4 mixture of the reactive bed, a channel ny cells wide
+    (120 cells = 3 mm at dx = 25 um) between isothermal walls at 300 K
+    (half-way bounce-back with the wall temperature, the sharp-interface
+    form), parabolic inlet profile, no solid.  The first quarter of the channel
+    holds the fresh mixture at 300 K, the rest the burnt products at the
+    adiabatic flame temperature; the inlet feedback on CH4 (Sec. 4.4.1) keeps
+    the flame near x = nx/4.  The first inlet speed is the calibrated burning
+    velocity as a mean (peak 1.5 S_F)."""
+    p = config2(nx=nx, ny=ny, precision=precision, steps=steps)
+    p.pop("bed", None)
+    p.pop("ignite", None)
+    p["bc"] = ["inlet", "outlet", "wall", "wall", "periodic", "periodic"]
+    p["wall_T"] = [0.0, 0.0, 300.0, 300.0, 0.0, 0.0]
+    p.update({"A_u": 0.0, "A_T": 0.0, "Ts_field": 0, "inlet_parabolic": 1,
+              "u_in": 1.5 * 0.2 * p["dt"] / p["dx"], "inlet_feedback": 0,
+              "name": f"cfg6_wall_bounded_flame_{nx}x{ny}_d2q9_{precision}"})
+    return p
+
+
+def config6_fields(p, blend=4.0):
+    """Fresh mixture up to x = nx/4, burnt products at T_ad beyond (tanh blend
+    of `blend` cells)."""
+    nx, ny = p["nx"], p["ny"]
+    x = np.broadcast_to(np.arange(nx, dtype=np.float64), (ny, nx)).reshape(-1)
+    w = 0.5 * (1.0 + np.tanh((x - nx / 4.0) / blend))
+    Tad = adiabatic_temperature(p)
+    T = p["T_in"] + (Tad - p["T_in"]) * w
+    Yin = np.asarray(p["Y_in"])
+    Yb = np.asarray(burnt_composition(p["Y_in"], p["species"], p["M"]))
+    Y = (Yin[:, None] * (1.0 - w) + Yb[:, None] * w).reshape(-1)
+    return {"phi": np.zeros(nx * ny), "T": T, "Y": Y, "Ts": None, "u": None}
 
 
 def with_initial_u(p, fields):

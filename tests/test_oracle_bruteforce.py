@@ -230,8 +230,18 @@ def brute_step(p, phi, g, T, Y, Ts, P0, P0p, m0):
     for c in cells:
         v0 = cellval(c)
         Mw = Mw_of(v0["Y"])
-        D = (Tn[c] - v0["T"]) / v0["T"]
-        D += Mw * sum((Yn[c][k] - v0["Y"][k]) / p["M"][k] for k in range(K))
+        # material derivative over the step, DT/Dt = d_t T + u.grad T: the
+        # Eulerian increment plus the convection with central differences
+        # (none in frozen cells)
+        fluid = (1 - v0["phi"]) >= p["phi_min"]
+        nbs = [(nbval(c, a, -1), nbval(c, a, +1)) for a in range(dim)]
+        cT = sum(u[c][a] * 0.5 * (vp["T"] - vm["T"]) for a, (vm, vp) in enumerate(nbs))
+        cY = [sum(u[c][a] * 0.5 * (vp["Y"][k] - vm["Y"][k]) for a, (vm, vp) in enumerate(nbs))
+              for k in range(K)]
+        if not fluid:
+            cT, cY = 0.0, [0.0] * K
+        D = (Tn[c] - v0["T"] + cT) / v0["T"]
+        D += Mw * sum((Yn[c][k] - v0["Y"][k] + cY[k]) / p["M"][k] for k in range(K))
         D -= (P0 - P0p) / P0
         r, uc = rho[c], u[c]
         G = []
@@ -239,17 +249,20 @@ def brute_step(p, phi, g, T, Y, Ts, P0, P0p, m0):
             vm, vp = nbval(c, a, -1), nbval(c, a, +1)
             G.append(CS2 * 0.5 * (rho_of(vp["T"], vp["Y"]) - rho_of(vm["T"], vm["Y"])))
         F = [p["Fb"][a] - Kd[c] * uc[a] for a in range(dim)]
-        Ph = sum(gin[c].values()) + 0.5 * r * CS2 * D
         tau = 0.5 + mu[c] / (r * CS2)
         uu = sum(x * x for x in uc)
-        for i, v in enumerate(vel):
+        feqs, xis = {}, {}
+        for v in vel:
             cu = sum(v[a] * uc[a] for a in range(dim))
-            feq = r * W[v] * (1 + cu / CS2 + cu * cu / (2 * CS2 ** 2) - uu / (2 * CS2))
-            geq = CS2 * feq + W[v] * (Ph - r * CS2)
-            xi = sum((v[a] - uc[a]) * (G[a] * (feq / r - W[v]) + F[a] * feq / r)
-                     for a in range(dim)) + r * CS2 * W[v] * D
+            feqs[v] = r * W[v] * (1 + cu / CS2 + cu * cu / (2 * CS2 ** 2) - uu / (2 * CS2))
+            xis[v] = sum((v[a] - uc[a]) * (G[a] * (feqs[v] / r - W[v]) + F[a] * feqs[v] / r)
+                         for a in range(dim)) + r * CS2 * W[v] * D
+        # P_h: the pulled zeroth moment plus half the source's zeroth moment
+        Ph = sum(gin[c].values()) + 0.5 * sum(xis.values())
+        for i, v in enumerate(vel):
+            geq = CS2 * feqs[v] + W[v] * (Ph - r * CS2)
             gi = gin[c][v]
-            gnew[i][idx[c]] = gi - (gi - geq) / tau + (1 - 1 / (2 * tau)) * xi
+            gnew[i][idx[c]] = gi - (gi - geq) / tau + (1 - 1 / (2 * tau)) * xis[v]
 
     Tout = np.array([Tn[c] for c in cells])
     Yout = np.array([[Yn[c][k] for c in cells] for k in range(K)]) if K else None
