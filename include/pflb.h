@@ -154,6 +154,20 @@ typedef struct pflb_mechanism {
    * lambda_k = mu_k (1.32 cv_k + 1.77 R / M_k), cv_k = cp_k - R / M_k. */
   int transport;
   double mu_k[PFLB_KMAX], suth_Tk[PFLB_KMAX], suth_Sk[PFLB_KMAX];
+  /* Inlet mass-flow feedback (Sec. 4.4.1: a flame held stationary by the
+   * inflow).  0: off, the inlet speed is the description's u_in.  k + 1: after
+   * every step the inlet peak speed of the next step is set so that species k
+   * flows in as fast as that step consumed it,
+   *   u_in = sum_cells phi_f (-omega_k) / (rho_in Y_in[k] A),
+   * omega_k the step's reaction source of the cells' state at its start (the
+   * rates, or the increments of the implicit integrator or surrogate times
+   * rho), rho_in the inlet density and A the inlet profile summed over the
+   * inlet face at unit peak speed; the result is held in [0, 0.3].  The
+   * description's u_in is the speed of the first step.  Needs an inlet face,
+   * PFLB_P0_FIXED and Y_in[k] > 0; pflb_batch_step and pflb_step_noalloc
+   * refuse such a domain (PFLB_ERR_UNSUPPORTED).  pflb_get_scalars reports
+   * the current speed and the consumption it came from. */
+  int inlet_feedback;
 } pflb_mechanism;
 
 #define PFLB_TRANSPORT_SINGLE 0
@@ -167,6 +181,9 @@ typedef struct pflb_scalars {
   double flux_in, flux_out;/* inlet / outlet mass flux of the last step (lattice units) */
   long long step;          /* steps taken */
   int status;              /* latched device status (PFLB_OK or PFLB_ERR_UNSTABLE) */
+  double u_in;             /* inlet peak speed of the next step (lattice units) */
+  double fuel;             /* with the inlet feedback: sum phi_f (-omega_k) of the last
+                              step (lattice units); else 0 */
 } pflb_scalars;
 
 /* Create a domain: validates the description, then allocates every device

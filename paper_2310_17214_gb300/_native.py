@@ -53,13 +53,15 @@ class Mechanism(C.Structure):
         ("rorder", (C.c_double * KMAX) * JMAX), ("p_ref", C.c_double),
         ("transport", C.c_int), ("mu_k", C.c_double * KMAX), ("suth_Tk", C.c_double * KMAX),
         ("suth_Sk", C.c_double * KMAX),
+        ("inlet_feedback", C.c_int),
     ]
 
 
 class Scalars(C.Structure):
     _fields_ = [("P0", C.c_double), ("P0_prev", C.c_double), ("mass", C.c_double),
                 ("I", C.c_double), ("flux_in", C.c_double), ("flux_out", C.c_double),
-                ("step", C.c_longlong), ("status", C.c_int)]
+                ("step", C.c_longlong), ("status", C.c_int), ("u_in", C.c_double),
+                ("fuel", C.c_double)]
 
 
 class Diagnostics(C.Structure):
@@ -213,6 +215,8 @@ def make_mechanism(prob: dict) -> Mechanism:
         for k in range(K):
             m.mu_k[k], m.suth_Tk[k], m.suth_Sk[k] = prob["mu_k"][k], prob["suth_Tk"][k], \
                 prob["suth_Sk"][k]
+    if prob.get("inlet_feedback") is not None:
+        m.inlet_feedback = int(prob["inlet_feedback"]) + 1  # species index + 1
     return m
 
 

@@ -140,7 +140,8 @@ Launcher* make_launcher(const pflb_domain* d) {
 void free_buffers(pflb_domain* d) {
   void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.M[0], d->B.M[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
                   d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
-                  d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats, d->B.tile_ctr};
+                  d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats, d->B.tile_ctr,
+                  d->B.feed_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::memset(&d->B, 0, sizeof(d->B));
@@ -214,6 +215,10 @@ int validate_mech(const pflb_mechanism& m, std::string& msg) {
     for (int k = 0; k < m.K; ++k)
       if (!(m.mu_k[k] > 0 && m.suth_Tk[k] > 0 && m.suth_Sk[k] >= 0))
         return bad(PFLB_ERR_ARG, "species viscosity laws must be positive");
+  if (m.inlet_feedback < 0 || m.inlet_feedback > m.K)
+    return bad(PFLB_ERR_ARG, "inlet_feedback must be 0 (off) or a species index + 1");
+  if (m.inlet_feedback > 0 && !(m.Y_in[m.inlet_feedback - 1] > 0))
+    return bad(PFLB_ERR_ARG, "the inlet feedback species must have Y_in > 0");
   return PFLB_OK;
 }
 
@@ -421,6 +426,7 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   al((void**)&d->B.partials, (size_t)blocks * 2 * 4 * sizeof(double));
   al((void**)&d->B.counter, sizeof(unsigned));
   al((void**)&d->B.tile_ctr, 2 * sizeof(unsigned));
+  al((void**)&d->B.feed_part, kFeedBlocks * sizeof(double));
   if (!ok) {
     cudaGetLastError();
     free_buffers(d);
@@ -438,6 +444,9 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
     int rc = validate_mech(*m, why);
     if (rc == PFLB_OK) rc = check_stability(d->desc, m, why);
     if (rc != PFLB_OK) return fail(d, rc, "%s", why.c_str());
+    if (m->inlet_feedback > 0 &&
+        (d->desc.bc[0] != PFLB_BC_INLET || d->desc.p0_mode != PFLB_P0_FIXED))
+      return fail(d, PFLB_ERR_ARG, "the inlet feedback needs an inlet face and a fixed P0");
   }
   if (d->has_fields) return fail(d, PFLB_ERR_STATE, "set_mechanism must precede set_fields");
   cudaSetDevice(d->desc.device);
@@ -555,6 +564,8 @@ int pflb_get_scalars(pflb_domain* d, pflb_scalars* out) {
   out->flux_out = h.flux_out;
   out->step = h.step;
   out->status = h.status;
+  out->u_in = h.u_in;
+  out->fuel = h.fuel;
   if (h.status != 0) return fail(d, h.status, "%s", status_message(h.status));
   return PFLB_OK;
 }
@@ -739,7 +750,7 @@ int pflb_get_state(pflb_domain* d, void* dst, size_t bytes, int where) {
   CK(d, d->L->finalize(d->B, d->stream));
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
-  std::memcpy(h.magic, "PFLBSTv2", 8);
+  std::memcpy(h.magic, "PFLBSTv3", 8);
   h.version = 1;
   h.dim = d->dim; h.nx = d->desc.nx; h.ny = d->desc.ny; h.nz = d->desc.nz;
   h.precision = d->desc.precision; h.K = d->K; h.Ts_field = d->desc.Ts_field; h.N = d->N;
@@ -766,7 +777,7 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
   StateHeader h;
   if (where == PFLB_HOST) std::memcpy(&h, src, sizeof(h));
   else CK(d, cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDeviceToHost));
-  if (std::memcmp(h.magic, "PFLBSTv2", 8) != 0 || h.dim != d->dim || h.nx != d->desc.nx ||
+  if (std::memcmp(h.magic, "PFLBSTv3", 8) != 0 || h.dim != d->dim || h.nx != d->desc.nx ||
       h.ny != d->desc.ny || h.nz != d->desc.nz || h.precision != d->desc.precision ||
       h.K != d->K || h.Ts_field != d->desc.Ts_field || h.N != d->N)
     return fail(d, PFLB_ERR_ARG, "state does not match this domain");

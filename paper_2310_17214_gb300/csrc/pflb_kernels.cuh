@@ -152,6 +152,10 @@ struct Params {
   Real mu_lat_k[KK], inv_suth_Tk[KK], suth_Sk[KK], suth_TSk[KK], eucken_k[KK];
   Real wA[KK][KK];         // (M_j / M_k)^(1/4)
   Real wB[KK][KK];         // 1 / (sqrt(8) sqrt(1 + M_k / M_j))
+  // inlet mass-flow feedback (Sec. 4.4.1): on, species index, and
+  // feed_c = 1 / (rho_in / P0 Y_in[k] A) so that u_in = fuel feed_c / P0
+  int feed, feed_k;
+  double feed_c;
 };
 
 // Scalar state on the device.  The per-step quantities the cells need (P0,
@@ -165,6 +169,10 @@ struct DevScalars {
   int pad;
   double dlnP0, dP0r;
   float P0_f, dlnP0_f, dP0r_f, pad_f;
+  // inlet peak speed of the next step and the consumption it was set from
+  // (inlet feedback; otherwise u_in stays the description's value)
+  double u_in, fuel;
+  float u_in_f, pad_f2;
 };
 
 // FP16 storage keeps, per cell, the FP32 moments (P, j) = (sum g*, sum c g*)
@@ -247,6 +255,9 @@ __device__ __forceinline__ double fpow(double x, double y) { return pow(x, y); }
 template <class Real> __device__ __forceinline__ Real scal_P0(const DevScalars* s);
 template <> __device__ __forceinline__ double scal_P0<double>(const DevScalars* s) { return s->P0; }
 template <> __device__ __forceinline__ float scal_P0<float>(const DevScalars* s) { return s->P0_f; }
+template <class Real> __device__ __forceinline__ Real scal_u_in(const DevScalars* s);
+template <> __device__ __forceinline__ double scal_u_in<double>(const DevScalars* s) { return s->u_in; }
+template <> __device__ __forceinline__ float scal_u_in<float>(const DevScalars* s) { return s->u_in_f; }
 template <class Real> __device__ __forceinline__ Real scal_dlnP0(const DevScalars* s);
 template <> __device__ __forceinline__ double scal_dlnP0<double>(const DevScalars* s) { return s->dlnP0; }
 template <> __device__ __forceinline__ float scal_dlnP0<float>(const DevScalars* s) { return s->dlnP0_f; }
@@ -616,8 +627,8 @@ __device__ __forceinline__ Real first_order(const MA& A, int i, int src, int dx,
 }
 
 template <class Real, int K>
-__device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, const int xyz[3], int dim) {
-  Real u = P.u_in;
+__device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, Real u, const int xyz[3],
+                                        int dim) {
   if (!P.inlet_parabolic) return u;
   for (int a = 1; a < dim; ++a) {
     if (P.bc[2 * a] != BC_WALL) continue;
@@ -737,7 +748,7 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
     }
   }
   if (f0 && P.bc[0] == BC_INLET) {
-    const Real ui = inlet_u(P, xyz, DIM);
+    const Real ui = inlet_u(P, P.feed ? scal_u_in<Real>(S.scal) : P.u_in, xyz, DIM);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       if (L::c(i, 0) != 1) continue;
@@ -1205,7 +1216,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
   // shared by every species, and the central differences of Y_k feed the
   // enthalpy-flux cross term of the temperature equation
   Real Yn[KK];
-  Real sYd = 0;  // sum_k (Y_k^{n+1} - Y_k^n) / M_k for the divergence
+  Real sYm = 0;  // sum_k (1/M_k) DY_k/Dt dt for the divergence
   Real sx[3] = {0, 0, 0};  // sum_k cp_k D_k (Y_k(+) - Y_k(-)) per axis
   {
     Real fm[DIM], fp[DIM];
@@ -1216,39 +1227,42 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      Real adv = 0, dif = 0;
+      Real adv = 0, dif = 0, cen = 0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const Real dm = Y0[k] - at(F_Y0 + k, a, -1), dp = at(F_Y0 + k, a, +1) - Y0[k];
         adv += u[a] * (u[a] > Real(0) ? dm : dp);
         dif += fp[a] * dp - fm[a] * dm;
+        cen += u[a] * (dp + dm);
         sx[a] += P.cpD[k] * (dp + dm);
       }
       const Real dY = fluid_on ? (-phif * rho * adv + P.Dlat[k] * dif + phif * om[k]) * iphr
                                : Real(0);
       Yn[k] = Y0[k] + dY;
-      // FP32 takes the increment as computed; FP64 the difference as written
-      sYd += (sizeof(Real) == 4 ? dY : Yn[k] - Y0[k]) * P.invM[k];
+      // material increment: the step's increment plus u.grad Y_k (central)
+      sYm += (fluid_on ? dY + Real(0.5) * cen : Real(0)) * P.invM[k];
     }
   }
 
   // (b) temperature
-  Real Tn = Ts0, dTn = Ts0 - T0;
+  Real Tn = Ts0, dTm = Ts0 - T0;  // frozen cells take the solid temperature
   if (fluid_on) {
-    Real adv = 0, dif = 0, cross = 0;
+    Real adv = 0, dif = 0, cross = 0, cen = 0;
     const Real kc = A.c(F_KT);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const Real tm = at(F_T, a, -1), tp = at(F_T, a, +1);
       adv += u[a] > Real(0) ? u[a] * (T0 - tm) : u[a] * (tp - T0);
+      cen += u[a] * (tp - tm);
       const Real km = Real(0.5) * (kc + at(F_KT, a, -1));
       const Real kp = Real(0.5) * (kc + at(F_KT, a, +1));
       dif += kp * (tp - T0) - km * (T0 - tm);
       if constexpr (K > 0) cross += Real(0.25) * fD * sx[a] * (tp - tm);
     }
     const Real rhs = -phif * rho * cp * adv + dif + phif * (rho * cross + dP0r + omT + SI);
-    dTn = rhs * iphr * fdiv(Real(1), cp);
+    const Real dTn = rhs * iphr * fdiv(Real(1), cp);
     Tn = T0 + dTn;
+    dTm = dTn + Real(0.5) * cen;  // plus u.grad T (central)
   }
 
   // solid temperature
@@ -1267,14 +1281,13 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     S.Ts_out[c] = Tsn;
   }
 
-  // low-Mach divergence D = (1/T) dT + Mw sum dY_k / M_k - dP0 / P0.  FP32
-  // takes the increments as computed (T^{n+1} - T^n rounded in FP32 would
-  // keep only a few digits of a small increment of a large T); FP64 forms
-  // the differences as the scheme writes them
-  Real D;
-  if constexpr (sizeof(Real) == 4) D = dTn * invT;
-  else D = (Tn - T0) * invT;
-  if constexpr (K > 0) D += fdiv(sYd, invMw);
+  // low-Mach divergence: continuity with the EOS at uniform P0,
+  // D = (1/T) DT/Dt + Mw sum_k (1/M_k) DY_k/Dt - (1/P0) dP0/dt, the material
+  // increments taken as the step's increments plus u.grad with central
+  // differences, the gradient the source takes of rho (with the upwind
+  // gradient the discrete continuity would keep a first-order mass defect)
+  Real D = dTm * invT;
+  if constexpr (K > 0) D += fdiv(sYm, invMw);
   D -= dlnP0;
 
   // (a) source and BGK collision: omega = 1/tau = 2 rho / (rho + 6 mu)
@@ -1284,7 +1297,12 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
     G[a] = CS2 * Real(0.5) * (at(F_RHO, a, +1) - at(F_RHO, a, -1));
     F[a] = P.Fb[a] - Kd * u[a];
   }
-  const Real Ph = sg + Real(0.5) * rho * CS2 * D;
+  // P_h: the pulled zeroth moment plus half the zeroth moment of the source,
+  // sum_i Xi_i = u.G + rho cs^2 D, so that a step adds the whole source
+  Real uG = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) uG += u[a] * G[a];
+  const Real Ph = sg + Real(0.5) * (rho * CS2 * D + uG);
   const Real omega = fdiv(Real(2) * rho, rho + Real(6) * mu);
   const Real src_w = Real(1) - Real(0.5) * omega;
   // f_eq / rho - w = w e with e = 3 cu + 9/2 cu^2 - 3/2 uu;
@@ -1561,6 +1579,68 @@ chem_implicit_kernel(const __grid_constant__ Params<Real, K> P, const State<Real
 #pragma unroll
   for (int k = 0; k < K; ++k) src[(size_t)k * P.N + c] = om[k];
   src[(size_t)K * P.N + c] = omT;
+}
+
+// ------------------------------------------------ inlet feedback
+// Sec. 4.4.1: the inflow of species feed_k is matched to its consumption.
+// After the step kernel of step n, whose inputs (T, Y and the pre-pass
+// increments) are still in place, feed_kernel sums phi_f (-omega_k) of that
+// state over the cells (FP64 block partials, grid-stride over at most
+// kFeedBlocks blocks) and feed_combine_kernel sums the partials in a fixed
+// order and sets the inlet peak speed of step n + 1.
+constexpr int kFeedBlocks = 1024;
+
+template <int K, class Real, class Store>
+__global__ void __launch_bounds__(BLOCK)
+feed_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __restrict__ part) {
+  constexpr int KK = Params<Real, K>::KK;
+  __shared__ double red_sh[32];
+  double acc = 0;
+  if constexpr (K > 0) {
+    const Real P0 = scal_P0<Real>(S.scal);
+    for (int c = blockIdx.x * BLOCK + threadIdx.x; c < P.N; c += gridDim.x * BLOCK) {
+      const Real phif = Real(1) - S.phi[c];
+      if (!(phif >= P.phi_min)) continue;
+      Real om[KK], omT = 0;
+      if (P.chem == 1) {
+        const Real T = S.T_in[c];
+        Real Y[KK];
+#pragma unroll
+        for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
+        const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
+        rates(P, T, Y, rho, fdiv(Real(1), T), om, omT);
+        acc += double(phif * -om[P.feed_k]);
+      } else if (P.chem >= 2) {
+        acc += double(phif * -S.src[(size_t)P.feed_k * P.N + c]);
+      }
+    }
+  }
+  const double s = block_sum<double>(acc, red_sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// One warp: u_in = fuel feed_c / P0, held in [0, 0.3].
+static __global__ void feed_combine_kernel(const double* __restrict__ part, unsigned nb,
+                                           DevScalars* scal, double feed_c) {
+  const int lane = threadIdx.x;
+  double v = 0;
+  for (unsigned b = lane; b < nb; b += 32) v += part[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    double u = v * feed_c / scal->P0;
+    u = u > 0.3 ? 0.3 : (u > 0.0 ? u : 0.0);  // NaN -> 0
+    scal->fuel = v;
+    scal->u_in = u;
+    scal->u_in_f = float(u);
+  }
+}
+
+// The inlet speed of the first step (and no consumption yet).
+static __global__ void set_inlet_kernel(DevScalars* scal, double u_in) {
+  scal->u_in = u_in;
+  scal->u_in_f = float(u_in);
+  scal->fuel = 0.0;
 }
 
 // ------------------------------------------------ initial equilibrium

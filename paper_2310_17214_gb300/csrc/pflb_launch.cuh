@@ -36,6 +36,7 @@ struct Buffers {
   double* partials;        // two buffers of `slots` x 4 doubles (step parity)
   unsigned* counter;
   unsigned* tile_ctr;      // tile counters of the persistent step, one per parity
+  double* feed_part;       // inlet feedback block partials [kFeedBlocks]
   int N;
   long long slots;         // partial slots per buffer (>= blocks of any launch)
   int pending;             // the last step's partials are not combined yet
@@ -223,6 +224,29 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
   P.c64.ln_pref_R = std::log(P.c64.p_ref / R_GAS);
   P.c64.rho_ref = d.rho_ref;
   P.c64.dt = d.dt;
+  // inlet feedback: rho_in / P0 (lattice) and the inlet area A, the inlet
+  // profile at unit peak speed summed over the x = 0 face
+  P.feed = (K > 0 && m.inlet_feedback > 0) ? 1 : 0;
+  P.feed_k = P.feed ? m.inlet_feedback - 1 : 0;
+  P.feed_c = 0.0;
+  if (P.feed) {
+    double invMw = 0;
+    for (int k = 0; k < K; ++k) invMw += m.Y_in[k] / m.M[k];
+    const double rin = 1.0 / (invMw * R_GAS * d.T_in * d.rho_ref);
+    const int nz = d.dim == 3 ? d.nz : 1;
+    double area = 0;
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < d.ny; ++y) {
+        double u = 1.0;
+        for (int a = 1; a < d.dim && d.inlet_parabolic; ++a) {
+          if (d.bc[2 * a] != PFLB_BC_WALL) continue;
+          const double n = a == 1 ? d.ny : d.nz, sa = (a == 1 ? y : z) + 0.5;
+          u *= 4.0 * sa * (n - sa) / (n * n);
+        }
+        area += u;
+      }
+    P.feed_c = 1.0 / (rin * m.Y_in[P.feed_k] * area);
+  }
   // FP16 residual scale: residuals |r / w| from 4 down to 3.7e-9 (lattice
   // units) stay in the normal FP16 range; smaller ones keep an absolute
   // resolution of 3.6e-12 as subnormals
@@ -257,9 +281,11 @@ struct LauncherImpl final : Launcher {
   using Store = typename ModeTypes<MODE>::Store;
   Params<Real, K> P;
   int p0_closed;
+  double u_in0;  // inlet peak speed of the first step
 
   LauncherImpl(const pflb_domain_desc& d, const pflb_mechanism& m)
-      : P(make_params<Real, K>(d, m, MODE)), p0_closed(d.p0_mode == PFLB_P0_CLOSED) {}
+      : P(make_params<Real, K>(d, m, MODE)), p0_closed(d.p0_mode == PFLB_P0_CLOSED),
+        u_in0(d.u_in) {}
 
   State<Real, Store> state(const Buffers& B, int cur) const {
     State<Real, Store> S;
@@ -301,6 +327,14 @@ struct LauncherImpl final : Launcher {
     S.M_out = static_cast<Real*>(B.M[cur]);
     init_kernel<DIM, K, Real, Store><<<blocks(), BLOCK, 0, st>>>(
         P, S, static_cast<const Real*>(u_init), P0);
+    set_inlet_kernel<<<1, 1, 0, st>>>(B.scal, u_in0);
+    return cudaGetLastError();
+  }
+  // inlet feedback after the step whose input state is buffer `cur`
+  cudaError_t feed(const Buffers& B, int cur, cudaStream_t st) const {
+    const int grid = blocks() < kFeedBlocks ? blocks() : kFeedBlocks;
+    feed_kernel<K, Real, Store><<<grid, BLOCK, 0, st>>>(P, state(B, cur), B.feed_part);
+    feed_combine_kernel<<<1, 32, 0, st>>>(B.feed_part, (unsigned)grid, B.scal, P.feed_c);
     return cudaGetLastError();
   }
   // The partials of a step go to buffer `cur` (the parity of its input
@@ -591,6 +625,10 @@ struct LauncherImpl final : Launcher {
         step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
                                                                      prev, (unsigned)B.last_nb);
         B.last_nb = step_blocks();
+      }
+      if (P.feed) {
+        e = feed(B, cur, st);
+        if (e != cudaSuccess) return e;
       }
       B.pending = p0_closed ? 0 : 1;
       B.last_parity = cur;

@@ -40,10 +40,35 @@ def test_lattice_tables_match_oracle_order():
         assert np.array_equal(w1, w2)
 
 
-def test_struct_layouts_are_plain_c():
-    # the ctypes mirrors must match the header's field order and sizes
-    assert ctypes.sizeof(nat.Scalars) == 7 * 8 + 8
-    assert ctypes.sizeof(nat.Mechanism) % 8 == 0
+def test_struct_layouts_are_plain_c(tmp_path):
+    """The ctypes mirrors of the binding match the header: a C program
+    compiled against include/pflb.h prints the size of each struct and the
+    offset of each field the mirror names."""
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"pflb_domain_desc": nat.Desc, "pflb_mechanism": nat.Mechanism,
+               "pflb_scalars": nat.Scalars, "pflb_diagnostics": nat.Diagnostics}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pflb.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        cname, field, value = line.split()
+        py = mirrors[cname]
+        got = ctypes.sizeof(py) if field == "sizeof" else getattr(py, field).offset
+        assert got == int(value), (cname, field, got, value)
 
 
 def test_create_rejects_bad_descriptions_without_touching_the_gpu():
