@@ -218,7 +218,8 @@ def workload_name(prob):
 
 def config_of(prob, fields, precision, world=1):
     """The workload's config, identical in both arms of the benchmark."""
-    return {"parallelism": f"replicas x{world}" if world > 1 else "single device","workload": workload_name(prob), "nx": prob["nx"], "ny": prob["ny"],
+    return {"parallelism": f"replicas x{world}" if world > 1 else "single device",
+            "workload": workload_name(prob), "nx": prob["nx"], "ny": prob["ny"],
             "nz": prob.get("nz", 1), "lattice": "D3Q19" if prob["dim"] == 3 else "D2Q9",
             "species": prob["K"], "particles": fields["info"]["placed"],
             "porosity_bed": round(fields["info"]["porosity_bed"], 3),
@@ -456,6 +457,51 @@ def bed2d_leg(dev, flush, peaks, steps=50):
                          "alg_bytes_per_cell": bpc}}
 
 
+def flame2d_leg(dev, flush, precisions=("fp32", "fp64"), settle=400, steps=200):
+    """The 2-D wall-bounded flame (480 x 120 D2Q9, five species, one-step
+    chemistry, isothermal walls) held by the inlet feedback: per step the fused
+    step kernel plus the two feedback kernels (consumption sum, inlet speed).
+    6 MB of state: L2-resident, so the L2 is flushed between steps; the
+    launch latency of three small kernels bounds it, not HBM."""
+    import torch
+    st = torch.cuda.current_stream(dev)
+    out = {}
+    for prec in precisions:
+        p = I.config6(precision=prec)
+        f = I.config6_fields(p)
+        dom = make_domain(p, f, prec, dev, st.cuda_stream)
+        dom.step(settle)
+        ms = _ms_per_step(dom, steps, flush, st)
+        sc = dom.scalars()
+        dom.close()
+        N = f["phi"].size
+        out[prec] = {"ms_per_step": ms, "mlups": N / ms / 1e3, "kernels_per_step": 3,
+                     "u_in_m_s": sc["u_in"] * p["dx"] / p["dt"],
+                     "steps_before": settle + steps + 3}
+    q = I.config6()
+    return {"workload": f"wall_bounded_flame_{q['nx']}x{q['ny']}_d2q9_k{q['K']}",
+            "l2": "flushed between steps (256 MiB write)",
+            **out}
+
+
+def calibration_leg(dev, values=(25, 50, 75, 100, 145, 200, 300, 450), steps=15000):
+    """The A_u calibration sweep of Sec. 4.1 (diffuse vs sharp channel,
+    L = 50, eta = 8, Re = 100, characteristic outlet): one library run per
+    A_u, each on its own stream; wall time of the whole sweep and the A_u
+    that minimises the velocity MSE (the paper's 145 is context: its outlet
+    scheme and numerics differ)."""
+    import time
+    import torch
+    from paper_2310_17214_gb300 import calibration
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r = calibration.sweep_A_u(values, steps=steps, precision="fp64", device=dev.index)
+    torch.cuda.synchronize(dev)
+    r["wall_s"] = time.perf_counter() - t0
+    r["runs"] = len(values) + 1
+    return r
+
+
 def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6):
     """The learned chemistry on the two-step bed (2048 x 512, six species):
     sample the Newton run (FP32 transport), train on the GPU, run the
@@ -642,6 +688,8 @@ def main():
                                     for p_ in ("fp32", "fp32_fp16")}
         extra["error_vs_fp64"] = errors_vs_fp64(prob, fields, 2000, dev, ("fp32", "fp32_fp16"))
         extra["bed_2d"] = bed2d_leg(dev, flush, peaks)
+        extra["flame_2d"] = flame2d_leg(dev, flush)
+        extra["calibration_A_u"] = calibration_leg(dev)
         extra["surrogate"] = surrogate_leg(dev, flush)
         extra["batch"] = batch_leg(dev, peaks)
         e2e_v, nb = e2e_measure(prob, fields, args.precision, 10, dev)

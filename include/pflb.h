@@ -108,7 +108,9 @@ typedef struct pflb_domain_desc {
   double Pr;               /* Prandtl number: lambda = mu cp / Pr */
   double A_u, A_T, eta;    /* coupling parameters, interface width (cells) */
   double Fb[3];            /* body-force density (lattice units) */
-  int inlet_parabolic;     /* inlet profile: 0 uniform, 1 parabola across wall-bounded axes */
+  int inlet_parabolic;     /* inlet profile: 0 uniform, 1 parabola across wall-bounded axes,
+                              2 uniform times the inlet cell's fluid fraction 1 - phi_s (a
+                              channel whose walls are diffuse solid layers, Sec. 4.1) */
   double u_in, T_in;       /* inlet peak velocity (lattice units), temperature (K) */
   int p0_mode;             /* PFLB_P0_FIXED / PFLB_P0_CLOSED */
   double P0;               /* initial thermodynamic pressure (Pa) */
@@ -119,6 +121,18 @@ typedef struct pflb_domain_desc {
   double T_max;            /* hottest temperature the run may reach (K), e.g. the adiabatic
                               flame temperature; 0 = none beyond T_in, Ts_uniform and the
                               wall temperatures.  Only the stability checks read it. */
+  int outlet_nscbc;        /* 1: partially non-reflecting outlet (Sec. 4.1, the
+                              characteristic outlet of Poinsot and Lele).  The
+                              anti-bounce-back imposes a boundary pressure P_b instead of
+                              P_h = 0; after every step P_b advances by
+                              dP_b/dt = -(L5 + L1)/2 with the outgoing plane wave
+                              L5 = (u + cs)(dP_h/dx + rho cs du/dx) from the face means of
+                              P_h, u_x (one-sided over the two outlet columns) and rho of
+                              the outlet column, and L1 = K P_b, K = nscbc_sigma cs / nx
+                              (the Mach-number factor 1 - Ma^2 taken as 1).  Needs an
+                              outlet face; pflb_batch_step and pflb_step_noalloc refuse it.
+                              0: P_h = 0. */
+  double nscbc_sigma;      /* relaxation factor sigma of K (e.g. 0.25) */
   void* stream;            /* cudaStream_t (NULL = legacy default stream) */
   int device;              /* CUDA device ordinal */
 } pflb_domain_desc;
@@ -164,7 +178,8 @@ typedef struct pflb_mechanism {
    * rho), rho_in the inlet density and A the inlet profile summed over the
    * inlet face at unit peak speed; the result is held in [0, 0.3].  The
    * description's u_in is the speed of the first step.  Needs an inlet face,
-   * PFLB_P0_FIXED and Y_in[k] > 0; pflb_batch_step and pflb_step_noalloc
+   * PFLB_P0_FIXED, Y_in[k] > 0 and an inlet profile other than 2;
+   * pflb_batch_step and pflb_step_noalloc
    * refuse such a domain (PFLB_ERR_UNSUPPORTED).  pflb_get_scalars reports
    * the current speed and the consumption it came from. */
   int inlet_feedback;
@@ -184,6 +199,8 @@ typedef struct pflb_scalars {
   double u_in;             /* inlet peak speed of the next step (lattice units) */
   double fuel;             /* with the inlet feedback: sum phi_f (-omega_k) of the last
                               step (lattice units); else 0 */
+  double outlet_pb;        /* boundary pressure of the next step at the characteristic
+                              outlet (lattice units); else 0 */
 } pflb_scalars;
 
 /* Create a domain: validates the description, then allocates every device

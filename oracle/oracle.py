@@ -57,6 +57,7 @@ class OrcParams(C.Structure):
         ("transport_mix", C.c_int), ("mu_k", C.c_double * KMAX),
         ("suth_Tk", C.c_double * KMAX), ("suth_Sk", C.c_double * KMAX),
         ("feedback", C.c_int), ("fb_k", C.c_int),
+        ("nscbc", C.c_int), ("nscbc_K", C.c_double), ("ob", C.POINTER(C.c_double)),
     ]
 
 
@@ -168,6 +169,10 @@ def make_params(prob: dict) -> OrcParams:
     p.p_ref = prob.get("p_ref", 101325.0)
     if prob.get("inlet_feedback") is not None:
         p.feedback, p.fb_k = 1, int(prob["inlet_feedback"])
+    if prob.get("outlet") == "nscbc":
+        # K = sigma cs (1 - Ma^2) / l with l the domain length (Ma^2 << 1 dropped)
+        p.nscbc = 1
+        p.nscbc_K = prob.get("nscbc_sigma", 0.25) * (1.0 / 3.0) ** 0.5 / prob["nx"]
     if prob.get("transport") == "mixture":
         p.transport_mix = 1
         for k in range(K):
@@ -200,6 +205,11 @@ class OracleState:
                    if Ts is not None else None)
         self.g = np.zeros(Q * N)
         self.scal = np.zeros(12)
+        # outlet state of the characteristic outlet: P_b, then P_h, u_x of the
+        # columns nx-1 and nx-2 (5 x ny nz); the params hold a pointer to it
+        nf = prob["ny"] * (prob.get("nz", 1) if prob["dim"] == 3 else 1)
+        self.ob = np.zeros(6 * nf)
+        self.p.ob = self.ob.ctypes.data_as(C.POINTER(C.c_double))
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
         pp = None if Ph is None else np.ascontiguousarray(Ph, dtype=np.float64).reshape(-1)
         lib().orc_init(C.byref(self.p), self.phi, self.g, self.T, self.Y, _ptr(uu), _ptr(pp),
@@ -246,6 +256,13 @@ class OracleState:
     @property
     def P0(self):
         return self.scal[0]
+
+    @property
+    def outlet_pressure(self):
+        """Boundary pressure P_b of the next step per outlet cell
+        (characteristic outlet; one value over the face)."""
+        nf = self.ob.size // 6
+        return self.ob[:nf].copy()
 
     @property
     def u_in(self):

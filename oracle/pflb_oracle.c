@@ -101,6 +101,19 @@ typedef struct {
    * the fuel the step consumed, u_in = sum phi_f (-omega_F) / (rho_in Y_F,in A),
    * A = sum over the inlet cells of the inlet profile; held in [0, 0.3] */
   int feedback, fb_k;
+  /* Partially non-reflecting outlet (Sec. 4.1, the characteristic outlet of
+   * Poinsot and Lele): instead of P_h = 0 the anti-bounce-back imposes a
+   * boundary pressure P_b that follows the 1-D characteristic relation
+   * dP_b/dt = -(L5 + L1)/2 of a plane wave leaving through the outlet, with
+   * the outgoing wave L5 = (u + cs) (dP_h/dx + rho cs du/dx) from the face
+   * means of the last step's P_h, u_x (one-sided differences over the two
+   * outlet columns) and rho of the outlet column, and the incoming wave
+   * L1 = K P_b (relaxation to the ambient P_h = 0).  ob (caller-owned, 6 NF
+   * doubles, NF = ny nz): P_b, then P_h and u_x of column nx-1, P_h and u_x
+   * of column nx-2 and rho of column nx-1, all of the last step. */
+  int nscbc;
+  double nscbc_K;
+  double* ob;
 } orc_params;
 
 /* ---------------------------------------------------------------- lattices */
@@ -517,10 +530,13 @@ static void coords(const orc_params* p, int c, int xyz[3]) {
   xyz[2] = c / (p->nx * p->ny);
 }
 
-/* Inlet velocity at a cell of the x = 0 column: uniform, or a parabola over
- * each wall-bounded transverse axis (walls half-way outside the domain). */
-static double inlet_u(const orc_params* p, const int xyz[3]) {
+/* Inlet velocity at a cell of the x = 0 column: uniform, uniform times the
+ * cell's fluid fraction (profile 2: a diffuse-interface channel whose walls
+ * are solid layers), or a parabola over each wall-bounded transverse axis
+ * (walls half-way outside the domain). */
+static double inlet_u(const orc_params* p, const int xyz[3], double phis) {
   double u = p->u_in;
+  if (p->inlet_parabolic == 2) return u * (1.0 - phis);
   if (!p->inlet_parabolic) return u;
   for (int a = 1; a < p->dim; ++a) {
     if (p->bc[2 * a] != ORC_BC_WALL) continue;
@@ -645,10 +661,30 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
 }
 
 /* ------------------------------------------------------------ streaming */
+/* The stored P_b advanced by dP_b/dt = -(L5 + L1)/2 over one lattice step
+ * from the stored outlet columns (the boundary pressure of the next step). */
+static double outlet_pb(const orc_params* p) {
+  int NF = p->ny * (p->dim == 3 ? p->nz : 1);
+  const double* ob = p->ob;
+  /* plane wave: face means of the outlet columns */
+  double P1 = 0, u1 = 0, P2 = 0, u2 = 0, r = 0;
+  for (int f = 0; f < NF; ++f) {
+    P1 += ob[NF + f]; u1 += ob[2 * NF + f]; P2 += ob[3 * NF + f]; u2 += ob[4 * NF + f];
+    r += ob[5 * NF + f];
+  }
+  P1 /= NF; u1 /= NF; P2 /= NF; u2 /= NF; r /= NF;
+  double pb = ob[0];
+  double cs = sqrt(CS2);
+  double L5 = (u1 + cs) * ((P1 - P2) + r * cs * (u1 - u2));
+  double L1 = p->nscbc_K * pb;
+  return pb - 0.5 * (L5 + L1);
+}
+
 /* Pull the populations arriving at cell c from the post-collision field gs,
  * applying the boundary rules; uw is the outlet wall-velocity estimate. */
 static void pull(const orc_params* p, lat_t L, const double* gs, int N, int c, const int xyz[3],
-                 double rho_c, double rho_in, const double* uw, double* gin) {
+                 double rho_c, double rho_in, double phis_c, const double* uw, double* gin) {
+  double pb = (p->nscbc && p->bc[1] == ORC_BC_OUTLET && xyz[0] == p->nx - 1) ? p->ob[0] : 0.0;
   for (int i = 0; i < L.Q; ++i) {
     int s[3] = {xyz[0] - L.c[i][0], xyz[1] - L.c[i][1], xyz[2] - L.c[i][2]};
     int out_face[3] = {-1, -1, -1};
@@ -674,12 +710,12 @@ static void pull(const orc_params* p, lat_t L, const double* gs, int N, int c, c
       for (int a = 0; a < p->dim; ++a) cu += L.c[i][a] * p->wall_u[wall][a];
       gin[i] = gs[(size_t)ib * N + c] + 2.0 * L.w[i] * rho_c * cu;
     } else if (inlet) {
-      double cu = L.c[i][0] * inlet_u(p, xyz);
+      double cu = L.c[i][0] * inlet_u(p, xyz, phis_c);
       gin[i] = gs[(size_t)ib * N + c] + 2.0 * L.w[i] * rho_in * cu;
     } else if (outlet) {
       double cu = 0, uu = 0;
       for (int a = 0; a < p->dim; ++a) { cu += L.c[i][a] * uw[a]; uu += uw[a] * uw[a]; }
-      gin[i] = -gs[(size_t)ib * N + c] + L.w[i] * (2.0 * 0.0 + rho_c * (cu * cu / CS2 - uu));
+      gin[i] = -gs[(size_t)ib * N + c] + L.w[i] * (2.0 * pb + rho_c * (cu * cu / CS2 - uu));
     } else {
       int sc = s[0] + p->nx * (s[1] + p->ny * s[2]);
       gin[i] = gs[(size_t)i * N + sc];
@@ -711,7 +747,7 @@ static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, 
     double gin[ORC_QMAX], uw[3] = {0, 0, 0}, uc[3] = {0, 0, 0};
     int passes = is_outlet_cell(p, xyz) ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
-      pull(p, L, gs, N, c, xyz, r, rho_in, uw, gin);
+      pull(p, L, gs, N, c, xyz, r, rho_in, phis, uw, gin);
       for (int a = 0; a < dim; ++a) {
         double m = 0;
         for (int i = 0; i < L.Q; ++i) m += L.c[i][a] * gin[i];
@@ -775,8 +811,11 @@ int orc_init(const orc_params* p, const double* phi, double* g, const double* T,
 
 /* Velocity, density and sum-of-populations pressure that the next step will
  * see at every cell (pull + moments of the current state, no collision). */
-int orc_moments(const orc_params* p, const double* phi, const double* g, const double* T,
+int orc_moments(const orc_params* p_in, const double* phi, const double* g, const double* T,
                 const double* Y, const double* scal, double* u, double* rho, double* Ph) {
+  orc_params pc = *p_in; /* the inlet speed of the next step */
+  pc.u_in = scal[9];
+  const orc_params* p = &pc;
   lat_t L = lattice_of(p->dim);
   int N = ncell(p);
   double* gin = malloc(sizeof(double) * (size_t)L.Q * N);
@@ -829,7 +868,7 @@ static double inlet_area(const orc_params* p) {
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < p->ny; ++y) {
       int xyz[3] = {0, y, z};
-      a += inlet_u(&q, xyz);
+      a += inlet_u(&q, xyz, 0.0);
     }
   return a;
 }
@@ -861,6 +900,8 @@ int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, do
   orc_fd_phase(p, phi, T, Y, p->Ts_field ? Ts : NULL, u, P0, P0prev, Tn, Yn, Tsn, DTm);
 
   /* 4-5: divergence from the low-Mach constraint, source, collision */
+  int NF = p->ny * (dim == 3 ? p->nz : 1);
+  double* obnew = (p->nscbc && p->bc[1] == ORC_BC_OUTLET) ? malloc(sizeof(double) * 5 * (size_t)NF) : NULL;
   #pragma omp parallel for schedule(static)
   for (int c = 0; c < N; ++c) {
     int xyz[3];
@@ -902,6 +943,20 @@ int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, do
       diag[(size_t)(dim + 1) * N + c] = Ph;
       diag[(size_t)(dim + 2) * N + c] = D;
     }
+    if (obnew && xyz[0] >= p->nx - 2) {
+      int col = xyz[0] == p->nx - 1 ? 0 : 1, f = xyz[1] + p->ny * xyz[2];
+      obnew[(2 * col) * NF + f] = Ph;
+      obnew[(2 * col + 1) * NF + f] = uc[0];
+      if (col == 0) obnew[4 * NF + f] = r;
+    }
+  }
+  /* characteristic outlet: keep this step's outlet columns, then advance P_b
+   * with them to the boundary pressure of the next step */
+  if (obnew) {
+    memcpy(p->ob + NF, obnew, sizeof(double) * 5 * (size_t)NF);
+    double pb = outlet_pb(p);
+    for (int f = 0; f < NF; ++f) p->ob[f] = pb;
+    free(obnew);
   }
 
   /* 6: global FP64 reduction -> P0^{n+1} */
@@ -954,8 +1009,11 @@ int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, do
  *   out[5]    sum over the outlet column of rho u_x cp T, and
  *   out[6]    of rho u_x cp: their ratio is the mixing-cup temperature T_m of
  *             Sec. 4.2, eq. Tmean-def (0 / 0 without an outlet). */
-int orc_diagnostics(const orc_params* p, const double* phi, const double* g, const double* T,
+int orc_diagnostics(const orc_params* p_in, const double* phi, const double* g, const double* T,
                     const double* Y, const double* Ts, const double* scal, double* out) {
+  orc_params pc = *p_in; /* the inlet speed of the next step */
+  pc.u_in = scal[9];
+  const orc_params* p = &pc;
   lat_t L = lattice_of(p->dim);
   int N = ncell(p), dim = p->dim;
   double* gin = malloc(sizeof(double) * (size_t)L.Q * N);

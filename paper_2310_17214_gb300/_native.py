@@ -37,7 +37,8 @@ class Desc(C.Structure):
         ("p0_mode", C.c_int), ("P0", C.c_double),
         ("Ts_field", C.c_int), ("Ts_uniform", C.c_double),
         ("rhocp_s", C.c_double), ("lambda_s", C.c_double), ("phi_min", C.c_double),
-        ("T_max", C.c_double), ("stream", C.c_void_p), ("device", C.c_int),
+        ("T_max", C.c_double), ("outlet_nscbc", C.c_int), ("nscbc_sigma", C.c_double),
+        ("stream", C.c_void_p), ("device", C.c_int),
     ]
 
 
@@ -61,7 +62,7 @@ class Scalars(C.Structure):
     _fields_ = [("P0", C.c_double), ("P0_prev", C.c_double), ("mass", C.c_double),
                 ("I", C.c_double), ("flux_in", C.c_double), ("flux_out", C.c_double),
                 ("step", C.c_longlong), ("status", C.c_int), ("u_in", C.c_double),
-                ("fuel", C.c_double)]
+                ("fuel", C.c_double), ("outlet_pb", C.c_double)]
 
 
 class Diagnostics(C.Structure):
@@ -183,6 +184,8 @@ def make_desc(prob: dict, precision: str = "fp64", stream: int = 0, device: int 
     d.rhocp_s, d.lambda_s = prob.get("rhocp_s", 1.0), prob.get("lambda_s", 0.0)
     d.phi_min = prob.get("phi_min", 1e-6)
     d.T_max = prob.get("T_max", 0.0)
+    if prob.get("outlet") == "nscbc":
+        d.outlet_nscbc, d.nscbc_sigma = 1, float(prob.get("nscbc_sigma", 0.25))
     d.stream = stream
     d.device = device
     return d

@@ -141,7 +141,7 @@ void free_buffers(pflb_domain* d) {
   void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.M[0], d->B.M[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
                   d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
                   d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats, d->B.tile_ctr,
-                  d->B.feed_part};
+                  d->B.feed_part, d->B.ob};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::memset(&d->B, 0, sizeof(d->B));
@@ -191,6 +191,12 @@ int validate_desc(const pflb_domain_desc& D, std::string& msg) {
   if (D.Ts_field && !(D.rhocp_s > 0)) return bad(PFLB_ERR_ARG, "rhocp_s must be > 0");
   if (!(D.A_u >= 0 && D.A_T >= 0 && D.lambda_s >= 0 && D.phi_min >= 0 && D.T_max >= 0))
     return bad(PFLB_ERR_ARG, "A_u, A_T, lambda_s, phi_min, T_max must be >= 0");
+  if (D.inlet_parabolic < 0 || D.inlet_parabolic > 2) return bad(PFLB_ERR_ARG, "bad inlet profile");
+  if (D.outlet_nscbc != 0 && D.outlet_nscbc != 1) return bad(PFLB_ERR_ARG, "bad outlet_nscbc");
+  if (D.outlet_nscbc && D.bc[1] != PFLB_BC_OUTLET)
+    return bad(PFLB_ERR_ARG, "the characteristic outlet needs an outlet face");
+  if (D.outlet_nscbc && !(D.nscbc_sigma > 0 && std::isfinite(D.nscbc_sigma)))
+    return bad(PFLB_ERR_ARG, "nscbc_sigma must be positive");
   return PFLB_OK;
 }
 
@@ -427,6 +433,7 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   al((void**)&d->B.counter, sizeof(unsigned));
   al((void**)&d->B.tile_ctr, 2 * sizeof(unsigned));
   al((void**)&d->B.feed_part, kFeedBlocks * sizeof(double));
+  if (D.outlet_nscbc) al(&d->B.ob, (size_t)5 * D.ny * (D.dim == 3 ? D.nz : 1) * d->real_sz);
   if (!ok) {
     cudaGetLastError();
     free_buffers(d);
@@ -447,6 +454,9 @@ int pflb_set_mechanism(pflb_domain* d, const pflb_mechanism* m) {
     if (m->inlet_feedback > 0 &&
         (d->desc.bc[0] != PFLB_BC_INLET || d->desc.p0_mode != PFLB_P0_FIXED))
       return fail(d, PFLB_ERR_ARG, "the inlet feedback needs an inlet face and a fixed P0");
+    if (m->inlet_feedback > 0 && d->desc.inlet_parabolic == 2)
+      return fail(d, PFLB_ERR_UNSUPPORTED,
+                  "the inlet feedback needs an inlet profile of fixed shape (0 or 1)");
   }
   if (d->has_fields) return fail(d, PFLB_ERR_STATE, "set_mechanism must precede set_fields");
   cudaSetDevice(d->desc.device);
@@ -566,6 +576,7 @@ int pflb_get_scalars(pflb_domain* d, pflb_scalars* out) {
   out->status = h.status;
   out->u_in = h.u_in;
   out->fuel = h.fuel;
+  out->outlet_pb = h.pb;
   if (h.status != 0) return fail(d, h.status, "%s", status_message(h.status));
   return PFLB_OK;
 }
@@ -1130,6 +1141,8 @@ int pflb_create_batch(pflb_domain** domains, int n, pflb_batch** out) {
     if (!d->L || !d->has_fields) return bfail(nullptr, PFLB_ERR_STATE, "set_fields must come first");
     if (d->L->batch_entry_bytes() == 0)
       return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "only 2-D domains without species batch");
+    if (d->desc.outlet_nscbc)
+      return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "the characteristic outlet steps alone");
     if (d->L->batch_key() != domains[0]->L->batch_key())
       return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "domains of a batch share one precision");
     if (d->desc.device != domains[0]->desc.device)

@@ -156,6 +156,9 @@ struct Params {
   // feed_c = 1 / (rho_in / P0 Y_in[k] A) so that u_in = fuel feed_c / P0
   int feed, feed_k;
   double feed_c;
+  // characteristic outlet (Sec. 4.1): on, and K = sigma cs / nx
+  int nscbc;
+  double nscbc_K;
 };
 
 // Scalar state on the device.  The per-step quantities the cells need (P0,
@@ -173,6 +176,9 @@ struct DevScalars {
   // (inlet feedback; otherwise u_in stays the description's value)
   double u_in, fuel;
   float u_in_f, pad_f2;
+  // boundary pressure of the next step at the characteristic outlet
+  double pb;
+  float pb_f, pad_f3;
 };
 
 // FP16 storage keeps, per cell, the FP32 moments (P, j) = (sum g*, sum c g*)
@@ -202,6 +208,8 @@ struct State {
   DevScalars* scal;
   double* partials;        // this step's block partials: [blocks][4]
   unsigned* counter;
+  Real* ob;                // characteristic outlet: P_h, u_x of columns nx-1 and nx-2 and rho
+                           // of column nx-1 of this step, [5][ny nz] (else null)
 };
 
 // ----------------------------------------------------- storage codecs
@@ -258,6 +266,9 @@ template <> __device__ __forceinline__ float scal_P0<float>(const DevScalars* s)
 template <class Real> __device__ __forceinline__ Real scal_u_in(const DevScalars* s);
 template <> __device__ __forceinline__ double scal_u_in<double>(const DevScalars* s) { return s->u_in; }
 template <> __device__ __forceinline__ float scal_u_in<float>(const DevScalars* s) { return s->u_in_f; }
+template <class Real> __device__ __forceinline__ Real scal_pb(const DevScalars* s);
+template <> __device__ __forceinline__ double scal_pb<double>(const DevScalars* s) { return s->pb; }
+template <> __device__ __forceinline__ float scal_pb<float>(const DevScalars* s) { return s->pb_f; }
 template <class Real> __device__ __forceinline__ Real scal_dlnP0(const DevScalars* s);
 template <> __device__ __forceinline__ double scal_dlnP0<double>(const DevScalars* s) { return s->dlnP0; }
 template <> __device__ __forceinline__ float scal_dlnP0<float>(const DevScalars* s) { return s->dlnP0_f; }
@@ -629,7 +640,7 @@ __device__ __forceinline__ Real first_order(const MA& A, int i, int src, int dx,
 template <class Real, int K>
 __device__ __forceinline__ Real inlet_u(const Params<Real, K>& P, Real u, const int xyz[3],
                                         int dim) {
-  if (!P.inlet_parabolic) return u;
+  if (P.inlet_parabolic != 1) return u;
   for (int a = 1; a < dim; ++a) {
     if (P.bc[2 * a] != BC_WALL) continue;
     Real n = Real(a == 1 ? P.ny : P.nz);
@@ -737,6 +748,7 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
     Real uu = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) uu += uw[a] * uw[a];
+    const Real pb2 = P.nscbc ? Real(2) * scal_pb<Real>(S.scal) : Real(0);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       if (L::c(i, 0) != -1) continue;
@@ -744,11 +756,12 @@ __device__ __forceinline__ void pull(const Params<Real, K>& P, const State<Real,
 #pragma unroll
       for (int a = 0; a < DIM; ++a) cu += Real(L::c(i, a)) * uw[a];
       gin[i] = -own_pop<DIM, Real, Store>(P, S, c, L::opp(i), mom) +
-               Real(L::w(i)) * rho_c * (Real(3) * cu * cu - uu);
+               Real(L::w(i)) * (pb2 + rho_c * (Real(3) * cu * cu - uu));
     }
   }
   if (f0 && P.bc[0] == BC_INLET) {
-    const Real ui = inlet_u(P, P.feed ? scal_u_in<Real>(S.scal) : P.u_in, xyz, DIM);
+    Real ui = inlet_u(P, P.feed ? scal_u_in<Real>(S.scal) : P.u_in, xyz, DIM);
+    if (P.inlet_parabolic == 2) ui *= Real(1) - S.phi[c];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
       if (L::c(i, 0) != 1) continue;
@@ -1303,6 +1316,14 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
 #pragma unroll
   for (int a = 0; a < DIM; ++a) uG += u[a] * G[a];
   const Real Ph = sg + Real(0.5) * (rho * CS2 * D + uG);
+  if (P.nscbc && xyz[0] >= P.nx - 2) {
+    // the two outlet columns of this step for the characteristic outlet
+    const int NF = P.ny * P.nz, f = xyz[1] + P.ny * xyz[2];
+    const int col = xyz[0] == P.nx - 1 ? 0 : 1;
+    S.ob[(size_t)(2 * col) * NF + f] = Ph;
+    S.ob[(size_t)(2 * col + 1) * NF + f] = u[0];
+    if (col == 0) S.ob[(size_t)4 * NF + f] = rho;
+  }
   const Real omega = fdiv(Real(2) * rho, rho + Real(6) * mu);
   const Real src_w = Real(1) - Real(0.5) * omega;
   // f_eq / rho - w = w e with e = 3 cu + 9/2 cu^2 - 3/2 uu;
@@ -1636,11 +1657,41 @@ static __global__ void feed_combine_kernel(const double* __restrict__ part, unsi
   }
 }
 
-// The inlet speed of the first step (and no consumption yet).
+// The inlet speed of the first step (and no consumption yet); the
+// characteristic outlet starts at the ambient pressure.
 static __global__ void set_inlet_kernel(DevScalars* scal, double u_in) {
   scal->u_in = u_in;
   scal->u_in_f = float(u_in);
   scal->fuel = 0.0;
+  scal->pb = 0.0;
+  scal->pb_f = 0.f;
+}
+
+// ------------------------------------------------ characteristic outlet
+// Sec. 4.1 (Poinsot and Lele): after a step, one block forms the face means
+// of the outlet columns it wrote (fixed-order FP64 sums) and advances the
+// boundary pressure, P_b <- P_b - (L5 + K P_b) / 2 with
+// L5 = (u + cs)((P1 - P2) + rho cs (u1 - u2)).
+template <class Real>
+__global__ void __launch_bounds__(BLOCK)
+outlet_kernel(const Real* __restrict__ ob, int NF, DevScalars* scal, double K) {
+  __shared__ double red_sh[32];
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int f = threadIdx.x; f < NF; f += BLOCK)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] += double(ob[(size_t)q * NF + f]);
+  double m[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) m[q] = block_sum<double>(v[q], red_sh) / NF;
+  if (threadIdx.x == 0) {
+    const double cs = 0.57735026918962576;  // sqrt(1/3)
+    const double P1 = m[0], u1 = m[1], P2 = m[2], u2 = m[3], r = m[4];
+    const double pb = scal->pb;
+    const double L5 = (u1 + cs) * ((P1 - P2) + r * cs * (u1 - u2));
+    const double nb = pb - 0.5 * (L5 + K * pb);
+    scal->pb = nb;
+    scal->pb_f = float(nb);
+  }
 }
 
 // ------------------------------------------------ initial equilibrium

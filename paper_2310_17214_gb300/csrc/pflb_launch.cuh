@@ -37,6 +37,7 @@ struct Buffers {
   unsigned* counter;
   unsigned* tile_ctr;      // tile counters of the persistent step, one per parity
   double* feed_part;       // inlet feedback block partials [kFeedBlocks]
+  void* ob;                // characteristic outlet columns [5][ny nz] (compute type)
   int N;
   long long slots;         // partial slots per buffer (>= blocks of any launch)
   int pending;             // the last step's partials are not combined yet
@@ -247,6 +248,8 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
       }
     P.feed_c = 1.0 / (rin * m.Y_in[P.feed_k] * area);
   }
+  P.nscbc = (d.outlet_nscbc && d.bc[1] == PFLB_BC_OUTLET) ? 1 : 0;
+  P.nscbc_K = P.nscbc ? d.nscbc_sigma * std::sqrt(1.0 / 3.0) / d.nx : 0.0;
   // FP16 residual scale: residuals |r / w| from 4 down to 3.7e-9 (lattice
   // units) stay in the normal FP16 range; smaller ones keep an absolute
   // resolution of 3.6e-12 as subnormals
@@ -305,6 +308,7 @@ struct LauncherImpl final : Launcher {
     S.scal = B.scal;
     S.partials = B.partials + (size_t)4 * B.slots * cur;
     S.counter = B.counter;
+    S.ob = static_cast<Real*>(B.ob);
     return S;
   }
   int blocks() const { return (P.N + BLOCK - 1) / BLOCK; }
@@ -630,6 +634,9 @@ struct LauncherImpl final : Launcher {
         e = feed(B, cur, st);
         if (e != cudaSuccess) return e;
       }
+      if (P.nscbc)
+        outlet_kernel<Real><<<1, BLOCK, 0, st>>>(static_cast<const Real*>(B.ob), P.ny * P.nz,
+                                                 B.scal, P.nscbc_K);
       B.pending = p0_closed ? 0 : 1;
       B.last_parity = cur;
       cur = 1 - cur;

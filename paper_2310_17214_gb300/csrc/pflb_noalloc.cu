@@ -60,6 +60,8 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
     if (rc != PFLB_OK) return err(rc, why);
   }
   if (D.dim != 2) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports D2Q9 only");
+  if (D.outlet_nscbc)
+    return err(PFLB_ERR_UNSUPPORTED, "the characteristic outlet needs a domain (pflb_create_domain)");
   if (mech && mech->inlet_feedback)
     return err(PFLB_ERR_UNSUPPORTED, "the inlet feedback needs a domain (pflb_create_domain)");
   if (K != 0 && K != 5) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports K = 0 or 5");
@@ -158,6 +160,7 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
   scalars->status = h.status;
   scalars->u_in = D.u_in;  // no inlet feedback on this path
   scalars->fuel = 0.0;
+  scalars->outlet_pb = 0.0;
   if (h.status != 0) return err(h.status, status_message(h.status));
   return PFLB_OK;
 }

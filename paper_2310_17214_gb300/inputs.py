@@ -601,6 +601,59 @@ def config6_fields(p, blend=4.0):
     return {"phi": np.zeros(nx * ny), "T": T, "Y": Y, "Ts": None, "u": None}
 
 
+def wall_phi(d, eta):
+    """Solid fraction at signed distance d from a wall (d > 0 in the fluid),
+    Sec. 4, eq. def-phi: 1/2 [1 - sin(pi d / eta)] across |d| < eta/2."""
+    d = np.asarray(d, dtype=np.float64)
+    return np.where(d <= -eta / 2, 1.0,
+                    np.where(d >= eta / 2, 0.0, 0.5 * (1.0 - np.sin(np.pi * d / eta))))
+
+
+def di_channel(L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, A_u=145.0, sharp=False):
+    """Isothermal channel of Sec. 4.1 (Fig. A_u-vs-MSE): width L cells between
+    two planar walls, inlet-outlet distance H = 5 L, uniform inlet speed,
+    characteristic (non-reflecting) outlet, Re = u_in L / nu = 100, air at
+    300 K everywhere.  Diffuse form: solid layers `solid` cells thick on both
+    sides with eq. def-phi interfaces of width eta centred on the walls, the
+    inlet speed weighted by the fluid fraction, drag A_u.  Sharp form
+    (sharp=True): the same channel with the walls as half-way bounce-back
+    lattice walls and no phase field (the coupling of Sec. 4 switched off)."""
+    H = 5 * L if H is None else H
+    ny = L if sharp else L + 2 * solid
+    p = _base(2, H, ny)
+    lattice_air(p, u_in * L / Re)
+    p["bc"] = ["inlet", "outlet", "wall", "wall", "periodic", "periodic"]
+    p.update({"u_in": u_in, "inlet_parabolic": 0 if sharp else 2, "outlet": "nscbc",
+              "A_u": 0.0 if sharp else A_u, "A_T": 0.0, "eta": float(eta), "T_in": 300.0,
+              "Ts_uniform": 300.0, "p0_mode": "fixed", "L": L, "solid": 0 if sharp else solid,
+              "name": f"channel_{'si' if sharp else 'di'}_L{L}_eta{eta}_Re{Re:g}"})
+    return p
+
+
+def di_channel_fields(p):
+    """Phase field of the channel walls (zero in the sharp form)."""
+    nx, ny, s, L = p["nx"], p["ny"], p["solid"], p["L"]
+    yc = np.arange(ny) + 0.5
+    d = np.minimum(yc - s, (s + L) - yc)
+    col = wall_phi(d, p["eta"]) if s > 0 else np.zeros(ny)
+    phi = np.repeat(col[:, None], nx, axis=1).reshape(-1)
+    return {"phi": phi, "T": np.full(nx * ny, 300.0), "Y": None, "Ts": None, "u": None}
+
+
+def channel_mse(u_si, u_di, p_si, p_di, at=0.9):
+    """Mean standard error of Sec. 4.1, eq. mean-standard-error-f: the
+    streamwise velocity across the cross-section at x = at H of the diffuse
+    run against the sharp run, over the bulk fluid eta/2 <= y <= L - eta/2
+    (y from the wall), normalised by the sharp profile's maximum."""
+    L, eta, s = p_si["L"], p_di["eta"], p_di["solid"]
+    xs = int(round(at * p_si["nx"])) - 1
+    f_si = np.asarray(u_si).reshape(p_si["ny"], p_si["nx"])[:, xs]
+    f_di = np.asarray(u_di).reshape(p_di["ny"], p_di["nx"])[s:s + L, xs]
+    y = np.arange(L) + 0.5
+    m = (y >= eta / 2) & (y <= L - eta / 2)
+    return float(np.mean(((f_si[m] - f_di[m]) / np.max(f_si)) ** 2))
+
+
 def with_initial_u(p, fields):
     """Initial velocity: the inlet profile times the fluid fraction."""
     N = fields["phi"].size

@@ -544,3 +544,58 @@ def test_inlet_feedback_is_refused_where_unsupported():
     p["p0_mode"] = "closed"
     with pytest.raises(PflbError, match="feedback"):
         Domain(p, "fp64")
+
+
+# ------------------------------------------------ characteristic outlet
+@pytest.mark.parametrize("precision,kern", [("fp64", "tiled"), ("fp64", "persistent"),
+                                            ("fp32", "tiled")])
+def test_characteristic_outlet_diffuse_channel(precision, kern):
+    """Diffuse-wall channel of Sec. 4.1 (eq. def-phi walls, fluid-fraction
+    inlet, drag A_u) with the characteristic outlet, against the oracle after
+    1200 steps (the start-up pressure wave has met the outlet): fields and the
+    boundary pressure within 1e-10 (FP64; FP32 1e-4 L2 in u and 1e-4 in P_b
+    relative to the pressure scale rho u_in^2)."""
+    p = I.di_channel(L=20, eta=4, solid=4, H=100, A_u=145.0)
+    f = I.di_channel_fields(p)
+    ora = O.OracleState(p, f["phi"], f["T"])
+    dom = Domain(p, precision)
+    dom.set_phase_field(f["phi"])
+    dom.set_fields(f["T"], None)
+    dom.select_kernel(kern)
+    for _ in range(4):
+        ora.step(300)
+        dom.step(300)
+    pb_ref = ora.outlet_pressure[0]
+    pb = dom.scalars()["outlet_pb"]
+    assert pb_ref != 0.0
+    got = dom.get("u", "g")
+    u, _, _ = ora.moments()
+    if precision == "fp64":
+        assert abs(pb - pb_ref) <= FP64_TOL * abs(pb_ref)
+        assert maxrel(got["u"], u) <= FP64_TOL
+        assert maxrel(got["g"], ora.g.reshape(ora.Q, ora.N)) <= FP64_TOL
+    else:
+        assert abs(pb - pb_ref) <= 1e-4 * p["u_in"] ** 2
+        assert l2rel(got["u"], u) <= 1e-4
+    dom.close()
+
+
+def test_characteristic_outlet_3d_march_fp64():
+    """The characteristic outlet on the 3-D z-march kernel: a wall-bounded
+    3-D channel (ragged 37 x 12 x 10) against the oracle, 400 steps."""
+    p = small_case(3, 37, 12, 10, bc=["inlet", "outlet", "wall", "wall", "wall", "wall"],
+                   u_in=0.04, inlet_parabolic=1, outlet="nscbc", nu=0.05)
+    N = 37 * 12 * 10
+    f = {"phi": np.zeros(N), "T": np.full(N, 300.0), "Y": None, "Ts": None}
+    ora = O.OracleState(p, f["phi"], f["T"])
+    dom = Domain(p, "fp64")
+    dom.set_phase_field(f["phi"])
+    dom.set_fields(f["T"], None)
+    dom.select_kernel("march")
+    ora.step(400)
+    dom.step(400)
+    assert ora.outlet_pressure[0] != 0.0
+    assert abs(dom.scalars()["outlet_pb"] / ora.outlet_pressure[0] - 1) <= FP64_TOL
+    u, _, _ = ora.moments()
+    assert maxrel(dom.get("u"), u) <= FP64_TOL
+    dom.close()

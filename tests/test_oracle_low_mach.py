@@ -99,3 +99,78 @@ def test_inlet_feedback_off_keeps_the_set_inlet_speed():
     p, s, _ = _flame_1d(nx=64, feedback=False)
     s.step(20)
     assert s.u_in == p["u_in"] == 0.0
+
+
+# ------------------------------------------------ characteristic outlet
+def _pulse_channel(outlet, nx=400, steps=700):
+    """A right-going plane acoustic pulse (P_h = rho cs u) in a 1-D channel
+    with a closed inlet; returns the acoustic energy before and after the
+    pulse has met the outlet."""
+    p = I._base(2, nx, 1)
+    I.lattice_air(p, 0.01)
+    p["bc"] = ["inlet", "outlet", "periodic", "periodic", "periodic", "periodic"]
+    p["u_in"] = 0.0
+    if outlet == "nscbc":
+        p["outlet"] = "nscbc"
+    x = np.arange(nx)
+    Ph = 1e-3 * np.exp(-((x - nx // 2) / 10.0) ** 2)
+    cs = 3.0 ** -0.5
+    u = np.zeros((2, nx))
+    u[0] = Ph / cs
+    s = O.OracleState(p, np.zeros(nx), np.full(nx, 300.0), u=u, Ph=Ph)
+
+    def energy():
+        uu, rho, ph = s.moments()
+        return float(np.sum(0.5 * ph ** 2 / (rho * cs * cs) + 0.5 * rho * uu[0] ** 2))
+
+    E0 = energy()
+    s.step(steps)
+    return E0, energy()
+
+
+def test_characteristic_outlet_absorbs_a_plane_pulse():
+    """Sec. 4.1 uses the non-reflecting outlet of Poinsot and Lele because a
+    fixed-pressure outlet reflects sound: a plane pulse leaving through a
+    P_h = 0 outlet comes back with almost all its energy (amplitude
+    reflection about 0.93 after viscous loss), through the characteristic
+    outlet with less than 2 % of it (reflection below 0.15)."""
+    E0, E1 = _pulse_channel("fixed")
+    assert np.sqrt(E1 / E0) > 0.9
+    E0, E1 = _pulse_channel("nscbc")
+    assert np.sqrt(E1 / E0) < 0.15
+
+
+def test_characteristic_outlet_keeps_the_steady_channel_flow():
+    """In a steady channel flow the outlet condition must not change the flow:
+    the velocity field with the characteristic outlet matches the one with
+    P_h = 0 to 2e-3 of the peak speed (only the pressure level moves: the
+    boundary pressure settles where the incoming wave balances the outgoing
+    one), and it no longer changes."""
+    res = {}
+    for outlet in ("fixed", "nscbc"):
+        p = I._base(2, 160, 24)
+        I.lattice_air(p, 0.05)
+        p["bc"] = ["inlet", "outlet", "wall", "wall", "periodic", "periodic"]
+        p.update({"u_in": 0.04, "inlet_parabolic": 1})
+        if outlet == "nscbc":
+            p["outlet"] = "nscbc"
+        s = O.OracleState(p, np.zeros(160 * 24), np.full(160 * 24, 300.0))
+        s.step(8000)
+        res[outlet] = (s.moments()[0][0], s)
+    ref = res["fixed"][0]
+    got, s = res["nscbc"]
+    assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max()
+    pb = s.outlet_pressure
+    assert np.all(pb == pb[0]) and pb[0] > 0
+    s.step(1000)
+    assert np.abs(s.moments()[0][0] - got).max() <= 2e-4 * np.abs(ref).max()
+
+
+def test_diffuse_channel_inlet_carries_the_sharp_channel_flux():
+    """Inlet profile 2 (uniform speed times the fluid fraction) over the
+    diffuse walls of eq. def-phi carries u_in times the channel width: the
+    fluid fractions of a wall interface sum to the sharp wall position."""
+    q = I.di_channel(L=50, eta=8, solid=8)
+    phi = I.di_channel_fields(q)["phi"].reshape(q["ny"], q["nx"])[:, 0]
+    assert abs(np.sum(1.0 - phi) - 50.0) <= 1e-12
+    assert phi[0] == 1.0 and phi[q["ny"] // 2] == 0.0
