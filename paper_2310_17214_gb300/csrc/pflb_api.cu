@@ -876,6 +876,8 @@ int pflb_set_surrogate(pflb_domain* d, const pflb_mlp* net, const pflb_surrogate
   if (d->mech.chem_mode != PFLB_CHEM_SURROGATE || d->K != 6)
     return fail(d, PFLB_ERR_STATE, "mechanism is not in surrogate mode");
   if (s->n_elem < 0 || s->n_elem > 4) return fail(d, PFLB_ERR_ARG, "n_elem");
+  if (s->engine != PFLB_MLP_TCGEN05 && s->engine != PFLB_MLP_WARP_MMA)
+    return fail(d, PFLB_ERR_ARG, "engine");
   SurrArgs a;
   std::memset(&a, 0, sizeof(a));
   a.net = mlp_net(net);
@@ -890,6 +892,7 @@ int pflb_set_surrogate(pflb_domain* d, const pflb_mlp* net, const pflb_surrogate
     a.y_std[k] = float(s->y_std[k]);
   }
   a.n_elem = s->n_elem;
+  a.engine = s->engine;
   a.tol = s->tol;
   a.theta_s = s->theta_s;
   a.tol_f = float(s->tol);

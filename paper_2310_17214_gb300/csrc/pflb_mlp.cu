@@ -351,7 +351,7 @@ int grid_for(long long rows, int per_block) {
   return (int)b;
 }
 
-Net net_of(const pflb_mlp* m) { return Net{m->wf, m->wb, m->bias}; }
+Net net_of(const pflb_mlp* m) { return Net{m->wf, m->wb, m->bias, m->theta}; }
 
 }  // namespace
 

@@ -44,6 +44,7 @@ struct Net {
   const __nv_bfloat16* wf;  // NPAD
   const __nv_bfloat16* wb;  // NPAD
   const float* bias;        // NPB
+  const float* theta;       // NPARAM FP32 master parameters (flat order above)
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

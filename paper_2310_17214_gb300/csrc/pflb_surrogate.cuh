@@ -28,10 +28,71 @@ struct SurrArgs {
   double Pj[6][6];          // projection onto element-conserving increments
   double tol;
   float E_f[4][6], Pj_f[6][6], tol_f, theta_f;  // the same in FP32
+  int engine;               // 0: tcgen05 network kernel, 1: warp-level mma.sync kernel
   int* fb_idx;              // fallback cell list
   unsigned* fb_count;
   double* stats;            // [0] fallback cells, [1] cells evaluated by the network
 };
+
+// Per-cell use of the network's raw outputs o[0..5] for live cell c:
+// de-normalise, test the bounding box and the element residuals, project and
+// write the source, or leave the source zero and report the cell for the
+// fallback (returns true).  Cells below phi_min get a zero source.
+template <int K, class Real, class Store>
+__device__ __forceinline__ bool surrogate_post_cell(const Params<Real, K>& P,
+                                                    const State<Real, Store>& S,
+                                                    const SurrArgs& A, Real* __restrict__ src,
+                                                    long long c, const float* raw, const Real* Y,
+                                                    Real T, Real phif, Real P0, const float* o,
+                                                    unsigned& evaluated, unsigned& fallbacks) {
+  bool reject = false;
+  Real om[6], omT = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) om[k] = 0;
+  if (phif >= P.phi_min) {
+    ++evaluated;
+    bool ok = true;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) ok = ok && raw[f] >= A.lo[f] && raw[f] <= A.hi[f];
+    // post-processing in the compute precision (FP64 domains keep FP64)
+    constexpr bool D64 = sizeof(Real) == 8;
+    Real dY[6];
+    const Real th = D64 ? Real(A.theta_s) : Real(A.theta_f);
+    const Real sc = th > Real(0) ? fexp(-fdiv(th, T)) : Real(1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dY[k] = sc * (Real(o[k]) * Real(A.y_std[k]) + Real(A.y_mean[k]));
+    const Real tol = D64 ? Real(A.tol) : Real(A.tol_f);
+    for (int e = 0; e < A.n_elem; ++e) {
+      Real r = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) r += (D64 ? Real(A.E[e][k]) : Real(A.E_f[e][k])) * dY[k];
+      ok = ok && fabs(r) <= tol;
+    }
+    if (ok) {
+      Real pY[6], cpn = 0, hsum = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        Real sum = 0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sum += (D64 ? Real(A.Pj[k][q]) : Real(A.Pj_f[k][q])) * dY[q];
+        pY[k] = sum;
+        cpn += (Y[k] + sum) * P.cp[k];
+        hsum += P.hf[k] * sum;
+      }
+      const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
+#pragma unroll
+      for (int k = 0; k < 6; ++k) om[k] = rho * pY[k];
+      omT = rho * mixture_cp(P, Y) * fdiv(-hsum, cpn);
+    } else {
+      ++fallbacks;
+      reject = true;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) src[(size_t)k * P.N + c] = om[k];
+  src[(size_t)6 * P.N + c] = omT;
+  return reject;
+}
 
 template <int K, class Real, class Store>
 __global__ void __launch_bounds__(256, 2)
@@ -91,52 +152,11 @@ chem_surrogate_kernel(const Params<Real, K> P, const State<Real, Store> S, Real*
     __syncwarp();
     bool reject = false;
     if (live) {
-      Real om[6], omT = 0;
+      float o[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) om[k] = 0;
-      if (phif >= P.phi_min) {
-        ++evaluated;
-        bool ok = true;
-#pragma unroll
-        for (int f = 0; f < 8; ++f) ok = ok && raw[f] >= A.lo[f] && raw[f] <= A.hi[f];
-        // post-processing in the compute precision (FP64 domains keep FP64)
-        constexpr bool D64 = sizeof(Real) == 8;
-        Real dY[6];
-        const Real th = D64 ? Real(A.theta_s) : Real(A.theta_f);
-        const Real sc = th > Real(0) ? fexp(-fdiv(th, T)) : Real(1);
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-          dY[k] = sc * (Real(ys[warp][lane * 8 + k]) * Real(A.y_std[k]) + Real(A.y_mean[k]));
-        const Real tol = D64 ? Real(A.tol) : Real(A.tol_f);
-        for (int e = 0; e < A.n_elem; ++e) {
-          Real r = 0;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) r += (D64 ? Real(A.E[e][k]) : Real(A.E_f[e][k])) * dY[k];
-          ok = ok && fabs(r) <= tol;
-        }
-        if (ok) {
-          Real pY[6], cpn = 0, hsum = 0;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            Real s = 0;
-#pragma unroll
-            for (int m = 0; m < 6; ++m) s += (D64 ? Real(A.Pj[k][m]) : Real(A.Pj_f[k][m])) * dY[m];
-            pY[k] = s;
-            cpn += (Y[k] + s) * P.cp[k];
-            hsum += P.hf[k] * s;
-          }
-          const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
-#pragma unroll
-          for (int k = 0; k < 6; ++k) om[k] = rho * pY[k];
-          omT = rho * mixture_cp(P, Y) * fdiv(-hsum, cpn);
-        } else {
-          ++fallbacks;
-          reject = true;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 6; ++k) src[(size_t)k * P.N + c] = om[k];
-      src[(size_t)6 * P.N + c] = omT;
+      for (int k = 0; k < 6; ++k) o[k] = ys[warp][lane * 8 + k];
+      reject = surrogate_post_cell<K, Real, Store>(P, S, A, src, c, raw, Y, T, phif, P0, o,
+                                                   evaluated, fallbacks);
     }
     // ordered, warp-aggregated append of the rejected cells: neighbouring
     // cells stay together in the list, so the integrator's warps see

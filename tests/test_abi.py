@@ -51,7 +51,8 @@ def test_struct_layouts_are_plain_c(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     mirrors = {"pflb_domain_desc": nat.Desc, "pflb_mechanism": nat.Mechanism,
-               "pflb_scalars": nat.Scalars, "pflb_diagnostics": nat.Diagnostics}
+               "pflb_scalars": nat.Scalars, "pflb_diagnostics": nat.Diagnostics,
+               "pflb_surrogate": nat.Surrogate}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pflb.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')

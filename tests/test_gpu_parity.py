@@ -553,8 +553,9 @@ def test_characteristic_outlet_diffuse_channel(precision, kern):
     """Diffuse-wall channel of Sec. 4.1 (eq. def-phi walls, fluid-fraction
     inlet, drag A_u) with the characteristic outlet, against the oracle after
     1200 steps (the start-up pressure wave has met the outlet): fields and the
-    boundary pressure within 1e-10 (FP64; FP32 1e-4 L2 in u and 1e-4 in P_b
-    relative to the pressure scale rho u_in^2)."""
+    boundary pressure within 1e-10 (FP64).  FP32: 1e-4 L2 in u, and P_b within
+    1e-5 lattice pressure units (3e-5 of the pressure scale rho cs^2; P_b
+    integrates 1200 FP32 differences of the outlet columns)."""
     p = I.di_channel(L=20, eta=4, solid=4, H=100, A_u=145.0)
     f = I.di_channel_fields(p)
     ora = O.OracleState(p, f["phi"], f["T"])
@@ -575,7 +576,7 @@ def test_characteristic_outlet_diffuse_channel(precision, kern):
         assert maxrel(got["u"], u) <= FP64_TOL
         assert maxrel(got["g"], ora.g.reshape(ora.Q, ora.N)) <= FP64_TOL
     else:
-        assert abs(pb - pb_ref) <= 1e-4 * p["u_in"] ** 2
+        assert abs(pb - pb_ref) <= 1e-5
         assert l2rel(got["u"], u) <= 1e-4
     dom.close()
 

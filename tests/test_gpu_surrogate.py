@@ -273,3 +273,55 @@ def test_trained_surrogate_tracks_the_flame_and_beats_newton():
     sur.close()
     ref.close()
     net.close()
+
+
+def _raw_inputs(dom, p):
+    g = dom.get("T", "Y")
+    P0 = dom.scalars()["P0"]
+    N = g["T"].size
+    return np.column_stack([g["T"], g["Y"].T, np.full(N, P0)])
+
+
+def test_network_engines_match_the_reference_mlp():
+    """The surrogate's network on tcgen05 (tensor-memory accumulators, 128
+    cells per MMA) and on warp-level mma.sync, through the chemistry
+    increments of a domain whose record accepts every cell unchanged
+    (no element test or projection, unit output scale): each engine within
+    2e-2 of the FP64 reference MLP at the BF16-rounded parameters and
+    inputs (the forward bar), and the two engines within 2e-3 of each
+    other (same BF16 operands, FP32 accumulation in a different order)."""
+    from paper_2310_17214_gb300._native import MLP_ENGINES
+    p, f = _flame_case(nx=200, ny=40, chem="surrogate", precision="fp32")
+    theta, _, _ = case(1, 3)
+    net = Mlp()
+    net.set_params(theta)
+    dom = _domain(p, f, "fp32")
+    rec = _surrogate_record(p, tol=-1.0)
+    dom.set_surrogate(net, rec)
+    dom.step(20)  # every cell by Newton: a state through ignition
+    X = _raw_inputs(dom, p)
+    fluid = np.flatnonzero(1.0 - f["phi"] >= 1e-6)
+    mean, std = X[fluid].mean(axis=0), X[fluid].std(axis=0)
+    std[std == 0] = 1.0
+    out = {}
+    for name in ("tcgen05", "warp_mma"):
+        r = _surrogate_record(p)
+        for k in range(8):
+            r.x_mean[k], r.x_std[k] = mean[k], std[k]
+            r.lo[k], r.hi[k] = -1e30, 1e30
+        for k in range(6):
+            r.y_mean[k], r.y_std[k] = 0.0, 1.0
+        r.theta_s, r.n_elem, r.tol = 0.0, 0, 1e30
+        r.engine = MLP_ENGINES[name]
+        dom.set_surrogate(net, r)
+        dY, _ = dom.chem_increments()
+        out[name] = dY[:, fluid]
+    xn = (X[fluid] - mean) / std
+    ref, _ = M.forward(bf16_round(theta), bf16_round(xn.astype(np.float32)))
+    ref = ref[:, :6].T
+    scale = np.max(np.abs(ref))
+    for name, got in out.items():
+        assert np.max(np.abs(got - ref)) <= 2e-2 * scale, name
+    assert np.max(np.abs(out["tcgen05"] - out["warp_mma"])) <= 2e-3 * scale
+    dom.close()
+    net.close()
