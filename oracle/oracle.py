@@ -58,6 +58,7 @@ class OrcParams(C.Structure):
         ("suth_Tk", C.c_double * KMAX), ("suth_Sk", C.c_double * KMAX),
         ("feedback", C.c_int), ("fb_k", C.c_int),
         ("nscbc", C.c_int), ("nscbc_K", C.c_double), ("ob", C.POINTER(C.c_double)),
+        ("moving", C.c_int), ("u_s", C.c_double * 3),
     ]
 
 
@@ -98,6 +99,7 @@ def lib():
         L.orc_step.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_void_p]
         L.orc_run.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, C.c_int]
         L.orc_diagnostics.argtypes = [P, dp, dp, dp, dp, C.c_void_p, dp, dp]
+        L.orc_phase_at.argtypes = [P, dp, C.c_double, dp]
         L.orc_mixture_transport.argtypes = [P, C.c_double, dp, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
         L.orc_set_threads.argtypes = [C.c_int]
@@ -169,6 +171,11 @@ def make_params(prob: dict) -> OrcParams:
     p.p_ref = prob.get("p_ref", 101325.0)
     if prob.get("inlet_feedback") is not None:
         p.feedback, p.fb_k = 1, int(prob["inlet_feedback"])
+    us = prob.get("u_s")
+    if us is not None and any(float(v) != 0.0 for v in us):
+        p.moving = 1
+        for a in range(3):
+            p.u_s[a] = float(us[a]) if a < len(us) else 0.0
     if prob.get("outlet") == "nscbc":
         # K = sigma cs (1 - Ma^2) / l with l the domain length (Ma^2 << 1 dropped)
         p.nscbc = 1
@@ -241,6 +248,13 @@ class OracleState:
         ph = np.zeros(self.N)
         lib().orc_moments(C.byref(self.p), self.phi, self.g, self.T, self.Y, self.scal, u, rho, ph)
         return u.reshape(dim, self.N), rho, ph
+
+    def phase(self):
+        """Solid fraction of the step the state is at (a moving solid is
+        displaced by steps x u_s from the field it was created with)."""
+        out = np.zeros(self.N)
+        lib().orc_phase_at(C.byref(self.p), self.phi, float(self.scal[6]), out)
+        return out
 
     def diagnostics(self):
         """Drag force (dim), heat from the solid, fluid mass, outlet mixing-cup

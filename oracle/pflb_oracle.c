@@ -114,6 +114,15 @@ typedef struct {
   int nscbc;
   double nscbc_K;
   double* ob;
+  /* Moving solid (v_I != 0, Sec. 2: the indicator is carried by the
+   * interface velocity, d chi/dt = d_t chi + v_I . grad chi = 0): the solid
+   * translates rigidly with the uniform velocity u_s (lattice units).  The
+   * phase field of step n is the given one (step 0) displaced by n u_s,
+   * multilinear interpolation between cells (periodic axes wrap, others
+   * clamp); the drag acts on u - u_s; the solid temperature is carried with
+   * u_s (upwind, as the FD convection of T). */
+  int moving;
+  double u_s[3];
 } orc_params;
 
 /* ---------------------------------------------------------------- lattices */
@@ -651,7 +660,14 @@ int orc_fd_phase(const orc_params* p, const double* phi, const double* T, const 
           double kp = 0.5 * (phis + vp[a].phi) * Lams;
           dif += kp * (vp[a].Ts - v0.Ts) - km * (v0.Ts - vm[a].Ts);
         }
-        Tsn[c] = v0.Ts + (dif - phif * SI) / (phis * Cs);
+        /* a moving solid carries its temperature with u_s (upwind) */
+        double advs = 0;
+        for (int a = 0; a < dim; ++a) {
+          double us = p->u_s[a];
+          if (us > 0) advs += us * (v0.Ts - vm[a].Ts);
+          else if (us < 0) advs += us * (vp[a].Ts - v0.Ts);
+        }
+        Tsn[c] = v0.Ts + (dif - phif * SI) / (phis * Cs) - advs;
       } else {
         Tsn[c] = v0.Ts;
       }
@@ -727,6 +743,43 @@ static int is_outlet_cell(const orc_params* p, const int xyz[3]) {
   return p->bc[1] == ORC_BC_OUTLET && xyz[0] == p->nx - 1;
 }
 
+/* Phase field of step n of a moving solid: the step-0 field phi0 displaced
+ * by s = n u_s, phi_n(x) = phi0(x - s), multilinear interpolation between
+ * the cells around x - s (periodic axes wrap, other axes clamp).  Without
+ * motion phi0 itself. */
+static const double* phase_at(const orc_params* p, const double* phi0, double n, double* buf) {
+  if (!p->moving) return phi0;
+  int N = ncell(p), dim = p->dim;
+  int ish[3] = {0, 0, 0};
+  double fr[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) {
+    double sa = n * p->u_s[a];
+    ish[a] = (int)floor(sa);
+    fr[a] = sa - ish[a];
+  }
+  #pragma omp parallel for schedule(static)
+  for (int c = 0; c < N; ++c) {
+    int xyz[3];
+    coords(p, c, xyz);
+    double v = 0;
+    for (int corner = 0; corner < (1 << dim); ++corner) {
+      double w = 1;
+      int q[3] = {xyz[0], xyz[1], xyz[2]};
+      for (int a = 0; a < dim; ++a) {
+        int up = (corner >> a) & 1; /* 0: x - i, 1: x - i - 1 */
+        w *= up ? fr[a] : 1.0 - fr[a];
+        int n_a = extent(p, a), qa = xyz[a] - ish[a] - up;
+        if (p->bc[2 * a] == ORC_BC_PERIODIC) qa = ((qa % n_a) + n_a) % n_a;
+        else qa = qa < 0 ? 0 : (qa >= n_a ? n_a - 1 : qa);
+        q[a] = qa;
+      }
+      v += w * phi0[q[0] + p->nx * (q[1] + p->ny * q[2])];
+    }
+    buf[c] = v;
+  }
+  return buf;
+}
+
 /* Pull + moments for every cell: gin (Q*N), u (dim*N), rho (N), Kd (N). */
 static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, const double* gs,
                                const double* T, const double* Y, double P0, double* gin_all,
@@ -752,7 +805,8 @@ static void stream_and_moments(const orc_params* p, lat_t L, const double* phi, 
         double m = 0;
         for (int i = 0; i < L.Q; ++i) m += L.c[i][a] * gin[i];
         m /= CS2;
-        uc[a] = (m + 0.5 * p->Fb[a]) / (r + 0.5 * kd);
+        /* rho u = m + F/2, F = F_b - K_d (u - u_s), implicit in u */
+        uc[a] = (m + 0.5 * p->Fb[a] + 0.5 * kd * p->u_s[a]) / (r + 0.5 * kd);
       }
       for (int a = 0; a < dim; ++a) uw[a] = uc[a];
     }
@@ -811,11 +865,13 @@ int orc_init(const orc_params* p, const double* phi, double* g, const double* T,
 
 /* Velocity, density and sum-of-populations pressure that the next step will
  * see at every cell (pull + moments of the current state, no collision). */
-int orc_moments(const orc_params* p_in, const double* phi, const double* g, const double* T,
+int orc_moments(const orc_params* p_in, const double* phi0, const double* g, const double* T,
                 const double* Y, const double* scal, double* u, double* rho, double* Ph) {
   orc_params pc = *p_in; /* the inlet speed of the next step */
   pc.u_in = scal[9];
   const orc_params* p = &pc;
+  double* phibuf = p->moving ? malloc(sizeof(double) * (size_t)ncell(p)) : NULL;
+  const double* phi = phase_at(p, phi0, scal[6], phibuf);
   lat_t L = lattice_of(p->dim);
   int N = ncell(p);
   double* gin = malloc(sizeof(double) * (size_t)L.Q * N);
@@ -828,6 +884,7 @@ int orc_moments(const orc_params* p_in, const double* phi, const double* g, cons
     Ph[c] = s;
   }
   free(gin); free(Kd); free(mu);
+  if (phibuf) free(phibuf);
   return 0;
 }
 
@@ -873,12 +930,15 @@ static double inlet_area(const orc_params* p) {
   return a;
 }
 
-int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, double* Y,
+int orc_step(const orc_params* p_in, const double* phi0, double* g, double* T, double* Y,
              double* Ts, double* scal, double* diag) {
   /* the inlet speed of this step is scal[9] (the feedback moves it) */
   orc_params pc = *p_in;
   pc.u_in = scal[9];
   const orc_params* p = &pc;
+  /* a moving solid: the phase field of this step (scal[6] steps taken) */
+  double* phibuf = p->moving ? malloc(sizeof(double) * (size_t)ncell(p)) : NULL;
+  const double* phi = phase_at(p, phi0, scal[6], phibuf);
   double fuel = p->feedback ? fuel_consumed(p, phi, T, Y, scal[0]) : 0.0;
   lat_t L = lattice_of(p->dim);
   int N = ncell(p), dim = p->dim, K = p->K;
@@ -920,7 +980,7 @@ int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, do
       double rm = eos_rho(p, P0, mixture_Mw(p, vm.Y), vm.T);
       double rp = eos_rho(p, P0, mixture_Mw(p, vp.Y), vp.T);
       G[a] = CS2 * 0.5 * (rp - rm);
-      F[a] = p->Fb[a] - Kd[c] * uc[a];
+      F[a] = p->Fb[a] - Kd[c] * (uc[a] - p->u_s[a]);
     }
     double sg = 0;
     for (int i = 0; i < L.Q; ++i) sg += gin[(size_t)i * N + c];
@@ -994,6 +1054,7 @@ int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, do
   }
 
   free(gin); free(u); free(rho); free(Kd); free(mu); free(Tn); free(Yn); free(DTm);
+  if (phibuf) free(phibuf);
   if (Tsn) free(Tsn);
   return 0;
 }
@@ -1009,11 +1070,13 @@ int orc_step(const orc_params* p_in, const double* phi, double* g, double* T, do
  *   out[5]    sum over the outlet column of rho u_x cp T, and
  *   out[6]    of rho u_x cp: their ratio is the mixing-cup temperature T_m of
  *             Sec. 4.2, eq. Tmean-def (0 / 0 without an outlet). */
-int orc_diagnostics(const orc_params* p_in, const double* phi, const double* g, const double* T,
+int orc_diagnostics(const orc_params* p_in, const double* phi0, const double* g, const double* T,
                     const double* Y, const double* Ts, const double* scal, double* out) {
   orc_params pc = *p_in; /* the inlet speed of the next step */
   pc.u_in = scal[9];
   const orc_params* p = &pc;
+  double* phibuf = p->moving ? malloc(sizeof(double) * (size_t)ncell(p)) : NULL;
+  const double* phi = phase_at(p, phi0, scal[6], phibuf);
   lat_t L = lattice_of(p->dim);
   int N = ncell(p), dim = p->dim;
   double* gin = malloc(sizeof(double) * (size_t)L.Q * N);
@@ -1032,7 +1095,7 @@ int orc_diagnostics(const orc_params* p_in, const double* phi, const double* g, 
     own(p, phi, T, Y, p->Ts_field ? Ts : NULL, N, c, &v);
     derive(p, &v, scal[0], &d);
     double phis = v.phi, phif = 1.0 - phis;
-    for (int a = 0; a < dim; ++a) out[a] += Kd[c] * u[(size_t)a * N + c];
+    for (int a = 0; a < dim; ++a) out[a] += Kd[c] * (u[(size_t)a * N + c] - p->u_s[a]);
     int fluid_on = phif >= p->phi_min;
     int solid_on = p->Ts_field ? (phis >= p->phi_min) : 1;
     if (fluid_on && solid_on) out[3] += phif * (p->A_T * d.lam * phif * phis * phis / eta2 * (v.Ts - v.T));
@@ -1043,6 +1106,7 @@ int orc_diagnostics(const orc_params* p_in, const double* phi, const double* g, 
     }
   }
   free(gin); free(u); free(rho); free(Kd); free(mu);
+  if (phibuf) free(phibuf);
   return 0;
 }
 
@@ -1053,6 +1117,13 @@ int orc_run(const orc_params* p, const double* phi, double* g, double* T, double
 }
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* The phase field of step n into out (N). */
+int orc_phase_at(const orc_params* p, const double* phi0, double n, double* out) {
+  const double* ph = phase_at(p, phi0, n, out);
+  if (ph != out) memcpy(out, ph, sizeof(double) * (size_t)ncell(p));
+  return 0;
+}
 
 /* Host threads used by the per-cell loops (n <= 0: all cores); returns the
  * number in effect (1 without OpenMP). */
