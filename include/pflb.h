@@ -133,6 +133,14 @@ typedef struct pflb_domain_desc {
                               outlet face; pflb_batch_step and pflb_step_noalloc refuse it.
                               0: P_h = 0. */
   double nscbc_sigma;      /* relaxation factor sigma of K (e.g. 0.25) */
+  double u_s[3];           /* velocity of a rigidly translating solid (lattice units; Sec. 2,
+                              the interface velocity v_I).  Nonzero: the phase field given to
+                              pflb_set_phase_field is the one of step 0 and the phase field of
+                              step n is it displaced by n u_s (multilinear interpolation between
+                              cells; periodic axes wrap, other axes clamp), the drag acts on
+                              u - u_s and the solid temperature is carried with u_s (upwind).
+                              pflb_batch_step and pflb_step_noalloc refuse it.  Zero: a static
+                              solid. */
   void* stream;            /* cudaStream_t (NULL = legacy default stream) */
   int device;              /* CUDA device ordinal */
 } pflb_domain_desc;

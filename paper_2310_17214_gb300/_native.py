@@ -38,6 +38,7 @@ class Desc(C.Structure):
         ("Ts_field", C.c_int), ("Ts_uniform", C.c_double),
         ("rhocp_s", C.c_double), ("lambda_s", C.c_double), ("phi_min", C.c_double),
         ("T_max", C.c_double), ("outlet_nscbc", C.c_int), ("nscbc_sigma", C.c_double),
+        ("u_s", C.c_double * 3),
         ("stream", C.c_void_p), ("device", C.c_int),
     ]
 
@@ -189,6 +190,8 @@ def make_desc(prob: dict, precision: str = "fp64", stream: int = 0, device: int 
     d.T_max = prob.get("T_max", 0.0)
     if prob.get("outlet") == "nscbc":
         d.outlet_nscbc, d.nscbc_sigma = 1, float(prob.get("nscbc_sigma", 0.25))
+    for a, v in enumerate(prob.get("u_s", [])[:3]):
+        d.u_s[a] = float(v)
     d.stream = stream
     d.device = device
     return d

@@ -141,7 +141,7 @@ void free_buffers(pflb_domain* d) {
   void* ptrs[] = {d->B.g[0], d->B.g[1], d->B.M[0], d->B.M[1], d->B.T[0], d->B.T[1], d->B.Y[0], d->B.Y[1],
                   d->B.Ts[0], d->B.Ts[1], d->B.phi, d->B.scal, d->B.partials, d->B.counter,
                   d->B.src, d->B.fb_idx, d->B.fb_count, d->B.chem_stats, d->B.tile_ctr,
-                  d->B.feed_part, d->B.ob};
+                  d->B.feed_part, d->B.ob, d->B.phi0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::memset(&d->B, 0, sizeof(d->B));
@@ -197,6 +197,8 @@ int validate_desc(const pflb_domain_desc& D, std::string& msg) {
     return bad(PFLB_ERR_ARG, "the characteristic outlet needs an outlet face");
   if (D.outlet_nscbc && !(D.nscbc_sigma > 0 && std::isfinite(D.nscbc_sigma)))
     return bad(PFLB_ERR_ARG, "nscbc_sigma must be positive");
+  for (int a = 0; a < 3; ++a)
+    if (!(std::fabs(D.u_s[a]) < 0.3)) return bad(PFLB_ERR_ARG, "|u_s| must be below 0.3");
   return PFLB_OK;
 }
 
@@ -434,6 +436,8 @@ int pflb_create_domain(const pflb_domain_desc* desc, pflb_domain** out) {
   al((void**)&d->B.tile_ctr, 2 * sizeof(unsigned));
   al((void**)&d->B.feed_part, kFeedBlocks * sizeof(double));
   if (D.outlet_nscbc) al(&d->B.ob, (size_t)5 * D.ny * (D.dim == 3 ? D.nz : 1) * d->real_sz);
+  if (D.u_s[0] != 0.0 || D.u_s[1] != 0.0 || (D.dim == 3 && D.u_s[2] != 0.0))
+    al(&d->B.phi0, n * d->real_sz);
   if (!ok) {
     cudaGetLastError();
     free_buffers(d);
@@ -496,6 +500,9 @@ int pflb_set_phase_field(pflb_domain* d, const void* phi, const void* Ts, int dt
   if (r) return r;
   CK(d, cudaSetDevice(d->desc.device));
   if ((r = upload(d, phi, dtype, where, d->B.phi, d->N))) return r;
+  if (d->B.phi0)  // a moving solid: this is the phase field of step 0
+    CK(d, cudaMemcpyAsync(d->B.phi0, d->B.phi, (size_t)d->N * d->real_sz,
+                          cudaMemcpyDeviceToDevice, d->stream));
   if (d->desc.Ts_field) {
     if (Ts) {
       if ((r = upload(d, Ts, dtype, where, d->B.Ts[d->cur], d->N))) return r;
@@ -544,6 +551,7 @@ int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, i
   d->L->set_wait_limit(d->wait_limit);
   d->B.pending = 0;
   cudaError_t e = d->L->init(d->B, d->cur, u, d->desc.P0, d->stream);
+  if (e == cudaSuccess) e = d->L->set_step(d->B, 0, d->stream);
   if (u) cudaFreeAsync(u, d->stream);
   CK(d, e);
   d->has_fields = true;
@@ -796,10 +804,17 @@ int pflb_set_state(pflb_domain* d, const void* src, size_t bytes, int where) {
   const cudaMemcpyKind k = where == PFLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(d, cudaMemcpyAsync(d->B.scal, in + sizeof(h), sizeof(DevScalars), k, d->stream));
   d->B.pending = 0;
-  return for_each_array(d, [&](size_t off, void* p, size_t b) {
+  int rc = for_each_array(d, [&](size_t off, void* p, size_t b) {
     CK(d, cudaMemcpyAsync(p, in + off, b, k, d->stream));
     return PFLB_OK;
   });
+  if (rc != PFLB_OK) return rc;
+  // the step count of the restored state (a moving solid's phase field)
+  DevScalars sc;
+  if (where == PFLB_HOST) std::memcpy(&sc, in + sizeof(h), sizeof(sc));
+  else CK(d, cudaMemcpy(&sc, in + sizeof(h), sizeof(sc), cudaMemcpyDeviceToHost));
+  if (d->L) CK(d, d->L->set_step(d->B, sc.step, d->stream));
+  return PFLB_OK;
 }
 
 int pflb_set_wait_limit(pflb_domain* d, long long cycles) {
@@ -1146,6 +1161,8 @@ int pflb_create_batch(pflb_domain** domains, int n, pflb_batch** out) {
       return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "only 2-D domains without species batch");
     if (d->desc.outlet_nscbc)
       return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "the characteristic outlet steps alone");
+    if (d->B.phi0)
+      return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "a moving solid steps alone");
     if (d->L->batch_key() != domains[0]->L->batch_key())
       return bfail(nullptr, PFLB_ERR_UNSUPPORTED, "domains of a batch share one precision");
     if (d->desc.device != domains[0]->desc.device)

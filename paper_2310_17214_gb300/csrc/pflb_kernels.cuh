@@ -159,6 +159,9 @@ struct Params {
   // characteristic outlet (Sec. 4.1): on, and K = sigma cs / nx
   int nscbc;
   double nscbc_K;
+  // moving solid (Sec. 2, interface velocity): rigid translation velocity
+  int moving;
+  Real u_s[3];
 };
 
 // Scalar state on the device.  The per-step quantities the cells need (P0,
@@ -1186,7 +1189,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
       for (int i = 0; i < Q; ++i)
         if (L::c(i, a) != 0) m += Real(L::c(i, a)) * gin[i];
       mraw[a] = m;
-      u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) * inv_rk;
+      u[a] = (m * Real(3) + Real(0.5) * (P.Fb[a] + Kd * P.u_s[a])) * inv_rk;
       uw[a] = u[a];
     }
   }
@@ -1290,6 +1293,17 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
         dif += kp * (at(F_TS, a, +1) - Ts0) - km * (Ts0 - at(F_TS, a, -1));
       }
       Tsn = Ts0 + fdiv(dif - phif * SI, phis * P.Cs);
+      if (P.moving) {
+        // a moving solid carries its temperature with u_s (upwind)
+        Real advs = 0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const Real us = P.u_s[a];
+          if (us > Real(0)) advs += us * (Ts0 - at(F_TS, a, -1));
+          else if (us < Real(0)) advs += us * (at(F_TS, a, +1) - Ts0);
+        }
+        Tsn -= advs;
+      }
     }
     S.Ts_out[c] = Tsn;
   }
@@ -1308,7 +1322,7 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     G[a] = CS2 * Real(0.5) * (at(F_RHO, a, +1) - at(F_RHO, a, -1));
-    F[a] = P.Fb[a] - Kd * u[a];
+    F[a] = P.Fb[a] - Kd * (u[a] - P.u_s[a]);
   }
   // P_h: the pulled zeroth moment plus half the zeroth moment of the source,
   // sum_i Xi_i = u.G + rho cs^2 D, so that a step adds the whole source
@@ -1667,6 +1681,40 @@ static __global__ void set_inlet_kernel(DevScalars* scal, double u_in) {
   scal->pb_f = 0.f;
 }
 
+// ------------------------------------------------ moving solid
+// Phase field of step n of a rigidly translating solid: the step-0 field phi0
+// displaced by s = n u_s, multilinear interpolation between the cells around
+// x - s; per axis the host passes the whole shift ish and the fraction fr in
+// [0, 1).  Periodic axes wrap, other axes clamp.
+template <int DIM, class Real>
+__global__ void __launch_bounds__(BLOCK)
+phase_shift_kernel(const Real* __restrict__ phi0, Real* __restrict__ phi, int nx, int ny, int nz,
+                   int per_mask, int3 ish, Real fx, Real fy, Real fz) {
+  const int c = blockIdx.x * BLOCK + threadIdx.x;
+  const int N = nx * ny * nz;
+  if (c >= N) return;
+  const int xyz[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
+  const int ext[3] = {nx, ny, nz}, sh[3] = {ish.x, ish.y, ish.z};
+  const Real fr[3] = {fx, fy, fz};
+  Real v = 0;
+#pragma unroll
+  for (int corner = 0; corner < (1 << DIM); ++corner) {
+    Real w = 1;
+    int q[3] = {xyz[0], xyz[1], xyz[2]};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int up = (corner >> a) & 1;
+      w *= up ? fr[a] : Real(1) - fr[a];
+      int qa = xyz[a] - sh[a] - up;
+      if ((per_mask >> a) & 1) qa = ((qa % ext[a]) + ext[a]) % ext[a];
+      else qa = qa < 0 ? 0 : (qa >= ext[a] ? ext[a] - 1 : qa);
+      q[a] = qa;
+    }
+    v += w * phi0[q[0] + nx * (q[1] + ny * q[2])];
+  }
+  phi[c] = v;
+}
+
 // ------------------------------------------------ characteristic outlet
 // Sec. 4.1 (Poinsot and Lele): after a step, one block forms the face means
 // of the outlet columns it wrote (fixed-order FP64 sums) and advances the
@@ -1774,7 +1822,7 @@ moments_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __re
     for (int a = 0; a < DIM; ++a) {
       Real m = 0;
       for (int i = 0; i < Q; ++i) m += Real(L::c(i, a)) * gin[i];
-      u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) / (rho + Real(0.5) * Kd);
+      u[a] = (m * Real(3) + Real(0.5) * (P.Fb[a] + Kd * P.u_s[a])) / (rho + Real(0.5) * Kd);
       uw[a] = u[a];
     }
   }
@@ -1828,11 +1876,11 @@ diag_kernel(const Params<Real, K> P, const State<Real, Store> S, double* __restr
       for (int a = 0; a < DIM; ++a) {
         Real m = 0;
         for (int i = 0; i < Q; ++i) m += Real(L::c(i, a)) * gin[i];
-        u[a] = (m * Real(3) + Real(0.5) * P.Fb[a]) / (rho + Real(0.5) * Kd);
+        u[a] = (m * Real(3) + Real(0.5) * (P.Fb[a] + Kd * P.u_s[a])) / (rho + Real(0.5) * Kd);
         uw[a] = u[a];
       }
     }
-    for (int a = 0; a < DIM; ++a) v[a] = double(Kd * u[a]);
+    for (int a = 0; a < DIM; ++a) v[a] = double(Kd * (u[a] - P.u_s[a]));
     const Real Ts = P.Ts_field ? S.Ts_in[c] : P.Ts_uniform;
     const bool fluid_on = phif >= P.phi_min;
     const bool solid_on = P.Ts_field ? (phis >= P.phi_min) : true;

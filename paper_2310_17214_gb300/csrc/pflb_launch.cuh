@@ -38,6 +38,8 @@ struct Buffers {
   unsigned* tile_ctr;      // tile counters of the persistent step, one per parity
   double* feed_part;       // inlet feedback block partials [kFeedBlocks]
   void* ob;                // characteristic outlet columns [5][ny nz] (compute type)
+  void* phi0;              // moving solid: the phase field of step 0 (phi is the current one)
+  long long nstep;         // steps taken (host copy; the phase field of a moving solid)
   int N;
   long long slots;         // partial slots per buffer (>= blocks of any launch)
   int pending;             // the last step's partials are not combined yet
@@ -124,6 +126,9 @@ struct Launcher {
   virtual cudaError_t diagnostics(const Buffers& B, int cur, double* part, double* out,
                                   cudaStream_t st) = 0;
   virtual int diag_blocks() const = 0;
+  // steps taken is n (after init or a restored state): a moving solid's phase
+  // field becomes the one of step n
+  virtual cudaError_t set_step(Buffers& B, long long n, cudaStream_t st) = 0;
 };
 
 constexpr double R_GAS = 8.314;  // J/(mol K), value printed in Sec. 3.1
@@ -248,6 +253,8 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
       }
     P.feed_c = 1.0 / (rin * m.Y_in[P.feed_k] * area);
   }
+  P.moving = (d.u_s[0] != 0.0 || d.u_s[1] != 0.0 || (d.dim == 3 && d.u_s[2] != 0.0)) ? 1 : 0;
+  for (int a = 0; a < 3; ++a) P.u_s[a] = Real(a < d.dim ? d.u_s[a] : 0.0);
   P.nscbc = (d.outlet_nscbc && d.bc[1] == PFLB_BC_OUTLET) ? 1 : 0;
   P.nscbc_K = P.nscbc ? d.nscbc_sigma * std::sqrt(1.0 / 3.0) / d.nx : 0.0;
   // FP16 residual scale: residuals |r / w| from 4 down to 3.7e-9 (lattice
@@ -333,6 +340,27 @@ struct LauncherImpl final : Launcher {
         P, S, static_cast<const Real*>(u_init), P0);
     set_inlet_kernel<<<1, 1, 0, st>>>(B.scal, u_in0);
     return cudaGetLastError();
+  }
+  // phase field of step n of a moving solid from the step-0 field
+  cudaError_t phase(const Buffers& B, long long n, cudaStream_t st) const {
+    int per = 0;
+    for (int a = 0; a < DIM; ++a)
+      if (P.bc[2 * a] == BC_PERIODIC) per |= 1 << a;
+    int sh[3] = {0, 0, 0};
+    double fr[3] = {0, 0, 0};
+    for (int a = 0; a < DIM; ++a) {
+      const double sa = double(n) * double(P.u_s[a]);
+      sh[a] = (int)std::floor(sa);
+      fr[a] = sa - sh[a];
+    }
+    phase_shift_kernel<DIM, Real><<<blocks(), BLOCK, 0, st>>>(
+        static_cast<const Real*>(B.phi0), static_cast<Real*>(B.phi), P.nx, P.ny, P.nz, per,
+        make_int3(sh[0], sh[1], sh[2]), Real(fr[0]), Real(fr[1]), Real(fr[2]));
+    return cudaGetLastError();
+  }
+  cudaError_t set_step(Buffers& B, long long n, cudaStream_t st) override {
+    B.nstep = n;
+    return P.moving ? phase(B, n, st) : cudaSuccess;
   }
   // inlet feedback after the step whose input state is buffer `cur`
   cudaError_t feed(const Buffers& B, int cur, cudaStream_t st) const {
@@ -637,6 +665,11 @@ struct LauncherImpl final : Launcher {
       if (P.nscbc)
         outlet_kernel<Real><<<1, BLOCK, 0, st>>>(static_cast<const Real*>(B.ob), P.ny * P.nz,
                                                  B.scal, P.nscbc_K);
+      ++B.nstep;
+      if (P.moving) {
+        e = phase(B, B.nstep, st);
+        if (e != cudaSuccess) return e;
+      }
       B.pending = p0_closed ? 0 : 1;
       B.last_parity = cur;
       cur = 1 - cur;

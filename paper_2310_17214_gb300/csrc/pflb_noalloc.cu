@@ -60,6 +60,8 @@ extern "C" int pflb_step_noalloc(const pflb_domain_desc* desc, const pflb_mechan
     if (rc != PFLB_OK) return err(rc, why);
   }
   if (D.dim != 2) return err(PFLB_ERR_UNSUPPORTED, "pflb_step_noalloc supports D2Q9 only");
+  if (D.u_s[0] != 0.0 || D.u_s[1] != 0.0 || D.u_s[2] != 0.0)
+    return err(PFLB_ERR_UNSUPPORTED, "a moving solid needs a domain (pflb_create_domain)");
   if (D.outlet_nscbc)
     return err(PFLB_ERR_UNSUPPORTED, "the characteristic outlet needs a domain (pflb_create_domain)");
   if (mech && mech->inlet_feedback)

@@ -130,7 +130,7 @@ __device__ __forceinline__ void load_b(__nv_bfloat16* dst, const float* theta, i
 // tcgen05.  Grid-strides over tiles of 128 cells; per cell the same
 // acceptance test, projection and fallback list as the warp-level kernel.
 template <int K, class Real, class Store>
-__global__ void __launch_bounds__(tc::M, 4)
+__global__ void __launch_bounds__(tc::M, 5)
 chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
                          Real* __restrict__ src, const SurrArgs A, long long wait_limit) {
   static_assert(K == 6, "the surrogate is built for the six-species mechanism");
@@ -199,21 +199,32 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
     return __syncthreads_or(ok ? 0 : 1) == 0;
   };
 
+  // the inputs of the block's next tile are loaded while the current one
+  // runs through the network
+  Real nT = 1, nphi = 0, nY[6];
+  auto fetch = [&](long long t) {
+    const long long cn = t * M + m;
+    nT = 1;
+    nphi = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nY[k] = 0;
+    if (t < tiles && cn < P.N) {
+      nT = S.T_in[cn];
+      nphi = S.phi[cn];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) nY[k] = S.Y_in[(size_t)k * P.N + cn];
+    }
+  };
+  fetch(blockIdx.x);
   for (long long tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
     const long long c = tile * M + m;
     const bool live = c < P.N;
     float raw[8];
     Real Y[6];
-    Real T = 1, phif = 0;
-    if (live) {
-      T = S.T_in[c];
-      phif = Real(1) - S.phi[c];
+    const Real T = nT, phif = Real(1) - nphi;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
-    } else {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) Y[k] = 0;
-    }
+    for (int k = 0; k < 6; ++k) Y[k] = nY[k];
+    fetch(tile + gridDim.x);
     raw[0] = float(T);
 #pragma unroll
     for (int k = 0; k < 6; ++k) raw[1 + k] = float(Y[k]);
@@ -298,6 +309,6 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
 }
 
 constexpr size_t tc_smem_bytes() { return sizeof(tc::Smem) + 128; }
-constexpr int kTcBlocksPerSm = 4;
+constexpr int kTcBlocksPerSm = 5;  // shared memory: 5 x 38 KB
 
 }  // namespace pflb
