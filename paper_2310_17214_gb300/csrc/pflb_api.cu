@@ -281,14 +281,35 @@ int check_stability(const pflb_domain_desc& D, const pflb_mechanism* m, std::str
     double mu = D.mu_ref;
     if (D.sutherland) mu *= std::pow(T / D.suth_T, 1.5) * (D.suth_T + D.suth_S) / (T + D.suth_S);
     const double rho_lat = D.P0 / (8.314 * T * invMw * D.rho_ref);
-    double a;  // lambda / (rho cp), lattice units
+    double a;        // lambda / (rho cp), lattice units
+    double lam_lat;  // lambda dt / (rho_ref dx^2) (J/kg/K)
     if (mix && m->transport == PFLB_TRANSPORT_MIXTURE) {
       double lam, cp = 0;
       mixture_mu_lam(*m, T, m->Y_in, mu, lam);
       for (int k = 0; k < m->K; ++k) cp += m->Y_in[k] * m->cp[k];
       a = lam * h2 / D.rho_ref / (rho_lat * cp);
+      lam_lat = lam * h2 / D.rho_ref;
     } else {
+      double cp = D.cp0;
+      if (mix) {
+        cp = 0;
+        for (int k = 0; k < m->K; ++k) cp += m->Y_in[k] * m->cp[k];
+      }
       a = mu * h2 / D.rho_ref / (rho_lat * D.Pr);
+      lam_lat = mu * h2 / D.rho_ref * cp / D.Pr;
+    }
+    // the solid side of the exchange: phi_f S_I / (phi_s (rho cp)_s) relaxes Ts
+    // at a rate A_T lambda phi_f^2 phi_s / (eta^2 (rho cp)_s), largest at
+    // phi_s = 1/3 (4/27); forward Euler needs it below 2
+    if (D.Ts_field && D.A_T > 0) {
+      const double rs = D.A_T * lam_lat * (4.0 / 27.0) / (D.eta * D.eta * (D.rhocp_s / D.rho_ref));
+      if (!(rs < 2.0)) {
+        std::snprintf(buf, sizeof(buf),
+                      "solid-side exchange number %.4g not below 2 at T = %g K (raise rhocp_s)",
+                      rs, T);
+        msg = buf;
+        return PFLB_ERR_UNSTABLE;
+      }
     }
     const double mu_lat = mu * h2 / D.rho_ref;
     const double tau = 0.5 + 3.0 * mu_lat / rho_lat;  // tau = 1/2 + nu / cs^2

@@ -36,6 +36,7 @@ struct Smem {
   __align__(8) uint64_t bar;
   uint32_t tmem;
   int err;
+  int layer_ok;  // the MMA group of the current layer reported in time
 };
 
 // Byte offset of element (row r, column k) in a K-major core-matrix layout
@@ -93,6 +94,21 @@ __device__ __forceinline__ void fence_before() {
 }
 __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane, without waiting:
+// the registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 // 16 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -191,12 +207,14 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
         tc::mma_bf16(tmem, da + (uint64_t)((ks * 256) >> 4), db + (uint64_t)((ks * 256) >> 4),
                      id, ks > 0 ? 1u : 0u);
       tc::mma_commit(&s.bar);
+      // one thread waits for the group; the barrier then releases the block
+      // (and makes the outcome the same for every thread)
+      s.layer_ok = mbar_wait_bounded(&s.bar, phase & 1u, wait_limit) ? 1 : 0;
     }
-    const bool ok = mbar_wait_bounded(&s.bar, phase & 1u, wait_limit);
     phase ^= 1u;
+    __syncthreads();
     fence_after();
-    // the whole block agrees on the outcome before anyone acts on it
-    return __syncthreads_or(ok ? 0 : 1) == 0;
+    return s.layer_ok != 0;
   };
 
   // the inputs of the block's next tile are loaded while the current one
@@ -247,19 +265,27 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
     for (int l = 0; l < 3 && !failed; ++l) {
       if (!run_layer(l == 0 ? da16 : da64, dws[l], ID64, l == 0 ? 1 : 4)) { failed = true; break; }
       // bias + tanh -> BF16 A operand of the next layer (K = 64)
+      // two 16-column groups in flight per wait
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float v[16];
-        tc::tmem_ld16(trow + 16 * q, v);
-        uint32_t w[8];
+      for (int h = 0; h < 2; ++h) {
+        uint32_t acc[2][16];
+        tc::tmem_ld16_async(trow + 32 * h, acc[0]);
+        tc::tmem_ld16_async(trow + 32 * h + 16, acc[1]);
+        tc::tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-          w[e] = mlp::pack_bf16(mlp::fast_tanh(v[2 * e] + bias[l][16 * q + 2 * e]),
-                                mlp::fast_tanh(v[2 * e + 1] + bias[l][16 * q + 2 * e + 1]));
-        *reinterpret_cast<uint4*>(abase + tc::kmajor_off(m, 16 * q, 64)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(abase + tc::kmajor_off(m, 16 * q + 8, 64)) =
-            make_uint4(w[4], w[5], w[6], w[7]);
+        for (int g = 0; g < 2; ++g) {
+          const int q = 2 * h + g;
+          uint32_t w[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            w[e] = mlp::pack_bf16(
+                mlp::fast_tanh(__uint_as_float(acc[g][2 * e]) + bias[l][16 * q + 2 * e]),
+                mlp::fast_tanh(__uint_as_float(acc[g][2 * e + 1]) + bias[l][16 * q + 2 * e + 1]));
+          *reinterpret_cast<uint4*>(abase + tc::kmajor_off(m, 16 * q, 64)) =
+              make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4*>(abase + tc::kmajor_off(m, 16 * q + 8, 64)) =
+              make_uint4(w[4], w[5], w[6], w[7]);
+        }
       }
     }
     if (failed || !run_layer(da64, dw3, ID16, 4)) { failed = true; break; }
@@ -282,8 +308,10 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
   if (failed) {
     // an MMA group that did not report: wait once more (bounded) for it
     // before the tensor memory is released
-    mbar_wait_bounded(&s.bar, (phase ^ 1u) & 1u, wait_limit);
-    if (threadIdx.x == 0) s.err = 1;
+    if (threadIdx.x == 0) {
+      mbar_wait_bounded(&s.bar, (phase ^ 1u) & 1u, wait_limit);
+      s.err = 1;
+    }
   }
   // counts of this warp
 #pragma unroll

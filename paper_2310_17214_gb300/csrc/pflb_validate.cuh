@@ -20,8 +20,9 @@ int validate_mech(const pflb_mechanism& m, std::string& msg);
 // Explicit-scheme limits at every temperature the description names (T_in,
 // Ts_uniform, wall temperatures, T_max): BGK relaxation time above 1/2, the
 // forward-Euler diffusion numbers of temperature, species and the solid at or
-// below 1/(2 dim), the interface exchange number A_T a / eta^2 below 2,
-// and an inlet speed below the lattice sound speed.  With m == nullptr (or
+// below 1/(2 dim), the interface exchange number A_T a / eta^2 below 2 (and
+// its solid side, A_T lambda (4/27) / (eta^2 (rho cp)_s), with a transported
+// solid temperature), and an inlet speed below the lattice sound speed.  With m == nullptr (or
 // K = 0) the gas is the single gas of the description (M0); otherwise the
 // inlet mixture of m.  PFLB_ERR_UNSTABLE with the reason in `msg`.
 int check_stability(const pflb_domain_desc& D, const pflb_mechanism* m, std::string& msg);

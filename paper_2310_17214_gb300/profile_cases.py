@@ -27,7 +27,11 @@ from ._native import Batch, Domain
 
 
 def surrogate_case(nx=2048, ny=512, precision="fp32"):
+    """The two-step bed with the trained surrogate on both network engines
+    (tcgen05 and warp-level mma.sync) beside the Newton run: CUDA-event time
+    per step of each, then two profiled steps of each."""
     import torch
+    from ._native import MLP_ENGINES
     p = I.config4(nx=nx, ny=ny, precision=precision)
     f = I.config4_fields(p)
 
@@ -42,22 +46,34 @@ def surrogate_case(nx=2048, ny=512, precision="fp32"):
     theta = S.theta_scale(p)
     stats, Xn, Yn = S.normalisation(X, D, theta)
     net, _ = S.train(Xn, Yn, epochs=30, batch=8192)
-    sd = dom_of("surrogate")
-    sd.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], 1e-6))
-    sd.set_state(d.get_state())
-    sd.step(5)
+    rec = S.make_surrogate(stats, X, theta, p["species"], 1e-6)
+    doms = {}
+    for name in ("tcgen05", "warp_mma"):
+        rec.engine = MLP_ENGINES[name]
+        sd = dom_of("surrogate")
+        sd.set_surrogate(net, rec)
+        sd.set_state(d.get_state())
+        sd.step(5)
+        doms[name] = sd
     d.step(5)
-    sd.scalars()
-    d.scalars()
+    for name, sd in list(doms.items()) + [("newton", d)]:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sd.step(20)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"{name}: {e0.elapsed_time(e1) / 20:.4f} ms per step", flush=True)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
-    sd.step(3)
+    for sd in doms.values():
+        sd.step(2)
     d.step(2)
-    sd.scalars()
-    d.scalars()
+    for sd in list(doms.values()) + [d]:
+        sd.scalars()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print("fallback/evaluated", sd.chem_stats())
+    print("fallback/evaluated", {k: v.chem_stats() for k, v in doms.items()})
 
 
 def batch_case(n=48, tile="32x16"):

@@ -117,7 +117,8 @@ def test_every_workload_passes_the_stability_checks():
     from paper_2310_17214_gb300 import inputs as I
     probs = [I.config1(), I.config2(), I.config2(precision="fp32"), I.config3(),
              I.config3_crop(64), I.config4(), I.config4(chem="surrogate"),
-             I.mixture_transport(I.config2()), I.mixture_transport(I.config3())] + I.config5()
+             I.mixture_transport(I.config2()), I.mixture_transport(I.config3()), I.config6(),
+             I.di_channel(), I.di_channel(sharp=True)] + I.config5()
     for p in probs:
         rc, msg = nat.validate(p, p.get("precision", "fp64"))
         assert rc == 0, (p.get("name"), rc, msg)
@@ -128,7 +129,8 @@ def test_create_rejects_unstable_descriptions_without_touching_the_gpu():
     thermal diffusion number above 1/6 in 3-D (the 3-D bed at the 2-D time
     step, at its hottest temperature), a species diffusion number above the
     limit (checked with the mechanism), a solid diffusion number above the
-    limit, the interface exchange number above 1, a sonic inlet."""
+    limit, the interface exchange number above 1, a sonic inlet, the solid
+    side of the exchange above 2."""
     from paper_2310_17214_gb300 import inputs as I
     L = nat.lib()
     h = ctypes.c_void_p()
@@ -165,3 +167,8 @@ def test_create_rejects_unstable_descriptions_without_touching_the_gpu():
     p["u_in"] = 0.6
     rc, msg = create(p)
     assert rc == -5 and "sound speed" in msg, msg
+    p = I.config2()
+    p["rhocp_s"] *= 1e-6  # a solid that the exchange would overshoot
+    p["lambda_s"] *= 1e-6  # (same solid diffusion number)
+    rc, msg = create(p)
+    assert rc == -5 and "solid-side exchange" in msg, msg

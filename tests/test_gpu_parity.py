@@ -620,7 +620,10 @@ def _moving_box(dim=2, ts_field=False):
     N = nx * ny * nz
     Ts = None
     if ts_field:
-        p.update({"Ts_field": 1, "rhocp_s": 2.0, "lambda_s": 0.02})
+        # solid heat capacity and conductivity twice the air's (physical units)
+        lam_air = p["mu_ref"] * p["cp0"] / p["Pr"]
+        p.update({"Ts_field": 1, "rhocp_s": 2.0 * p["rho_ref"] * p["cp0"],
+                  "lambda_s": 2.0 * lam_air})
         Ts = np.full(N, 600.0)
     T = (1.0 - phi) * 300.0 + phi * 600.0
     return p, {"phi": phi, "T": T, "Y": None, "Ts": Ts}
