@@ -402,14 +402,15 @@ typedef struct pflb_surrogate {
   double elem[4][PFLB_KMAX];    /* atoms of element e in species k */
   double elem_mass[4];          /* element molar masses (kg/mol) */
   double tol;                   /* element residual tolerance, e.g. 1e-6 */
-  int engine;                   /* network kernel: PFLB_MLP_TCGEN05 (0, tensor-memory
-                                   accumulators, 128 cells per MMA) or PFLB_MLP_WARP_MMA (1,
-                                   warp-level mma.sync); both use the network's FP32
-                                   parameters rounded to BF16 and FP32 accumulation */
+  int engine;                   /* network kernel: PFLB_MLP_WARP_MMA (0, warp-level
+                                   mma.sync, 32 cells per warp; the faster of the two on the
+                                   bench's bed) or PFLB_MLP_TCGEN05 (1, tensor-memory
+                                   accumulators, 128 cells per MMA); both use the network's
+                                   FP32 parameters rounded to BF16 and FP32 accumulation */
 } pflb_surrogate;
 
-#define PFLB_MLP_TCGEN05 0
-#define PFLB_MLP_WARP_MMA 1
+#define PFLB_MLP_WARP_MMA 0
+#define PFLB_MLP_TCGEN05 1
 
 /* Attach a trained network to a domain whose mechanism has chem_mode
  * PFLB_CHEM_SURROGATE and six species.  A cell uses the network when its

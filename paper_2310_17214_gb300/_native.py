@@ -83,7 +83,7 @@ class Surrogate(C.Structure):
     ]
 
 
-MLP_ENGINES = {"tcgen05": 0, "warp_mma": 1}
+MLP_ENGINES = {"warp_mma": 0, "tcgen05": 1}
 
 
 _lib = None

@@ -25,7 +25,7 @@ cudaError_t chem_pass_launch(const Params<Real, K>& P, const State<Real, Real>& 
       a.stats = stats;
       cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(unsigned), st);
       if (e != cudaSuccess) return e;
-      if (a.engine == 0) {
+      if (a.engine == 1) {
         // tcgen05 network: 128 cells per tile, persistent grid of 4 blocks per SM
         constexpr size_t smem = tc_smem_bytes();
         auto kern = chem_surrogate_tc_kernel<K, Real, Real>;

@@ -56,15 +56,6 @@ __device__ __forceinline__ float fast_tanh(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-// tanh of two values straight into a packed BF16 pair (inference: the next
-// layer takes BF16 operands anyway, and the BF16x2 form halves the
-// special-function work of the FP32 one)
-__device__ __forceinline__ uint32_t tanh_bf16x2(float lo, float hi) {
-  const uint32_t x = pack_bf16(lo, hi);
-  uint32_t y;
-  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
-  return y;
-}
 __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0,
                                          uint32_t b1) {
   asm volatile(
@@ -166,17 +157,6 @@ __device__ __forceinline__ void to_a(float acc[8][4], uint32_t* a) {
   }
 }
 
-// Inference form of to_a<true>: tanh in BF16x2 on the packed pairs.
-__device__ __forceinline__ void to_a_tanh_bf16(const float acc[8][4], uint32_t* a) {
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    a[4 * kk + 0] = tanh_bf16x2(acc[2 * kk][0], acc[2 * kk][1]);
-    a[4 * kk + 1] = tanh_bf16x2(acc[2 * kk][2], acc[2 * kk][3]);
-    a[4 * kk + 2] = tanh_bf16x2(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
-    a[4 * kk + 3] = tanh_bf16x2(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
-  }
-}
-
 // A fragments of a 16 x 16 BF16 input tile (row stride `ld` elements).
 __device__ __forceinline__ void x_frags(const __nv_bfloat16* x, int ld, uint32_t* a) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -201,14 +181,14 @@ __device__ __forceinline__ void forward32(const SmemFwd& s, const __nv_bfloat16*
   x_frags(x + 16 * XLD, XLD, a1);
   float c0[8][4], c1[8][4];
   layer_fwd2<0>(s.wf, s.bias, a0, a1, c0, c1);
-  to_a_tanh_bf16(c0, a0);
-  to_a_tanh_bf16(c1, a1);
+  to_a<true>(c0, a0);
+  to_a<true>(c1, a1);
   layer_fwd2<1>(s.wf, s.bias, a0, a1, c0, c1);
-  to_a_tanh_bf16(c0, a0);
-  to_a_tanh_bf16(c1, a1);
+  to_a<true>(c0, a0);
+  to_a<true>(c1, a1);
   layer_fwd2<2>(s.wf, s.bias, a0, a1, c0, c1);
-  to_a_tanh_bf16(c0, a0);
-  to_a_tanh_bf16(c1, a1);
+  to_a<true>(c0, a0);
+  to_a<true>(c1, a1);
   float o0[1][4], o1[1][4];
   layer_fwd2<3>(s.wf, s.bias, a0, a1, o0, o1);
 #pragma unroll

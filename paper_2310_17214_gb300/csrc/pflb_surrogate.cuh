@@ -28,7 +28,7 @@ struct SurrArgs {
   double Pj[6][6];          // projection onto element-conserving increments
   double tol;
   float E_f[4][6], Pj_f[6][6], tol_f, theta_f;  // the same in FP32
-  int engine;               // 0: tcgen05 network kernel, 1: warp-level mma.sync kernel
+  int engine;               // 0: warp-level mma.sync network kernel, 1: tcgen05 kernel
   int* fb_idx;              // fallback cell list
   unsigned* fb_count;
   double* stats;            // [0] fallback cells, [1] cells evaluated by the network

@@ -10,8 +10,8 @@
 // (leading byte offset) and along M or N K * 2 * 8 bytes apart (stride byte
 // offset).  One elected thread issues the MMAs and commits them to an
 // mbarrier; every warp then reads its 32 lanes of the accumulator with
-// tcgen05.ld, adds the bias, applies tanh (BF16x2) and writes the BF16
-// activations back as the next layer's A operand.  The weights are the network's FP32 master
+// tcgen05.ld, adds the bias, applies tanh and writes the BF16 activations back
+// as the next layer's A operand.  The weights are the network's FP32 master
 // parameters rounded to BF16 (round to nearest), the same values as the
 // warp-level kernel's; the accumulation is FP32.
 #pragma once
@@ -278,8 +278,9 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
           uint32_t w[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            w[e] = mlp::tanh_bf16x2(__uint_as_float(acc[g][2 * e]) + bias[l][16 * q + 2 * e],
-                                    __uint_as_float(acc[g][2 * e + 1]) + bias[l][16 * q + 2 * e + 1]);
+            w[e] = mlp::pack_bf16(
+                mlp::fast_tanh(__uint_as_float(acc[g][2 * e]) + bias[l][16 * q + 2 * e]),
+                mlp::fast_tanh(__uint_as_float(acc[g][2 * e + 1]) + bias[l][16 * q + 2 * e + 1]));
           *reinterpret_cast<uint4*>(abase + tc::kmajor_off(m, 16 * q, 64)) =
               make_uint4(w[0], w[1], w[2], w[3]);
           *reinterpret_cast<uint4*>(abase + tc::kmajor_off(m, 16 * q + 8, 64)) =
