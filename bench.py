@@ -457,6 +457,24 @@ def bed2d_leg(dev, flush, peaks, steps=50):
                          "alg_bytes_per_cell": bpc}}
 
 
+def moving_bed_leg(dev, prob, fields, static_ms, steps=20):
+    """The headline 3-D bed with its particles translating along the
+    periodic y axis (u_s = 0.002 lattice units): per step the z-march step
+    plus the kernel that writes the displaced phase field."""
+    import torch
+    st = torch.cuda.current_stream(dev)
+    p = dict(prob, u_s=[0.0, 0.002, 0.0])
+    dom = make_domain(p, fields, "fp32", dev, st.cuda_stream)
+    dom.select_kernel("march")
+    times, _, _ = time_steps(dom, steps, 3, dev, st)
+    dom.close()
+    ms = float(np.mean(times))
+    N = fields["phi"].size
+    return {"workload": workload_name(prob) + "_moving_particles", "u_s": p["u_s"],
+            "ms_per_step": ms, "mlups": N / ms / 1e3, "kernels_per_step": 2,
+            "overhead_vs_static": ms / static_ms - 1.0}
+
+
 def flame2d_leg(dev, flush, precisions=("fp32", "fp64"), settle=400, steps=200):
     """The 2-D wall-bounded flame (480 x 120 D2Q9, five species, one-step
     chemistry, isothermal walls) held by the inlet feedback: per step the fused
@@ -700,6 +718,7 @@ def main():
         extra["error_vs_fp64"] = errors_vs_fp64(prob, fields, 2000, dev, ("fp32", "fp32_fp16"))
         extra["bed_2d"] = bed2d_leg(dev, flush, peaks)
         extra["flame_2d"] = flame2d_leg(dev, flush)
+        extra["moving_bed"] = moving_bed_leg(dev, prob, fields, legs["fp32"]["ms_per_step"])
         extra["calibration_A_u"] = calibration_leg(dev)
         extra["surrogate"] = surrogate_leg(dev, flush)
         extra["batch"] = batch_leg(dev, peaks)
