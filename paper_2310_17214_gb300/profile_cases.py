@@ -16,6 +16,9 @@ at the most resident blocks; profiles two batch steps.
 step3d: the 3-D D3Q19 reactive bed (256 x 128 x 128, or its first ncols
 columns) in one precision; times 20 steps with CUDA events, then profiles
 two steps.
+step2d: the 2-D reactive bed (1024 x 256 D2Q9) in one precision with one
+kernel; times 50 steps with CUDA events (L2 flushed between steps), then
+profiles two steps.
 """
 from __future__ import annotations
 
@@ -132,6 +135,36 @@ def step3d_case(precision="fp32_fp16", ncols=256, kernel="tiled"):
     print("scalars", d.scalars())
 
 
+def step2d_case(precision="fp32", kernel="tiled", steps=50):
+    import torch
+    p = I.config2(precision=precision)
+    f = I.config2_fields(p)
+    d = Domain(p, precision)
+    d.set_phase_field(f["phi"], f["Ts"])
+    d.set_fields(f["T"], f["Y"])
+    d.select_kernel(kernel)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    d.step(5)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        d.step(1)
+        e1.record()
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    N = f["phi"].size
+    print(f"step2d {precision} {p['nx']}x{p['ny']} kernel {kernel}: "
+          f"{ms * 1e3:.1f} us/step, {N / ms / 1e3:.0f} MLUPS", flush=True)
+    torch.cuda.profiler.start()
+    d.step(2)
+    d.scalars()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "surrogate"
     if case == "surrogate":
@@ -144,5 +177,8 @@ if __name__ == "__main__":
         step3d_case(sys.argv[2] if len(sys.argv) > 2 else "fp32_fp16",
                     int(sys.argv[3]) if len(sys.argv) > 3 else 256,
                     sys.argv[4] if len(sys.argv) > 4 else "tiled")
+    elif case == "step2d":
+        step2d_case(sys.argv[2] if len(sys.argv) > 2 else "fp32",
+                    sys.argv[3] if len(sys.argv) > 3 else "tiled")
     else:
         raise SystemExit(f"unknown case {case}")
