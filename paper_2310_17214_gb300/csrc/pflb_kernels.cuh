@@ -105,6 +105,19 @@ struct Chem64 {
   double p_ref, ln_pref_R, rho_ref, dt;  // ln_pref_R = ln(p_ref / R)
 };
 
+// FP32 copy of the chemistry for the Newton fallback of the surrogate in FP32
+// domains (rate constants as logarithms: ln k = ln A + b ln T - EaR / T).
+template <int K>
+struct Chem32 {
+  static constexpr int KK = K > 0 ? K : 1;
+  float lnA[JMAX], b[JMAX], EaR[JMAX], dn[JMAX], dS_R[JMAX], dH_R[JMAX];
+  int on[JMAX], rev[JMAX];
+  float order[JMAX][KK], rorder[JMAX][KK];
+  float Ms[JMAX][KK];  // M_k s_kj
+  float invM[KK], cp[KK], hf[KK];
+  float ln_pref_R, dt;
+};
+
 // Everything in lattice units, converted once on the host (pflb_launch.cuh).
 template <class Real, int K>
 struct Params {
@@ -146,6 +159,7 @@ struct Params {
   // FP64 copy of the chemistry for the implicit Newton integrator (FP64 in
   // every precision mode: the stiff chemistry keeps double precision)
   Chem64<K> c64;
+  Chem32<K> c32;
   // mixture-averaged transport (Sec. 4.4): species Sutherland laws (lattice
   // units), modified Eucken factors, Wilke's constant factors
   int mix;
@@ -404,35 +418,41 @@ __device__ __forceinline__ void rates(const Params<Real, K>& P, Real T, const Re
 
 // Power C^o of a concentration for the reaction orders that occur (0, 1, 2,
 // 1/2: multiplications and a square root), pow() otherwise; d = dC^o/dC for
-// C > 0.
-__device__ __forceinline__ double conc_power(double C, double o, double& d) {
-  if (o == 1.0) { d = 1.0; return C; }
-  if (o == 0.0) { d = 0.0; return 1.0; }
-  if (o == 2.0) { d = 2.0 * C; return C * C; }
+// C > 0, in the precision LA of the Jacobian.
+template <class LA>
+__device__ __forceinline__ double conc_power(double C, double o, LA& d) {
+  if (o == 1.0) { d = LA(1); return C; }
+  if (o == 0.0) { d = LA(0); return 1.0; }
+  if (o == 2.0) { d = LA(2) * LA(C); return C * C; }
   if (o == 0.5) {
     const double s = sqrt(C);
-    d = s > 0.0 ? 0.5 / s : 0.0;
+    d = s > 0.0 ? LA(0.5) / LA(s) : LA(0);
     return s;
   }
-  d = C > 0.0 ? o * pow(C, o - 1.0) : 0.0;
+  d = C > 0.0 ? LA(o * pow(C, o - 1.0)) : LA(0);
   return pow(C, o);
 }
 
-// Rates w_k (kg/(m^3 s)) and their Jacobian dw_k/dz_m, z = (Y_1..Y_K, T).
-template <int K>
+// Rates w_k (kg/(m^3 s), FP64) and their Jacobian dw_k/dz_m, z = (Y_1..Y_K,
+// T), in the precision LA: FP64 for FP64 domains; FP32 for FP32 domains,
+// where the Jacobian only steers the Newton iteration and the FP64 residual
+// decides where it converges.
+template <int K, class LA>
 __device__ __forceinline__ void rates_jacobian64(const Chem64<K>& c, const double* z, double rho,
-                                                 double* w, double (*dw)[K + 1]) {
+                                                 double* w, LA (*dw)[K + 1]) {
   constexpr int KK = K > 0 ? K : 1;
   constexpr int n = K + 1;
   const double T = z[K], invT = 1.0 / T;
-  double Cc[KK], dC[KK];
+  double Cc[KK];
+  LA dC[KK];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    dC[k] = z[k] > 0 ? rho * c.invM[k] : 0.0;
-    Cc[k] = z[k] > 0 ? z[k] * dC[k] : 0.0;
+    const double d = z[k] > 0 ? rho * c.invM[k] : 0.0;
+    dC[k] = LA(d);
+    Cc[k] = z[k] > 0 ? z[k] * d : 0.0;
     w[k] = 0;
 #pragma unroll
-    for (int m = 0; m < n; ++m) dw[k][m] = 0;
+    for (int m = 0; m < n; ++m) dw[k][m] = LA(0);
   }
   double lnT = 0.0;
   bool have_lnT = false;
@@ -453,67 +473,70 @@ __device__ __forceinline__ void rates_jacobian64(const Chem64<K>& c, const doubl
       kr = kf * exp(-lnKc);
       dlkr = dlkf - (c.dH_R[j] * invT + c.dn[j]) * invT;
     }
-    double dq[K + 1];
+    LA dq[K + 1];
 #pragma unroll
-    for (int m = 0; m < n; ++m) dq[m] = 0;
+    for (int m = 0; m < n; ++m) dq[m] = LA(0);
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
       if (dir == 1 && !c.rev[j]) break;
       const double kk = dir == 0 ? kf : -kr;
-      double Pw[KK], Dp[KK], pre[K + 1], suf[K + 1];
+      double Pw[KK], pre[K + 1];
+      LA Dp[KK], suf[K + 1];
 #pragma unroll
       for (int k = 0; k < K; ++k)
         Pw[k] = conc_power(Cc[k], dir == 0 ? c.order[j][k] : c.rorder[j][k], Dp[k]);
       // prefix / suffix products: the product without factor m, no division
       pre[0] = 1.0;
-      suf[K] = 1.0;
+      suf[K] = LA(1);
 #pragma unroll
       for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] * Pw[k];
 #pragma unroll
-      for (int k = K - 1; k >= 0; --k) suf[k] = Pw[k] * suf[k + 1];
+      for (int k = K - 1; k >= 0; --k) suf[k] = LA(Pw[k]) * suf[k + 1];
       const double q = kk * pre[K];
 #pragma unroll
       for (int k = 0; k < K; ++k) w[k] += c.Ms[j][k] * q;
-      dq[K] += q * (dir == 0 ? dlkf : dlkr);
+      dq[K] += LA(q) * LA(dir == 0 ? dlkf : dlkr);
 #pragma unroll
-      for (int m = 0; m < K; ++m) dq[m] += kk * (pre[m] * suf[m + 1]) * Dp[m] * dC[m];
+      for (int m = 0; m < K; ++m) dq[m] += LA(kk * pre[m]) * suf[m + 1] * Dp[m] * dC[m];
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int m = 0; m < n; ++m) dw[k][m] += c.Ms[j][k] * dq[m];
+      for (int m = 0; m < n; ++m) dw[k][m] += LA(c.Ms[j][k]) * dq[m];
   }
 }
 
 // Solve A x = r in place (r <- x) by Gaussian elimination with partial
-// pivoting, every index a compile-time constant so that A stays in
-// registers; false if a pivot is zero.
-template <int n>
-__device__ __forceinline__ bool solve_pivoted(double (*A)[n], double* r) {
-  double dinv[n];
+// pivoting; false if a pivot is zero.  The compiler keeps a 7 x 7 matrix in
+// local memory here (the row swap after the pivot search defeats its scalar
+// replacement); a fully unrolled form with the matrix in registers was tried
+// and is slower, its register pressure spilling more than the matrix.
+template <int n, class LA>
+__device__ __forceinline__ bool solve_pivoted(LA (*A)[n], LA* r) {
+  LA dinv[n];
 #pragma unroll
   for (int col = 0; col < n; ++col) {
     int piv = col;
-    double best = fabs(A[col][col]);
+    LA best = fabs(A[col][col]);
 #pragma unroll
     for (int rr = col + 1; rr < n; ++rr) {
-      const double v = fabs(A[rr][col]);
+      const LA v = fabs(A[rr][col]);
       if (v > best) { best = v; piv = rr; }
     }
-    if (best == 0.0) return false;
+    if (best == LA(0)) return false;
 #pragma unroll
     for (int rr = col + 1; rr < n; ++rr) {
       if (rr == piv) {
 #pragma unroll
-        for (int k = col; k < n; ++k) { const double t = A[col][k]; A[col][k] = A[rr][k]; A[rr][k] = t; }
-        const double t = r[col]; r[col] = r[rr]; r[rr] = t;
+        for (int k = col; k < n; ++k) { const LA t = A[col][k]; A[col][k] = A[rr][k]; A[rr][k] = t; }
+        const LA t = r[col]; r[col] = r[rr]; r[rr] = t;
       }
     }
-    const double inv = 1.0 / A[col][col];
+    const LA inv = LA(1) / A[col][col];
     dinv[col] = inv;
 #pragma unroll
     for (int rr = col + 1; rr < n; ++rr) {
-      const double f = A[rr][col] * inv;
+      const LA f = A[rr][col] * inv;
 #pragma unroll
       for (int k = col + 1; k < n; ++k) A[rr][k] -= f * A[col][k];
       r[rr] -= f * r[col];
@@ -521,7 +544,7 @@ __device__ __forceinline__ bool solve_pivoted(double (*A)[n], double* r) {
   }
 #pragma unroll
   for (int rr = n - 1; rr >= 0; --rr) {
-    double s = r[rr];
+    LA s = r[rr];
 #pragma unroll
     for (int k = rr + 1; k < n; ++k) s -= A[rr][k] * r[k];
     r[rr] = s * dinv[rr];
@@ -539,7 +562,14 @@ __device__ __forceinline__ bool solve_pivoted(double (*A)[n], double* r) {
 // allocation of the rest of the step.  The arithmetic is laid out for a short
 // dependency chain (FP64 latency sets the time of a warp): reciprocals taken
 // once, square roots for half orders, no dynamic array indices.
-template <int K>
+// The state, the rates and the residual are FP64 in every mode; the Jacobian,
+// the Newton matrix and its elimination take the precision LA (FP64 for FP64
+// domains, FP32 for FP32 domains).  A direction from an FP32 elimination is
+// off by about cond(A) x 6e-8 of itself, so the iteration still contracts and
+// stops where the FP64 residual puts the root (the update test is relative
+// to the update, not to the FP32 rounding), and the elimination runs on the
+// FP32 pipe instead of GB300's narrow FP64 one.
+template <int K, class LA>
 __device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
                                             double T0, const double* Y0, double rho,
                                             double* dY, double* dT) {
@@ -567,8 +597,9 @@ __device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
       ok = -1;
 #pragma unroll 1
       for (int it = 0; it < 30; ++it) {
-        double w[K + 1], dw[K + 1][K + 1];
-        rates_jacobian64<K>(c, z, rho, w, dw);
+        double w[K + 1];
+        LA A[K + 1][K + 1];  // rows 0..K-1: dw_k/dz_m, then the Newton matrix
+        rates_jacobian64<K, LA>(c, z, rho, w, A);
         double cp = 0, hw = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -576,31 +607,35 @@ __device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
           hw += c.hf[k] * w[k];
         }
         const double inv_rcp = inv_rho / cp;
-        // Newton system (I - h dF/dz) dz = -(z - zs - h F)
-        double A[K + 1][K + 1], r[K + 1];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          r[k] = -(z[k] - zs[k] - hr * w[k]);
-#pragma unroll
-          for (int m = 0; m < n; ++m) A[k][m] = (k == m ? 1.0 : 0.0) - hr * dw[k][m];
-        }
-        r[K] = -(z[K] - zs[K] + h * hw * inv_rcp);
+        // Newton system (I - h dF/dz) dz = -(z - zs - h F): residual in FP64,
+        // matrix in LA, built in place (the T row first, from the rates'
+        // Jacobian, then the species rows)
+        const LA hrL = LA(hr), hL = LA(h), inv_rcpL = LA(inv_rcp);
+        const LA hwcL = LA(hw * inv_rcp / cp);
+        LA r[K + 1];
 #pragma unroll
         for (int m = 0; m < n; ++m) {
-          double dhw = 0;
+          LA dhw = LA(0);
 #pragma unroll
-          for (int k = 0; k < K; ++k) dhw += c.hf[k] * dw[k][m];
-          double dFT = -dhw * inv_rcp;
-          if (m < K) dFT += hw * c.cp[m] * inv_rcp / cp;
-          A[K][m] = (m == K ? 1.0 : 0.0) - h * dFT;
+          for (int k = 0; k < K; ++k) dhw += LA(c.hf[k]) * A[k][m];
+          LA dFT = -dhw * inv_rcpL;
+          if (m < K) dFT += hwcL * LA(c.cp[m]);
+          A[K][m] = LA(m == K ? 1 : 0) - hL * dFT;
         }
-        if (!solve_pivoted<K + 1>(A, r)) break;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          r[k] = LA(-(z[k] - zs[k] - hr * w[k]));
+#pragma unroll
+          for (int m = 0; m < n; ++m) A[k][m] = LA(k == m ? 1 : 0) - hrL * A[k][m];
+        }
+        r[K] = LA(-(z[K] - zs[K] + h * hw * inv_rcp));
+        if (!solve_pivoted<K + 1, LA>(A, r)) break;
         double big = 0;
         bool bad = false;
 #pragma unroll
         for (int m = 0; m < n; ++m) {
-          z[m] += r[m];
-          const double e = fabs(r[m]) * (m < K ? 1.0 : inv_Ts);
+          z[m] += double(r[m]);
+          const double e = fabs(double(r[m])) * (m < K ? 1.0 : inv_Ts);
           if (!(e == e)) bad = true;
           if (e > big) big = e;
         }
@@ -614,6 +649,175 @@ __device__ __forceinline__ void chem_be_newton(const Chem64<K>* C0,
 #pragma unroll
   for (int k = 0; k < K; ++k) dY[k] = zs[k] - y0[k];
   *dT = zs[K] - T0;
+}
+
+// ------------------------------------ Newton fallback of FP32 domains (FP32)
+// Rates w_k (kg/(m^3 s)) and their Jacobian dw_k/dz_m in FP32, z = (Y, T);
+// k_f and k_r are taken as exponentials of their logarithms, so that neither
+// over- nor underflows on the way (k_r = exp(ln k_f - ln K_c)).
+template <int K>
+__device__ __forceinline__ void rates_jacobian32(const Chem32<K>& c, const float* z, float rho,
+                                                 float* w, float (*dw)[K + 1]) {
+  constexpr int KK = K > 0 ? K : 1;
+  constexpr int n = K + 1;
+  const float T = z[K], invT = 1.f / T, lnT = logf(T);
+  float Cc[KK], dC[KK];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    dC[k] = z[k] > 0.f ? rho * c.invM[k] : 0.f;
+    Cc[k] = z[k] > 0.f ? z[k] * dC[k] : 0.f;
+    w[k] = 0.f;
+#pragma unroll
+    for (int m = 0; m < n; ++m) dw[k][m] = 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < JMAX; ++j) {
+    if (!c.on[j]) continue;
+    const float lkf = c.lnA[j] + c.b[j] * lnT - c.EaR[j] * invT;
+    const float kf = expf(lkf);
+    const float dlkf = (c.EaR[j] * invT + c.b[j]) * invT;
+    float kr = 0.f, dlkr = dlkf;
+    if (c.rev[j]) {
+      const float lnKc = c.dS_R[j] - c.dH_R[j] * invT + c.dn[j] * (c.ln_pref_R - lnT);
+      kr = expf(lkf - lnKc);
+      dlkr = dlkf - (c.dH_R[j] * invT + c.dn[j]) * invT;
+    }
+    float dq[K + 1];
+#pragma unroll
+    for (int m = 0; m < n; ++m) dq[m] = 0.f;
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      if (dir == 1 && !c.rev[j]) break;
+      const float kk = dir == 0 ? kf : -kr;
+      float Pw[KK], Dp[KK], pre[K + 1], suf[K + 1];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float o = dir == 0 ? c.order[j][k] : c.rorder[j][k];
+        const float C = Cc[k];
+        if (o == 1.f) { Pw[k] = C; Dp[k] = 1.f; }
+        else if (o == 0.f) { Pw[k] = 1.f; Dp[k] = 0.f; }
+        else if (o == 2.f) { Pw[k] = C * C; Dp[k] = 2.f * C; }
+        else if (o == 0.5f) {
+          const float sq = sqrtf(C);
+          Pw[k] = sq;
+          Dp[k] = sq > 0.f ? 0.5f / sq : 0.f;
+        } else {
+          Pw[k] = powf(C, o);
+          Dp[k] = C > 0.f ? o * powf(C, o - 1.f) : 0.f;
+        }
+      }
+      pre[0] = 1.f;
+      suf[K] = 1.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) pre[k + 1] = pre[k] * Pw[k];
+#pragma unroll
+      for (int k = K - 1; k >= 0; --k) suf[k] = Pw[k] * suf[k + 1];
+      const float q = kk * pre[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) w[k] += c.Ms[j][k] * q;
+      dq[K] += q * (dir == 0 ? dlkf : dlkr);
+#pragma unroll
+      for (int m = 0; m < K; ++m) dq[m] += kk * (pre[m] * suf[m + 1]) * Dp[m] * dC[m];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int m = 0; m < n; ++m) dw[k][m] += c.Ms[j][k] * dq[m];
+  }
+}
+
+// The backward-Euler step of chem_be_newton in FP32 for the cells that the
+// surrogate rejects in FP32 domains.  FP32 cannot hold the root to the FP64
+// integrator's 1e-13, so the unknown is the sub-step's increment d = z - zs
+// (small numbers keep their relative precision), the residual is
+// d - h F(zs + d), and the iteration stops once every update is below
+// 1e-5 |d_m| + 1e-6 |zs_m| (a few units in the last place of the FP32 field
+// that receives the increment).  On GB300 the FP64 pipe issues one warp
+// instruction every 16 cycles per SM, so the FP64 integrator's chain on a
+// short list of cells takes tens of microseconds; this one runs on the FP32
+// pipe and the special-function unit.
+template <int K>
+__device__ __forceinline__ void chem_be_newton32(const Chem32<K>& c, float T0, const float* Y0,
+                                                 float rho, float* dY, float* dT) {
+  constexpr int n = K + 1;
+  const float inv_rho = 1.f / rho;
+  float y0[K + 1], acc[K + 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) y0[k] = Y0[k];
+  y0[K] = T0;
+#pragma unroll
+  for (int m = 0; m < n; ++m) acc[m] = 0.f;
+  int ok = -1;
+#pragma unroll 1
+  for (int nsub = 1; nsub <= 64 && ok != 0; nsub *= 2) {
+    float zs[K + 1];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      zs[m] = y0[m];
+      acc[m] = 0.f;
+    }
+    ok = 0;
+    const float h = c.dt / float(nsub), hr = h * inv_rho;
+#pragma unroll 1
+    for (int sub = 0; sub < nsub && ok == 0; ++sub) {
+      float d[K + 1];
+#pragma unroll
+      for (int m = 0; m < n; ++m) d[m] = 0.f;
+      ok = -1;
+#pragma unroll 1
+      for (int it = 0; it < 30; ++it) {
+        float z[K + 1], w[K + 1];
+#pragma unroll
+        for (int m = 0; m < n; ++m) z[m] = zs[m] + d[m];
+        if (!(z[K] > 0.f)) break;
+        float A[K + 1][K + 1];
+        rates_jacobian32<K>(c, z, rho, w, A);
+        float cp = 0.f, hw = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          cp += z[k] * c.cp[k];
+          hw += c.hf[k] * w[k];
+        }
+        const float inv_rcp = inv_rho / cp;
+        const float hwc = hw * inv_rcp / cp;
+        float r[K + 1];
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          float dhw = 0.f;
+#pragma unroll
+          for (int k = 0; k < K; ++k) dhw += c.hf[k] * A[k][m];
+          float dFT = -dhw * inv_rcp;
+          if (m < K) dFT += hwc * c.cp[m];
+          A[K][m] = (m == K ? 1.f : 0.f) - h * dFT;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          r[k] = -(d[k] - hr * w[k]);
+#pragma unroll
+          for (int m = 0; m < n; ++m) A[k][m] = (k == m ? 1.f : 0.f) - hr * A[k][m];
+        }
+        r[K] = -(d[K] + h * hw * inv_rcp);
+        if (!solve_pivoted<K + 1, float>(A, r)) break;
+        bool bad = false, done = true;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          d[m] += r[m];
+          if (!(r[m] == r[m])) bad = true;
+          if (fabsf(r[m]) > 1e-5f * fabsf(d[m]) + 1e-6f * fabsf(zs[m])) done = false;
+        }
+        if (bad) break;
+        if (done) { ok = 0; break; }
+      }
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        zs[m] += d[m];
+        acc[m] += d[m];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) dY[k] = acc[k];
+  *dT = acc[K];
 }
 
 // Moments read straight from global memory (the moments kernel, no staging).
@@ -1606,7 +1810,7 @@ chem_implicit_kernel(const __grid_constant__ Params<Real, K> P, const State<Real
     double Yd[KK], dY[KK], dT;
 #pragma unroll
     for (int k = 0; k < K; ++k) Yd[k] = double(Y[k]);
-    chem_be_newton<K>(&P.c64, double(T), Yd, double(rho) * P.c64.rho_ref, dY, &dT);
+    chem_be_newton<K, Real>(&P.c64, double(T), Yd, double(rho) * P.c64.rho_ref, dY, &dT);
 #pragma unroll
     for (int k = 0; k < K; ++k) om[k] = rho * Real(dY[k]);
     omT = rho * mixture_cp(P, Y) * Real(dT);

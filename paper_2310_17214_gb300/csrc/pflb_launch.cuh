@@ -230,6 +230,32 @@ Params<Real, K> make_params(const pflb_domain_desc& d, const pflb_mechanism& m, 
   P.c64.ln_pref_R = std::log(P.c64.p_ref / R_GAS);
   P.c64.rho_ref = d.rho_ref;
   P.c64.dt = d.dt;
+  {
+    auto& f = P.c32;
+    const auto& c = P.c64;
+    for (int j = 0; j < P.J; ++j) {
+      f.on[j] = c.A[j] > 0.0 ? 1 : 0;
+      f.lnA[j] = float(c.A[j] > 0.0 ? std::log(c.A[j]) : 0.0);
+      f.b[j] = float(c.b[j]);
+      f.EaR[j] = float(c.EaR[j]);
+      f.dn[j] = float(c.dn[j]);
+      f.dS_R[j] = float(c.dS_R[j]);
+      f.dH_R[j] = float(c.dH_R[j]);
+      f.rev[j] = c.rev[j];
+      for (int k = 0; k < K; ++k) {
+        f.order[j][k] = float(c.order[j][k]);
+        f.rorder[j][k] = float(c.rorder[j][k]);
+        f.Ms[j][k] = float(c.Ms[j][k]);
+      }
+    }
+    for (int k = 0; k < K; ++k) {
+      f.invM[k] = float(c.invM[k]);
+      f.cp[k] = float(c.cp[k]);
+      f.hf[k] = float(c.hf[k]);
+    }
+    f.ln_pref_R = float(c.ln_pref_R);
+    f.dt = float(c.dt);
+  }
   // inlet feedback: rho_in / P0 (lattice) and the inlet area A, the inlet
   // profile at unit peak speed summed over the x = 0 face
   P.feed = (K > 0 && m.inlet_feedback > 0) ? 1 : 0;

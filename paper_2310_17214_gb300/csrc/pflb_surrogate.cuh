@@ -197,17 +197,26 @@ __device__ __forceinline__ void fallback_cell(const Params<Real, K>& P, const St
   for (int k = 0; k < K; ++k) Y[k] = S.Y_in[(size_t)k * P.N + c];
   const Real P0 = scal_P0<Real>(S.scal);
   const Real rho = fdiv(P0 * P.eos_cr, T * mixture_invMw(P, Y));
-  double Yd[KK], dY[KK], dT;
+  if constexpr (sizeof(Real) == 4) {
+    // FP32 domains: the FP32 integrator (the fields it feeds are FP32)
+    float dY[KK], dT;
+    chem_be_newton32<K>(P.c32, T, Y, rho * float(P.c64.rho_ref), dY, &dT);
 #pragma unroll
-  for (int k = 0; k < K; ++k) Yd[k] = double(Y[k]);
-  chem_be_newton<K>(&P.c64, double(T), Yd, double(rho) * P.c64.rho_ref, dY, &dT);
+    for (int k = 0; k < K; ++k) src[(size_t)k * P.N + c] = rho * dY[k];
+    src[(size_t)K * P.N + c] = rho * mixture_cp(P, Y) * dT;
+  } else {
+    double Yd[KK], dY[KK], dT;
 #pragma unroll
-  for (int k = 0; k < K; ++k) src[(size_t)k * P.N + c] = rho * Real(dY[k]);
-  src[(size_t)K * P.N + c] = rho * mixture_cp(P, Y) * Real(dT);
+    for (int k = 0; k < K; ++k) Yd[k] = double(Y[k]);
+    chem_be_newton<K, Real>(&P.c64, double(T), Yd, double(rho) * P.c64.rho_ref, dY, &dT);
+#pragma unroll
+    for (int k = 0; k < K; ++k) src[(size_t)k * P.N + c] = rho * Real(dY[k]);
+    src[(size_t)K * P.N + c] = rho * mixture_cp(P, Y) * Real(dT);
+  }
 }
 
 // Backward-Euler Newton for the cells the surrogate rejected.  The list is
-// short and the integrator is bound by the FP64 pipe of the SM it runs on,
+// short and the integrator is bound by the latency of its chain,
 // so the kernel runs one warp per block, grid-striding: a list of a few
 // hundred cells spreads over as many SMs as it has warps.
 constexpr int FALLBACK_BLOCK = 32;

@@ -6,7 +6,9 @@ Bars: forward and per-tensor gradients within 2e-2 relative of the FP64
 reference evaluated at the BF16-rounded parameters (BF16 operands, FP32
 accumulation); the first Adam step moves each parameter by -lr sign(g)
 exactly where the gradient is clearly non-zero; a surrogate that rejects
-every cell reproduces the Newton chemistry bit for bit; a surrogate whose
+every cell reproduces the Newton chemistry bit for bit in FP64 and to the
+FP32 resolution of the fields in FP32 (where the fallback has its own FP32
+integrator, checked cell by cell against the oracle); a surrogate whose
 network predicts no change reproduces the run without chemistry."""
 import numpy as np
 import pytest
@@ -19,6 +21,10 @@ from paper_2310_17214_gb300._native import Domain, Mlp, MLP_PARAMS
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+
+def l2rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
 def bf16_round(a):
@@ -159,27 +165,77 @@ def _surrogate_record(p, theta_s=0.0, tol=1e-6):
     return s
 
 
+def _all_fallback(p, f, precision):
+    """A surrogate-mode domain whose network is rejected in every fluid cell
+    (tolerance -1): every cell goes through the fallback integrator."""
+    dom = _domain(dict(p, chem="surrogate"), f, precision)
+    net = Mlp()
+    net.set_params(np.zeros(MLP_PARAMS, dtype=np.float32))
+    dom.set_surrogate(net, _surrogate_record(p, tol=-1.0))
+    return dom, net
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_surrogate_rejecting_every_cell_equals_newton(precision):
-    """Tolerance -1 sends every fluid cell through the fallback list: the run
-    must be the Newton run exactly."""
+    """Tolerance -1 sends every fluid cell through the fallback list.  FP64:
+    the fallback is the Newton pre-pass's integrator and the run is the Newton
+    run bit for bit.  FP32: the fallback integrator is the FP32 one (increment
+    form, stopped at a few units in the last place of the field), the Newton
+    pre-pass keeps the FP64 residual; after 60 steps through ignition the two
+    runs agree to the FP32 resolution of the fields."""
     p, f = _flame_case(precision=precision)
     ref = _domain(p, f, precision)
     ref.step(60)
     a = ref.get("T", "Y", "g")
-    ps = dict(p, chem="surrogate")
-    dom = _domain(ps, f, precision)
-    net = Mlp()
-    net.set_params(np.zeros(MLP_PARAMS, dtype=np.float32))
-    dom.set_surrogate(net, _surrogate_record(p, tol=-1.0))
+    dom, net = _all_fallback(p, f, precision)
     dom.step(60)
     b = dom.get("T", "Y", "g")
-    for k in a:
-        assert np.array_equal(a[k], b[k]), k
+    if precision == "fp64":
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    else:
+        dT = np.abs(a["T"] - b["T"])
+        dYm = np.abs(a["Y"] - b["Y"])
+        print("fp32 fallback vs Newton run: max dT", dT.max(), "max dY", dYm.max(),
+              "L2 T", l2rel(b["T"] - 300.0, a["T"] - 300.0))
+        assert np.max(a["T"]) > 1500.0
+        assert l2rel(b["T"] - 300.0, a["T"] - 300.0) <= 1e-5
+        assert dT.max() <= 0.05 and dYm.max() <= 2e-5
     fb, ev = dom.chem_stats()
     assert ev > 0 and fb == ev
     dom.close()
     ref.close()
+    net.close()
+
+
+def test_fp32_fallback_integrator_matches_one_step():
+    """The FP32 fallback integrator against the oracle's FP64 backward-Euler
+    step, cell by cell, on an FP32 state after ignition: the increment form
+    holds the increments to 1e-4 of themselves or a few units in the last
+    place of the field they are added to."""
+    from oracle import oracle as O
+    p, f = _flame_case(nx=96, ny=24, precision="fp32")
+    dom, net = _all_fallback(p, f, "fp32")
+    dom.step(5)
+    dY, dT = dom.chem_increments()
+    g = dom.get("T", "Y")
+    P0 = dom.scalars()["P0"]
+    rng = np.random.default_rng(0)
+    fluid = np.flatnonzero(1.0 - f["phi"] >= 1e-6)
+    cells = np.concatenate([rng.choice(fluid, 40, replace=False),
+                            fluid[np.argsort(-np.abs(dT[fluid]))[:20]]])
+    assert np.max(np.abs(dT[cells])) > 0.1  # reacting cells are in the sample
+    eT, eY = 0.0, 0.0
+    for c in cells:
+        T, Y = float(g["T"][c]), g["Y"][:, c].astype(np.float64)
+        rho_lat = P0 / (I.R_GAS * T * np.sum(Y / np.asarray(p["M"]))) / p["rho_ref"]
+        ry, rt, rc = O.chem_implicit(p, T, Y, rho_lat)
+        assert rc == 0
+        eT = max(eT, abs(dT[c] - rt) / (1e-4 * abs(rt) + 4e-6 * T))
+        eY = max(eY, np.max(np.abs(dY[:, c] - ry) / (1e-4 * np.abs(ry) + 4e-6 * np.abs(Y) + 1e-12)))
+    print("fp32 fallback vs oracle, error / bar: T", eT, "Y", eY)
+    assert eT <= 1.0 and eY <= 1.0
+    dom.close()
     net.close()
 
 
