@@ -526,7 +526,8 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
     surrogate from the same initial state, and compare it with the Newton
     run and with the plain FP64 run after `steps` steps; then time the plain
     FP64 step (FP64 transport and Newton), the FP32 + Newton step and the
-    FP32 + surrogate step."""
+    FP32 + surrogate step, the latter also with cold tiles skipping the
+    network (skip_eps)."""
     import torch
     from paper_2310_17214_gb300 import surrogate as S
     st = torch.cuda.current_stream(dev)
@@ -556,6 +557,13 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
     d64.step(steps)
     err64 = S.flame_errors(T_sur, d64.get("T"), f["phi"], p)
     d64.close()
+    # the same network with cold tiles skipping it (increment bound 1e-12)
+    skip_eps = 1e-12
+    sk = dom_of("surrogate", "fp32")
+    sk.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], tol,
+                                           skip_eps=skip_eps))
+    sk.step(steps)
+    err_skip = S.flame_errors(sk.get("T"), ref.get("T"), f["phi"], p)
     fb, ev = sur.chem_stats()
     t_newton32 = _ms_per_step(ref, 30, flush, st)
     t_sur = _ms_per_step(sur, 100, flush, st)
@@ -568,6 +576,9 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
     sw.set_state(sur.get_state())
     t_tc = _ms_per_step(sw, 100, flush, st)
     sw.close()
+    sk.set_state(sur.get_state())
+    t_skip = _ms_per_step(sk, 100, flush, st)
+    sk.close()
     d64 = dom_of("implicit", "fp64")
     t_plain64 = _ms_per_step(d64, 20, flush, st)
     for d in (ref, sur, d64):
@@ -579,6 +590,8 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
             "fp32_surrogate_ms_per_step": t_sur,
             "network_engine": "warp-level mma.sync (32 cells per warp)",
             "fp32_surrogate_tcgen05_ms_per_step": t_tc,
+            "fp32_surrogate_cold_skip_ms_per_step": t_skip, "cold_skip_eps": skip_eps,
+            "error_vs_fp32_newton_cold_skip": err_skip,
             "surrogate_mlups": N / t_sur / 1e3, "plain_fp64_mlups": N / t_plain64 / 1e3,
             "speedup_vs_plain_fp64": t_plain64 / t_sur,
             "speedup_vs_fp32_newton": t_newton32 / t_sur,

@@ -407,6 +407,17 @@ typedef struct pflb_surrogate {
                                    bench's bed) or PFLB_MLP_TCGEN05 (1, tensor-memory
                                    accumulators, 128 cells per MMA); both use the network's
                                    FP32 parameters rounded to BF16 and FP32 accumulation */
+  double skip_eps;              /* 0: the network runs on every tile of cells.  > 0: a
+                                   tile of cells (32 for the warp engine, 128 for tcgen05)
+                                   skips the network when none of its cells needs it, i.e.
+                                   each is solid (phi_f < phi_min), outside [lo, hi] (the
+                                   fallback takes it anyway) or at T <= T_skip, where the
+                                   projected increment the network could give is bounded by
+                                   skip_eps in every species: |out_k| <= sum_j |W_3[j][k]|
+                                   + |b_3[k]| because |tanh| <= 1, so T_skip = theta_s /
+                                   ln(|P|_inf max_k (|y_mean_k| + y_std_k max|out_k|) /
+                                   skip_eps).  Such cold cells take a zero increment.
+                                   Needs theta_s > 0; negative or NaN: PFLB_ERR_ARG */
 } pflb_surrogate;
 
 #define PFLB_MLP_WARP_MMA 0

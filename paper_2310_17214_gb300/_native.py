@@ -79,7 +79,7 @@ class Surrogate(C.Structure):
         ("theta_s", C.c_double),
         ("lo", C.c_double * 8), ("hi", C.c_double * 8),
         ("n_elem", C.c_int), ("elem", (C.c_double * KMAX) * 4), ("elem_mass", C.c_double * 4),
-        ("tol", C.c_double), ("engine", C.c_int),
+        ("tol", C.c_double), ("engine", C.c_int), ("skip_eps", C.c_double),
     ]
 
 

@@ -5,6 +5,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <string>
 #include <algorithm>
@@ -974,6 +975,34 @@ int pflb_set_surrogate(pflb_domain* d, const pflb_mlp* net, const pflb_surrogate
       a.Pj[i][j] = v;
       a.Pj_f[i][j] = float(v);
     }
+  // cold tiles may skip the network: with |tanh| <= 1 the output layer bounds
+  // |out_k| by sum_j |W_3[j][k]| + |b_3[k]| (the factor 1 + 2^-7 covers the
+  // BF16 rounding of the weights and of the activations), the projection by
+  // its infinity norm, and exp(-theta_s / T) does the rest
+  if (!(s->skip_eps >= 0.0)) return fail(d, PFLB_ERR_ARG, "skip_eps");
+  a.T_skip = 0.0;
+  if (s->skip_eps > 0.0) {
+    if (!(s->theta_s > 0.0)) return fail(d, PFLB_ERR_ARG, "skip_eps needs theta_s > 0");
+    std::vector<float> th(mlp::NPARAM);
+    const int r = pflb_mlp_get_params(const_cast<pflb_mlp*>(net), th.data());
+    CK(d, cudaSetDevice(d->desc.device));
+    if (r) return fail(d, r, "reading the network parameters");
+    const float* W3 = th.data() + mlp::woff(3);
+    const float* b3 = th.data() + mlp::boff(3);
+    double bound = 0.0, pinf = 0.0;
+    for (int k = 0; k < 6; ++k) {
+      double o = std::fabs(b3[k]);
+      for (int j = 0; j < 64; ++j) o += 1.0078125 * std::fabs(W3[j * 6 + k]);
+      bound = std::max(bound, std::fabs(s->y_mean[k]) + std::fabs(s->y_std[k]) * o);
+      double row = 0.0;
+      for (int q = 0; q < 6; ++q) row += std::fabs(a.Pj[k][q]);
+      pinf = std::max(pinf, row);
+    }
+    bound *= pinf;
+    a.T_skip = bound > s->skip_eps ? s->theta_s / std::log(bound / s->skip_eps)
+                                   : std::numeric_limits<double>::infinity();
+  }
+  a.T_skip_f = float(a.T_skip);
   if (!d->L->set_surrogate(a)) return fail(d, PFLB_ERR_UNSUPPORTED, "surrogate not available");
   return PFLB_OK;
 }

@@ -28,11 +28,68 @@ struct SurrArgs {
   double Pj[6][6];          // projection onto element-conserving increments
   double tol;
   float E_f[4][6], Pj_f[6][6], tol_f, theta_f;  // the same in FP32
+  double T_skip;            // cells at T <= T_skip need no network (0: none)
+  float T_skip_f;
   int engine;               // 0: warp-level mma.sync network kernel, 1: tcgen05 kernel
   int* fb_idx;              // fallback cell list
   unsigned* fb_count;
   double* stats;            // [0] fallback cells, [1] cells evaluated by the network
 };
+
+// Raw inputs (T, Y_1..Y_6, P0) inside the training bounding box.
+__device__ __forceinline__ bool surrogate_in_box(const SurrArgs& A, const float* raw) {
+  bool ok = true;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) ok = ok && raw[f] >= A.lo[f] && raw[f] <= A.hi[f];
+  return ok;
+}
+
+// Whether live cell c needs the network: a fluid cell inside the box above
+// T_skip (a solid cell takes no source, a cell outside the box goes to the
+// fallback whatever the network says, and below T_skip the network's
+// projected increment is bounded by the record's skip_eps).
+template <int K, class Real>
+__device__ __forceinline__ bool surrogate_needs_net(const Params<Real, K>& P, const SurrArgs& A,
+                                                    const float* raw, Real T, Real phif) {
+  const Real Ts = sizeof(Real) == 8 ? Real(A.T_skip) : Real(A.T_skip_f);
+  return phif >= P.phi_min && T > Ts && surrogate_in_box(A, raw);
+}
+
+// Live cell c of a tile that skips the network (no cell of it needs the
+// network): zero source, and the bookkeeping of surrogate_post_cell (a fluid
+// cell is evaluated; outside the box it is reported for the fallback: true).
+template <int K, class Real>
+__device__ __forceinline__ bool surrogate_skip_cell(const Params<Real, K>& P, const SurrArgs& A,
+                                                    Real* __restrict__ src, long long c,
+                                                    const float* raw, Real phif,
+                                                    unsigned& evaluated, unsigned& fallbacks) {
+  bool reject = false;
+  if (phif >= P.phi_min) {
+    ++evaluated;
+    if (!surrogate_in_box(A, raw)) {
+      ++fallbacks;
+      reject = true;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= 6; ++k) src[(size_t)k * P.N + c] = Real(0);
+  return reject;
+}
+
+// Ordered, warp-aggregated append of the warp's rejected cells to the
+// fallback list: neighbouring cells stay together in the list, so the
+// integrator's warps see similar states.  Every lane of the warp calls it.
+__device__ __forceinline__ void surrogate_append_fallback(const SurrArgs& A, bool reject,
+                                                          long long c) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned mask = __ballot_sync(0xffffffffu, reject);
+  if (mask) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(A.fb_count, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (reject) A.fb_idx[base + __popc(mask & ((1u << lane) - 1u))] = (int)c;
+  }
+}
 
 // Per-cell use of the network's raw outputs o[0..5] for live cell c:
 // de-normalise, test the bounding box and the element residuals, project and
@@ -51,9 +108,7 @@ __device__ __forceinline__ bool surrogate_post_cell(const Params<Real, K>& P,
   for (int k = 0; k < 6; ++k) om[k] = 0;
   if (phif >= P.phi_min) {
     ++evaluated;
-    bool ok = true;
-#pragma unroll
-    for (int f = 0; f < 8; ++f) ok = ok && raw[f] >= A.lo[f] && raw[f] <= A.hi[f];
+    bool ok = surrogate_in_box(A, raw);
     // post-processing in the compute precision (FP64 domains keep FP64)
     constexpr bool D64 = sizeof(Real) == 8;
     Real dY[6];
@@ -131,6 +186,13 @@ chem_surrogate_kernel(const Params<Real, K> P, const State<Real, Store> S, Real*
 #pragma unroll
     for (int k = 0; k < 6; ++k) raw[1 + k] = float(Y[k]);
     raw[7] = float(P0);
+    if (!__any_sync(0xffffffffu, live && surrogate_needs_net<K, Real>(P, A, raw, T, phif))) {
+      // no cell of the tile needs the network
+      const bool reject =
+          live && surrogate_skip_cell<K, Real>(P, A, src, c, raw, phif, evaluated, fallbacks);
+      surrogate_append_fallback(A, reject, c);
+      continue;
+    }
     {
       uint32_t* xr = reinterpret_cast<uint32_t*>(xs[warp] + lane * mlp::XLD);
 #pragma unroll
@@ -158,16 +220,7 @@ chem_surrogate_kernel(const Params<Real, K> P, const State<Real, Store> S, Real*
       reject = surrogate_post_cell<K, Real, Store>(P, S, A, src, c, raw, Y, T, phif, P0, o,
                                                    evaluated, fallbacks);
     }
-    // ordered, warp-aggregated append of the rejected cells: neighbouring
-    // cells stay together in the list, so the integrator's warps see
-    // similar states
-    const unsigned mask = __ballot_sync(0xffffffffu, reject);
-    if (mask) {
-      unsigned base = 0;
-      if (lane == 0) base = atomicAdd(A.fb_count, (unsigned)__popc(mask));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (reject) A.fb_idx[base + __popc(mask & ((1u << lane) - 1u))] = (int)c;
-    }
+    surrogate_append_fallback(A, reject, c);
     __syncwarp();
   }
   // counts of this warp

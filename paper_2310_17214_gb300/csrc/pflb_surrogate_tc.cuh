@@ -247,6 +247,13 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
 #pragma unroll
     for (int k = 0; k < 6; ++k) raw[1 + k] = float(Y[k]);
     raw[7] = float(P0);
+    if (!__syncthreads_or(live && surrogate_needs_net<K, Real>(P, A, raw, T, phif))) {
+      // no cell of the tile needs the network
+      const bool reject =
+          live && surrogate_skip_cell<K, Real>(P, A, src, c, raw, phif, evaluated, fallbacks);
+      surrogate_append_fallback(A, reject, c);
+      continue;
+    }
     // layer-0 input row: 8 normalised features and 8 zeros (K = 16)
     {
       uint32_t w[8];
@@ -297,13 +304,7 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
     if (live)
       reject = surrogate_post_cell<K, Real, Store>(P, S, A, src, c, raw, Y, T, phif, P0, o,
                                                    evaluated, fallbacks);
-    const unsigned mask = __ballot_sync(0xffffffffu, reject);
-    if (mask) {
-      unsigned base = 0;
-      if (lane == 0) base = atomicAdd(A.fb_count, (unsigned)__popc(mask));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (reject) A.fb_idx[base + __popc(mask & ((1u << lane) - 1u))] = (int)c;
-    }
+    surrogate_append_fallback(A, reject, c);
   }
   if (failed) {
     // an MMA group that did not report: wait once more (bounded) for it

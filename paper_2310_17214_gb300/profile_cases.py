@@ -31,8 +31,9 @@ from ._native import Batch, Domain
 
 def surrogate_case(nx=2048, ny=512, precision="fp32"):
     """The two-step bed with the trained surrogate on both network engines
-    (tcgen05 and warp-level mma.sync) beside the Newton run: CUDA-event time
-    per step of each, then two profiled steps of each."""
+    (tcgen05 and warp-level mma.sync, the latter also with cold tiles
+    skipping the network) beside the Newton run: CUDA-event time per step of
+    each, then two profiled steps of each."""
     import torch
     from ._native import MLP_ENGINES
     p = I.config4(nx=nx, ny=ny, precision=precision)
@@ -51,8 +52,9 @@ def surrogate_case(nx=2048, ny=512, precision="fp32"):
     net, _ = S.train(Xn, Yn, epochs=30, batch=8192)
     rec = S.make_surrogate(stats, X, theta, p["species"], 1e-6)
     doms = {}
-    for name in ("tcgen05", "warp_mma"):
-        rec.engine = MLP_ENGINES[name]
+    for name in ("tcgen05", "warp_mma", "warp_mma_cold_skip"):
+        rec.engine = MLP_ENGINES["tcgen05" if name == "tcgen05" else "warp_mma"]
+        rec.skip_eps = 1e-12 if name.endswith("cold_skip") else 0.0
         sd = dom_of("surrogate")
         sd.set_surrogate(net, rec)
         sd.set_state(d.get_state())

@@ -86,13 +86,14 @@ def normalisation(X, D, theta_s):
     return (x_mean, x_std, y_mean, y_std), Xn.astype(np.float32), Yn.astype(np.float32)
 
 
-def make_surrogate(stats, X, theta_s, species, tol=1e-6, pad=0.01):
+def make_surrogate(stats, X, theta_s, species, tol=1e-6, pad=0.01, skip_eps=0.0):
     """The pflb_surrogate record: normalisation, bounding box of the raw
     training inputs, element matrix and residual tolerance.  The box is
     widened by `pad` times each feature's range (1e-6 of the value for a
     constant feature): the fresh and the burnt gas, where most cells sit,
     are corners of the box, and round-off would otherwise put them just
-    outside it."""
+    outside it.  skip_eps > 0 lets tiles of cold cells skip the network
+    where its increment is bounded by skip_eps (pflb_surrogate.skip_eps)."""
     from .inputs import element_matrix
     x_mean, x_std, y_mean, y_std = stats
     s = N.Surrogate()
@@ -112,6 +113,7 @@ def make_surrogate(stats, X, theta_s, species, tol=1e-6, pad=0.01):
         for k in range(len(species)):
             s.elem[e][k] = elem[e][k]
     s.tol = tol
+    s.skip_eps = skip_eps
     return s
 
 

@@ -16,7 +16,7 @@ import pytest
 from oracle import mlp as M
 from paper_2310_17214_gb300 import inputs as I
 from paper_2310_17214_gb300 import surrogate as S
-from paper_2310_17214_gb300._native import Domain, Mlp, MLP_PARAMS
+from paper_2310_17214_gb300._native import Domain, Mlp, MLP_PARAMS, PflbError
 
 pytestmark = pytest.mark.gpu
 
@@ -263,6 +263,47 @@ def test_surrogate_predicting_no_change_equals_no_chemistry():
     net.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cold_skip_is_exact_for_a_network_that_predicts_no_change(precision):
+    """skip_eps > 0 with a network whose output bound is zero: every tile
+    skips the network (T_skip is infinite), and the run equals the run that
+    evaluates the network everywhere bit for bit, with the same counts (the
+    cells outside the narrow training box still fall back)."""
+    p, f = _flame_case(precision=precision)
+    runs = []
+    for eps in (0.0, 1e-12):
+        dom = _domain(dict(p, chem="surrogate"), f, precision)
+        net = Mlp()
+        net.set_params(np.zeros(MLP_PARAMS, dtype=np.float32))
+        rec = _surrogate_record(p, theta_s=12000.0)
+        rec.skip_eps = eps
+        dom.set_surrogate(net, rec)
+        dom.step(40)
+        runs.append((dom.get("T", "Y", "g"), dom.chem_stats()))
+        dom.close()
+        net.close()
+    (a, sa), (b, sb) = runs
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert sa == sb and sa[0] > 0 and sa[1] > sa[0]
+
+
+def test_cold_skip_arguments():
+    """A negative or NaN skip_eps, or skip_eps without the temperature
+    scaling (theta_s = 0), is refused."""
+    p, f = _flame_case(precision="fp32")
+    dom = _domain(dict(p, chem="surrogate"), f, "fp32")
+    net = Mlp()
+    net.set_params(np.zeros(MLP_PARAMS, dtype=np.float32))
+    for theta_s, eps in ((12000.0, -1.0), (12000.0, float("nan")), (0.0, 1e-12)):
+        rec = _surrogate_record(p, theta_s=theta_s)
+        rec.skip_eps = eps
+        with pytest.raises(PflbError):
+            dom.set_surrogate(net, rec)
+    dom.close()
+    net.close()
+
+
 def test_chem_increments_of_newton_mode_match_one_step():
     """pflb_chem_increments in the Newton mode against the oracle's
     backward-Euler integrator, cell by cell, on a state after ignition."""
@@ -324,8 +365,22 @@ def test_trained_surrogate_tracks_the_flame_and_beats_newton():
     assert err["T_max_abs_diff_K"] <= 20.0
     fb, ev = sur.chem_stats()
     assert fb / ev < 0.02
+    # cold tiles skipping the network (increment bound 1e-12 per step): the
+    # same flame against the Newton run, and next to the full evaluation
+    sk = _domain(dict(p, chem="surrogate"), f, "fp32")
+    sk.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], 1e-6,
+                                           skip_eps=1e-12))
+    sk.step(steps)
+    Tk = sk.get("T")
+    err_k = S.flame_errors(Tk, Tb, f["phi"], p)
+    assert err_k["rows_front_mismatch"] == 0 and err_k["front_max_diff_cells"] <= 1.0
+    assert err_k["T_max_abs_diff_K"] <= 20.0
+    err_ks = S.flame_errors(Tk, Ta, f["phi"], p)
+    print("cold skip vs full evaluation:", err_ks)
+    assert err_ks["front_max_diff_cells"] <= 0.1 and err_ks["T_max_abs_diff_K"] <= 1.0
     t_newton, t_sur = _ms_per_step(ref), _ms_per_step(sur)
     assert t_sur * 3.0 < t_newton, (t_sur, t_newton)
+    sk.close()
     sur.close()
     ref.close()
     net.close()
