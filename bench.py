@@ -560,8 +560,9 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
     # the same network with cold tiles skipping it (increment bound 1e-12)
     skip_eps = 1e-12
     sk = dom_of("surrogate", "fp32")
-    sk.set_surrogate(net, S.make_surrogate(stats, X, theta, p["species"], tol,
-                                           skip_eps=skip_eps))
+    rec_skip = S.make_surrogate(stats, X, theta, p["species"], tol, skip_eps=skip_eps)
+    T_skip = S.skip_temperature(net.get_params(), rec_skip, p["M"])
+    sk.set_surrogate(net, rec_skip)
     sk.step(steps)
     err_skip = S.flame_errors(sk.get("T"), ref.get("T"), f["phi"], p)
     fb, ev = sur.chem_stats()
@@ -591,6 +592,7 @@ def surrogate_leg(dev, flush, steps=2000, samples=1_000_000, epochs=40, tol=1e-6
             "network_engine": "warp-level mma.sync (32 cells per warp)",
             "fp32_surrogate_tcgen05_ms_per_step": t_tc,
             "fp32_surrogate_cold_skip_ms_per_step": t_skip, "cold_skip_eps": skip_eps,
+            "cold_skip_T_K": T_skip,
             "error_vs_fp32_newton_cold_skip": err_skip,
             "surrogate_mlups": N / t_sur / 1e3, "plain_fp64_mlups": N / t_plain64 / 1e3,
             "speedup_vs_plain_fp64": t_plain64 / t_sur,

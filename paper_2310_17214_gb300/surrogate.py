@@ -117,6 +117,23 @@ def make_surrogate(stats, X, theta_s, species, tol=1e-6, pad=0.01, skip_eps=0.0)
     return s
 
 
+def skip_temperature(theta, rec, M):
+    """T_skip of a record with skip_eps > 0 for the network parameters theta
+    (flat FP32 vector) and molar masses M: the bound the library derives in
+    pflb_set_surrogate, restated here for reports."""
+    eps = float(rec.skip_eps)
+    if not eps > 0.0:
+        return 0.0
+    th = np.asarray(theta, dtype=np.float64)
+    b4, W4 = th[-6:], th[-6 - 64 * 6:-6].reshape(64, 6)
+    out = np.abs(b4) + 1.0078125 * np.abs(W4).sum(axis=0)
+    bound = max(abs(rec.y_mean[k]) + abs(rec.y_std[k]) * out[k] for k in range(6))
+    B = np.array([[rec.elem[e][k] / M[k] for k in range(6)] for e in range(rec.n_elem)])
+    Pj = np.eye(6) - B.T @ np.linalg.solve(B @ B.T, B) if rec.n_elem else np.eye(6)
+    bound *= np.abs(Pj).sum(axis=1).max()
+    return rec.theta_s / np.log(bound / eps) if bound > eps else float("inf")
+
+
 def glorot(seed):
     """Seeded Glorot-uniform weights and zero biases in the flat order."""
     rng = np.random.default_rng(seed)
