@@ -25,26 +25,26 @@ cudaError_t chem_pass_launch(const Params<Real, K>& P, const State<Real, Real>& 
       a.stats = stats;
       cudaError_t e = cudaMemsetAsync(fb_count, 0, sizeof(unsigned), st);
       if (e != cudaSuccess) return e;
+      int dev = 0, sms = 0;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
       if (a.engine == 1) {
-        // tcgen05 network: 128 cells per tile, persistent grid of 4 blocks per SM
+        // tcgen05 network: 128 cells per tile, persistent grid of kTcBlocksPerSm blocks per SM
         constexpr size_t smem = tc_smem_bytes();
         auto kern = chem_surrogate_tc_kernel<K, Real, Real>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         const int nb = (int)std::min<long long>(((long long)P.N + tc::M - 1) / tc::M,
                                                 (long long)sms * kTcBlocksPerSm);
         kern<<<nb, tc::M, smem, st>>>(P, S, src, a, kDefaultWaitCycles);
       } else {
         // warp-level network; persistent grid: each block loads the network once
-        const int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, 152 * 4);
+        const int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, (long long)sms * 4);
         chem_surrogate_kernel<K, Real, Real><<<nb, 256, 0, st>>>(P, S, src, a);
       }
       const int fb_blocks = (int)std::min<long long>(
-          ((long long)P.N + FALLBACK_BLOCK - 1) / FALLBACK_BLOCK, 152 * 16);
+          ((long long)P.N + FALLBACK_BLOCK - 1) / FALLBACK_BLOCK, (long long)sms * 16);
       chem_fallback_kernel<K, Real, Real><<<fb_blocks, FALLBACK_BLOCK, 0, st>>>(P, S, src,
                                                                                 fb_idx, fb_count);
     } else {
