@@ -272,6 +272,42 @@ template <> struct Codec<__half, float> {
 // FP32 uses the fast hardware approximations (a few ulp); FP64 stays IEEE.
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
+// Packed FP32 pairs (the f32x2 arithmetic of sm_100 and later: one
+// instruction for two lanes of independent FP32 work).
+__device__ __forceinline__ uint64_t f2_bits(float2 v) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_of(uint64_t r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  uint64_t d;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)),
+      "l"(f2_bits(c)));
+  return f2_of(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  uint64_t d;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_of(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  uint64_t d;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_of(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  uint64_t d;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_of(d);
+}
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fpow(float x, float y) { return __powf(x, y); }
@@ -1445,8 +1481,43 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
       fm[a] = Real(0.5) * (rf0 + at(F_RF, a, -1));
       fp[a] = Real(0.5) * (rf0 + at(F_RF, a, +1));
     }
+    // FP32: species in pairs with packed f32x2 arithmetic; the last one of an
+    // odd count (and every species in FP64) one at a time
+    constexpr int KP = sizeof(Real) == 4 ? (K / 2) * 2 : 0;
+    if constexpr (KP > 0) {
+      float2 sx2[3] = {splat2(0.f), splat2(0.f), splat2(0.f)}, sYm2 = splat2(0.f);
+      const float2 prf = splat2(-phif * rho), pf = splat2(phif), ip = splat2(iphr);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+      for (int k = 0; k < KP; k += 2) {
+        const float2 y0 = make_float2(Y0[k], Y0[k + 1]);
+        float2 adv = splat2(0.f), dif = splat2(0.f), cen = splat2(0.f);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const float2 dm = sub2(y0, make_float2(at(F_Y0 + k, a, -1), at(F_Y0 + k + 1, a, -1)));
+          const float2 dp = sub2(make_float2(at(F_Y0 + k, a, +1), at(F_Y0 + k + 1, a, +1)), y0);
+          adv = fma2(splat2(u[a]), u[a] > 0.f ? dm : dp, adv);
+          dif = fma2(splat2(fp[a]), dp, dif);
+          dif = fma2(splat2(-fm[a]), dm, dif);
+          const float2 sd = add2(dp, dm);
+          cen = fma2(splat2(u[a]), sd, cen);
+          sx2[a] = fma2(make_float2(P.cpD[k], P.cpD[k + 1]), sd, sx2[a]);
+        }
+        float2 dY = fma2(prf, adv, fma2(make_float2(P.Dlat[k], P.Dlat[k + 1]), dif,
+                                        mul2(pf, make_float2(om[k], om[k + 1]))));
+        dY = fluid_on ? mul2(dY, ip) : splat2(0.f);
+        const float2 yn = add2(y0, dY);
+        Yn[k] = yn.x;
+        Yn[k + 1] = yn.y;
+        // material increment: the step's increment plus u.grad Y_k (central)
+        const float2 dm2 = fluid_on ? fma2(splat2(0.5f), cen, dY) : splat2(0.f);
+        sYm2 = fma2(make_float2(P.invM[k], P.invM[k + 1]), dm2, sYm2);
+      }
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) sx[a] += sx2[a].x + sx2[a].y;
+      sYm += sYm2.x + sYm2.y;
+    }
+#pragma unroll
+    for (int k = KP; k < K; ++k) {
       Real adv = 0, dif = 0, cen = 0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
@@ -1574,19 +1645,48 @@ __device__ __forceinline__ Real cell_update(const Params<Real, K>& P, const Stat
 #pragma unroll
     for (int a = 0; a < DIM; ++a) jst[a] = keep * mraw[a] + B * u[a] + src_w * CS2 * F[a];
   }
+  // FP32 updates a direction and its opposite together with packed f32x2
+  // arithmetic (c.u, c.H, c.F of the opposite are the negated ones); the rest
+  // direction, and every direction in FP64, one at a time
+  constexpr bool PAIRS = sizeof(Real) == 4;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const Real w = Real(L::w(i));
+    if constexpr (PAIRS) {
+      if (L::opp(i) < i) continue;  // done with its opposite
+    }
     Real cu = 0, cH = 0, cF = 0, cj = 0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       if (L::c(i, a) > 0) { cu += u[a]; cH += H[a]; cF += F[a]; cj += jst[a]; }
       if (L::c(i, a) < 0) { cu -= u[a]; cH -= H[a]; cF -= F[a]; cj -= jst[a]; }
     }
-    const Real e = cu * (Real(3) + Real(4.5) * cu) - uu15;
-    const Real x = (cH - uH) * e + (cF - uF);
     Real gi = gin[i];
     if constexpr (Acc::kStash) gi = A.st[i * BLOCK + threadIdx.x];
+    if constexpr (PAIRS) {
+      if (i > 0) {
+        const int j = L::opp(i);
+        Real gj = gin[j];
+        if constexpr (Acc::kStash) gj = A.st[j * BLOCK + threadIdx.x];
+        const float2 cu2 = make_float2(cu, -cu);
+        const float2 e = fma2(cu2, fma2(cu2, splat2(4.5f), splat2(3.f)), splat2(-uu15));
+        const float2 x = fma2(sub2(make_float2(cH, -cH), splat2(uH)), e,
+                              sub2(make_float2(cF, -cF), splat2(uF)));
+        float2 t = fma2(splat2(B), e, splat2(A0));
+        t = fma2(splat2(src_w), x, t);
+        const float w = float(L::w(i));
+        float2 g = fma2(splat2(keep), make_float2(gi, gj), mul2(splat2(w), t));
+        if constexpr (FO)
+          g = sub2(g, mul2(splat2(w), fma2(splat2(3.f), make_float2(cj, -cj), splat2(Pst))));
+        Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g.x,
+                                  P.g_scale * Real(1.0 / L::w(i)));
+        Codec<Store, Real>::store(S.g_out + (size_t)j * P.N + c, g.y,
+                                  P.g_scale * Real(1.0 / L::w(j)));
+        continue;
+      }
+    }
+    const Real w = Real(L::w(i));
+    const Real e = cu * (Real(3) + Real(4.5) * cu) - uu15;
+    const Real x = (cH - uH) * e + (cF - uF);
     Real g = keep * gi + w * (A0 + B * e + src_w * x);
     if constexpr (FO) g -= w * (Pst + Real(3) * cj);
     Codec<Store, Real>::store(S.g_out + (size_t)i * P.N + c, g, P.g_scale * Real(1.0 / L::w(i)));
