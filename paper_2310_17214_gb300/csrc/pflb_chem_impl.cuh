@@ -34,14 +34,24 @@ cudaError_t chem_pass_launch(const Params<Real, K>& P, const State<Real, Real>& 
         constexpr size_t smem = tc_smem_bytes();
         auto kern = chem_surrogate_tc_kernel<K, Real, Real>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // all of the SM's unified memory as shared memory, so that the blocks
+        // of the resident wave fit side by side
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         const int nb = (int)std::min<long long>(((long long)P.N + tc::M - 1) / tc::M,
                                                 (long long)sms * kTcBlocksPerSm);
         kern<<<nb, tc::M, smem, st>>>(P, S, src, a, kDefaultWaitCycles);
       } else {
-        // warp-level network; persistent grid: each block loads the network once
-        const int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, (long long)sms * 4);
-        chem_surrogate_kernel<K, Real, Real><<<nb, 256, 0, st>>>(P, S, src, a);
+        // warp-level network; one resident wave: each block loads the network once
+        auto kern = chem_surrogate_kernel<K, Real, Real>;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+        if (e != cudaSuccess) return e;
+        occ = std::max(1, occ);
+        const int nb = (int)std::min<long long>(((long long)P.N + 255) / 256, (long long)sms * occ);
+        kern<<<nb, 256, 0, st>>>(P, S, src, a);
       }
       const int fb_blocks = (int)std::min<long long>(
           ((long long)P.N + FALLBACK_BLOCK - 1) / FALLBACK_BLOCK, (long long)sms * 16);

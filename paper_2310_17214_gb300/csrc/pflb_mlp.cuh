@@ -72,10 +72,11 @@ struct SmemNet {
   float bias[NPB];
 };
 // Shared-memory copy for inference (forward layout only).
-struct SmemFwd {
+struct __align__(16) SmemFwd {
   __nv_bfloat16 wf[NPAD];
   float bias[NPB];
 };
+static_assert(NPAD * 2 % 16 == 0 && NPB * 4 % 16 == 0, "16-byte copies of the network");
 
 __device__ __forceinline__ void load_words(uint32_t* dst, const uint32_t* src, int words) {
   for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
@@ -85,9 +86,29 @@ __device__ __forceinline__ void load_net(SmemNet& s, const Net& n) {
   load_words(reinterpret_cast<uint32_t*>(s.wb), reinterpret_cast<const uint32_t*>(n.wb), NPAD / 2);
   load_words(reinterpret_cast<uint32_t*>(s.bias), reinterpret_cast<const uint32_t*>(n.bias), NPB);
 }
+// 16-byte copy of NV vectors by a block of BT threads, every load issued
+// before the first store (a block loads the network once; a copy that waits
+// on each load in turn costs microseconds per block)
+template <int NV, int BT>
+__device__ __forceinline__ void load_vec16(uint4* dst, const uint4* __restrict__ src) {
+  constexpr int R = (NV + BT - 1) / BT;
+  uint4 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = threadIdx.x + r * BT;
+    if (i < NV) v[r] = __ldg(src + i);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = threadIdx.x + r * BT;
+    if (i < NV) dst[i] = v[r];
+  }
+}
+template <int BT = 256>
 __device__ __forceinline__ void load_fwd(SmemFwd& s, const Net& n) {
-  load_words(reinterpret_cast<uint32_t*>(s.wf), reinterpret_cast<const uint32_t*>(n.wf), NPAD / 2);
-  load_words(reinterpret_cast<uint32_t*>(s.bias), reinterpret_cast<const uint32_t*>(n.bias), NPB);
+  load_vec16<NPAD * 2 / 16, BT>(reinterpret_cast<uint4*>(s.wf), reinterpret_cast<const uint4*>(n.wf));
+  load_vec16<NPB * 4 / 16, BT>(reinterpret_cast<uint4*>(s.bias),
+                               reinterpret_cast<const uint4*>(n.bias));
 }
 
 // B fragment (b0, b1) of layer L, n-tile j, k-tile kk for this lane.

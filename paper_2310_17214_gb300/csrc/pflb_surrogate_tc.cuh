@@ -127,16 +127,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // Weight W_l (input-major [in][out], FP32, inside the flat parameter vector)
-// as the B operand (N = out padded to np, K = in padded to kp), BF16.
-__device__ __forceinline__ void load_b(__nv_bfloat16* dst, const float* theta, int l, int np,
-                                       int kp) {
-  const int in = mlp::dim(l), out = mlp::dim(l + 1);
-  const float* W = theta + mlp::woff(l);
+// as the B operand (N = out padded to NP, K = in padded to KP), BF16, by the
+// block's M threads: every load is issued before the first store (read along
+// the output index, so that neighbouring threads read neighbouring weights).
+template <int L, int NP, int KP>
+__device__ __forceinline__ void load_b(__nv_bfloat16* dst, const float* __restrict__ theta) {
+  constexpr int IN = mlp::dim(L), OUT = mlp::dim(L + 1), R = NP * KP / M;
+  static_assert(NP * KP % M == 0, "whole rounds of the block");
+  constexpr int C = R < 16 ? R : 16;  // loads in flight per thread
+  static_assert(R % C == 0, "whole chunks");
+  const float* W = theta + mlp::woff(L);
   char* base = reinterpret_cast<char*>(dst);
-  for (int i = threadIdx.x; i < np * kp; i += blockDim.x) {
-    const int n = i / kp, k = i % kp;
-    const float w = (n < out && k < in) ? W[k * out + n] : 0.f;
-    *reinterpret_cast<__nv_bfloat16*>(base + kmajor_off(n, k, kp)) = __float2bfloat16_rn(w);
+#pragma unroll 1
+  for (int r0 = 0; r0 < R; r0 += C) {
+    float v[C];
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const int i = threadIdx.x + (r0 + r) * M, n = i % NP, k = i / NP;
+      v[r] = (n < OUT && k < IN) ? __ldg(W + k * OUT + n) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const int i = threadIdx.x + (r0 + r) * M, n = i % NP, k = i / NP;
+      *reinterpret_cast<__nv_bfloat16*>(base + kmajor_off(n, k, KP)) = __float2bfloat16_rn(v[r]);
+    }
   }
 }
 
@@ -158,10 +172,10 @@ chem_surrogate_tc_kernel(const Params<Real, K> P, const State<Real, Store> S,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   // weights, biases, barrier, tensor memory
-  load_b(s.w0, A.net.theta, 0, 64, 16);
-  load_b(s.w1, A.net.theta, 1, 64, 64);
-  load_b(s.w2, A.net.theta, 2, 64, 64);
-  load_b(s.w3, A.net.theta, 3, 16, 64);
+  load_b<0, 64, 16>(s.w0, A.net.theta);
+  load_b<1, 64, 64>(s.w1, A.net.theta);
+  load_b<2, 64, 64>(s.w2, A.net.theta);
+  load_b<3, 16, 64>(s.w3, A.net.theta);
   for (int i = threadIdx.x; i < 64; i += blockDim.x) {
     s.b0[i] = A.net.theta[mlp::boff(0) + i];
     s.b1[i] = A.net.theta[mlp::boff(1) + i];
