@@ -68,8 +68,12 @@ extern "C" {
 /* chemistry */
 #define PFLB_CHEM_NONE 0
 #define PFLB_CHEM_EXPLICIT 1    /* forward-Euler Arrhenius source */
-#define PFLB_CHEM_IMPLICIT 2    /* per-cell backward Euler + Newton, FP64 (operator split) */
-#define PFLB_CHEM_SURROGATE 3   /* learned MLP increments, Newton fallback (six species) */
+#define PFLB_CHEM_IMPLICIT 2    /* per-cell backward Euler + Newton, FP64 state and residual
+                                   (operator split); FP32 domains build and eliminate the
+                                   Newton matrix in FP32, the root is the same (update < 1e-13) */
+#define PFLB_CHEM_SURROGATE 3   /* learned MLP increments, Newton fallback (six species); the
+                                   fallback of FP32 domains is an FP32 backward-Euler step in
+                                   increment form, converged to a few ulp of the fields */
 
 #define PFLB_HOST 0
 #define PFLB_DEVICE 1
@@ -427,7 +431,8 @@ typedef struct pflb_surrogate {
  * PFLB_CHEM_SURROGATE and six species.  A cell uses the network when its
  * inputs are inside [lo, hi] and |sum_k elem[e][k] M_e / M_k dY_k| <= tol for
  * every element; the increment is then projected onto the element-conserving
- * subspace.  Other fluid cells take the backward-Euler Newton integrator.
+ * subspace.  Other fluid cells take the backward-Euler Newton integrator (FP32
+ * in FP32 domains, see PFLB_CHEM_SURROGATE).
  * The network must outlive the domain's use of it. */
 int pflb_set_surrogate(pflb_domain* d, const pflb_mlp* m, const pflb_surrogate* s);
 
