@@ -647,6 +647,64 @@ struct LauncherImpl final : Launcher {
     }
   }
 
+  // One step's launches on stream st, with its host bookkeeping.
+  cudaError_t one_step(Buffers& B, int& cur, cudaStream_t st, dim3 grid, size_t smem) {
+    cudaError_t e = cudaSuccess;
+    if constexpr (K > 0) {
+      if (P.chem >= 2) {
+        e = chem_pass(B, cur, nullptr, st);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    const double* prev = (!p0_closed && B.pending)
+                             ? B.partials + (size_t)4 * B.slots * B.last_parity : nullptr;
+    if (kernel_sel == 1 && tma_usable(B, cur)) {
+      e = step_tma(B, cur, st, prev);
+      if (e != cudaSuccess) return e;
+    } else if (kernel_sel == 2) {
+      e = step_persistent<Tile<DIM, 32, 1>>(B, cur, st, prev, pgrid[0]);
+      if (e != cudaSuccess) return e;
+    } else if (kernel_sel == 3) {
+      e = step_persistent<Tile<DIM, 32, 2>>(B, cur, st, prev, pgrid[1]);
+      if (e != cudaSuccess) return e;
+    } else if (kernel_sel == 4 || kernel_sel == 5) {
+      e = kernel_sel == 5 ? step_march<true>(B, cur, st, prev) : step_march<false>(B, cur, st, prev);
+      if (e != cudaSuccess) return e;
+    } else {
+      step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
+                                                                   prev, (unsigned)B.last_nb);
+      B.last_nb = step_blocks();
+    }
+    if (P.feed) {
+      e = feed(B, cur, st);
+      if (e != cudaSuccess) return e;
+    }
+    if (P.nscbc)
+      outlet_kernel<Real><<<1, BLOCK, 0, st>>>(static_cast<const Real*>(B.ob), P.ny * P.nz,
+                                               B.scal, P.nscbc_K);
+    ++B.nstep;
+    if (P.moving) {
+      e = phase(B, B.nstep, st);
+      if (e != cudaSuccess) return e;
+    }
+    B.pending = p0_closed ? 0 : 1;
+    B.last_parity = cur;
+    cur = 1 - cur;
+    return cudaGetLastError();
+  }
+
+  // Steps are replayed in pairs from a CUDA graph when a call asks for many:
+  // after two plain steps every launch argument repeats every second step
+  // (the ping-pong buffers, the reduction's parity and block count), and a
+  // graph launch of the pair costs one launch instead of one per kernel
+  // (the small domains are launch-bound).  Not for moving solids, whose
+  // phase kernel takes the step number as an argument.
+  static constexpr int kGraphMinSteps = 32;
+  cudaStream_t cap_st = nullptr;  // capture stream, created on first use
+  ~LauncherImpl() override {
+    if (cap_st) cudaStreamDestroy(cap_st);
+  }
+
   cudaError_t step(Buffers& B, int& cur, int nsteps, cudaStream_t st) override {
     constexpr size_t smem = step_smem_bytes<DIM, K, Real, Store>();
     cudaError_t e = cudaFuncSetAttribute(step_kernel<DIM, K, Real, Store>,
@@ -658,47 +716,55 @@ struct LauncherImpl final : Launcher {
       e = cudaMemsetAsync(B.tile_ctr, 0, 2 * sizeof(unsigned), st);
       if (e != cudaSuccess) return e;
     }
-    for (int n = 0; n < nsteps; ++n) {
-      if constexpr (K > 0) {
-        if (P.chem >= 2) {
-          e = chem_pass(B, cur, nullptr, st);
-          if (e != cudaSuccess) return e;
+    int n = 0;
+    if (nsteps >= kGraphMinSteps && !P.moving) {
+      for (; n < 2; ++n) {
+        e = one_step(B, cur, st, grid, smem);
+        if (e != cudaSuccess) return e;
+      }
+      if (!cap_st) {
+        e = cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+      }
+      const int cur0 = cur;
+      const long long nstep0 = B.nstep;
+      const int pending0 = B.pending, parity0 = B.last_parity;
+      const long long last_nb0 = B.last_nb;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t x = nullptr;
+      e = cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        cudaError_t e1 = one_step(B, cur, cap_st, grid, smem);
+        if (e1 == cudaSuccess) e1 = one_step(B, cur, cap_st, grid, smem);
+        e = cudaStreamEndCapture(cap_st, &g);
+        if (e == cudaSuccess) e = e1;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+      if (e == cudaSuccess) {
+        // the capture advanced the bookkeeping by the pair the first launch runs
+        const int pairs = (nsteps - n) / 2;
+        for (int q = 0; q < pairs && e == cudaSuccess; ++q) {
+          e = cudaGraphLaunch(x, st);
+          if (q > 0) B.nstep += 2;
         }
-      }
-      const double* prev = (!p0_closed && B.pending)
-                               ? B.partials + (size_t)4 * B.slots * B.last_parity : nullptr;
-      if (kernel_sel == 1 && tma_usable(B, cur)) {
-        e = step_tma(B, cur, st, prev);
-        if (e != cudaSuccess) return e;
-      } else if (kernel_sel == 2) {
-        e = step_persistent<Tile<DIM, 32, 1>>(B, cur, st, prev, pgrid[0]);
-        if (e != cudaSuccess) return e;
-      } else if (kernel_sel == 3) {
-        e = step_persistent<Tile<DIM, 32, 2>>(B, cur, st, prev, pgrid[1]);
-        if (e != cudaSuccess) return e;
-      } else if (kernel_sel == 4 || kernel_sel == 5) {
-        e = kernel_sel == 5 ? step_march<true>(B, cur, st, prev) : step_march<false>(B, cur, st, prev);
-        if (e != cudaSuccess) return e;
+        n += 2 * pairs;
       } else {
-        step_kernel<DIM, K, Real, Store><<<grid, BLOCK, smem, st>>>(P, state(B, cur), p0_closed,
-                                                                     prev, (unsigned)B.last_nb);
-        B.last_nb = step_blocks();
+        // capture refused: undo its bookkeeping, step without a graph
+        cudaGetLastError();
+        cur = cur0;
+        B.nstep = nstep0;
+        B.pending = pending0;
+        B.last_parity = parity0;
+        B.last_nb = last_nb0;
+        e = cudaSuccess;
       }
-      if (P.feed) {
-        e = feed(B, cur, st);
-        if (e != cudaSuccess) return e;
-      }
-      if (P.nscbc)
-        outlet_kernel<Real><<<1, BLOCK, 0, st>>>(static_cast<const Real*>(B.ob), P.ny * P.nz,
-                                                 B.scal, P.nscbc_K);
-      ++B.nstep;
-      if (P.moving) {
-        e = phase(B, B.nstep, st);
-        if (e != cudaSuccess) return e;
-      }
-      B.pending = p0_closed ? 0 : 1;
-      B.last_parity = cur;
-      cur = 1 - cur;
+      if (x) cudaGraphExecDestroy(x);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return e;
+    }
+    for (; n < nsteps; ++n) {
+      e = one_step(B, cur, st, grid, smem);
+      if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
   }
