@@ -265,7 +265,11 @@ int pflb_set_fields(pflb_domain* d, unsigned mask, const void* src, int dtype, i
  * NaN in T, Y, the populations' sum or the velocity of any cell makes the
  * step's FP64 reduction NaN); a bounded device wait that ran out latches
  * PFLB_ERR_TIMEOUT.  The latched code is returned by the next synchronising
- * call (get_fields / get_scalars); the fields are then not to be trusted. */
+ * call (get_fields / get_scalars); the fields are then not to be trusted.
+ * A call for 32 steps or more replays pairs of steps from a CUDA graph that
+ * it captures on a private stream (not for a moving solid); the graph is
+ * launched on the domain's stream, so the call must not run while that
+ * stream is being captured. */
 int pflb_step(pflb_domain* d, int nsteps);
 
 /* Copy fields out, packed in the order T, Y, Ts, U, RHO, PH, G of the mask
