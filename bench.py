@@ -419,6 +419,22 @@ def errors_vs_fp64(prob, fields, steps, dev, precisions):
     return res
 
 
+def _ms_per_call(dom, nsteps, calls, flush, st):
+    """Mean device time of one dom.step(nsteps) call (CUDA events, L2 flushed
+    before each call)."""
+    import torch
+    tot = 0.0
+    for _ in range(calls):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        dom.step(nsteps)
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / calls
+
+
 def _ms_per_step(dom, steps, flush, st):
     """Mean device time of one step (CUDA events, L2 flushed between steps)."""
     import torch
@@ -480,7 +496,9 @@ def flame2d_leg(dev, flush, precisions=("fp32", "fp64"), settle=400, steps=200):
     chemistry, isothermal walls) held by the inlet feedback: per step the fused
     step kernel plus the two feedback kernels (consumption sum, inlet speed).
     6 MB of state: L2-resident, so the L2 is flushed between steps; the
-    launch latency of three small kernels bounds it, not HBM."""
+    launch latency of three small kernels bounds it, not HBM.  Also timed:
+    calls of 200 steps (the library replays step pairs from a CUDA graph),
+    the L2 flushed before each call."""
     import torch
     st = torch.cuda.current_stream(dev)
     out = {}
@@ -490,12 +508,14 @@ def flame2d_leg(dev, flush, precisions=("fp32", "fp64"), settle=400, steps=200):
         dom = make_domain(p, f, prec, dev, st.cuda_stream)
         dom.step(settle)
         ms = _ms_per_step(dom, steps, flush, st)
+        ms_long = _ms_per_call(dom, 200, 5, flush, st) / 200
         sc = dom.scalars()
         dom.close()
         N = f["phi"].size
         out[prec] = {"ms_per_step": ms, "mlups": N / ms / 1e3, "kernels_per_step": 3,
+                     "ms_per_step_200_step_calls": ms_long, "mlups_200_step_calls": N / ms_long / 1e3,
                      "u_in_m_s": sc["u_in"] * p["dx"] / p["dt"],
-                     "steps_before": settle + steps + 3}
+                     "steps_before": settle + steps + 3 + 1000}
     q = I.config6()
     return {"workload": f"wall_bounded_flame_{q['nx']}x{q['ny']}_d2q9_k{q['K']}",
             "l2": "flushed between steps (256 MiB write)",
