@@ -683,6 +683,10 @@ def main():
     ap.add_argument("--precision", default=DEFAULT_PRECISION,
                     choices=["fp32", "fp64", "fp32_fp16"])
     ap.add_argument("--quick", action="store_true", help="the headline only, no legs")
+    ap.add_argument("--kernel", default=None,
+                    help="step kernel of the headline (tiled, march, ...) instead of the "
+                         "autotuner's choice (for profiler runs, where the autotuner's own "
+                         "timings are distorted)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -702,7 +706,10 @@ def main():
     N = fields["phi"].size
     peaks, peak_kind = measured_peaks()
 
-    dom = make_domain(prob, fields, args.precision, dev, st.cuda_stream, tune=True)
+    dom = make_domain(prob, fields, args.precision, dev, st.cuda_stream, tune=args.kernel is None)
+    if args.kernel is not None:
+        dom.select_kernel(args.kernel)
+        dom.tuned = {"chosen": args.kernel, "us_per_step": None}
     tuned = dom.tuned
     ms, wall, clk = time_steps(dom, args.steps, args.warmup, dev, st, pg=pg, clocks=(rank == 0))
     final_step = dom.scalars()["step"]
