@@ -102,3 +102,45 @@ def test_flame_errors_see_a_shift_of_a_third_of_a_cell():
     e = S.flame_errors(test, ref, np.zeros(64 * 4), p)
     assert abs(e["front_max_diff_cells"] - 1.0 / 3.0) < 0.02
     assert e["rows_with_front"] == 4 and e["rows_front_mismatch"] == 0
+
+
+def _record(y_mean, y_std, theta_s, skip_eps):
+    X = np.array([[300.0] + [0.1] * 6 + [1e5], [2000.0] + [0.2] * 6 + [1e5]])
+    stats = (X.mean(axis=0), X.std(axis=0), np.asarray(y_mean), np.asarray(y_std))
+    return S.make_surrogate(stats, X, theta_s, I.SPECIES6, 1e-6, skip_eps=skip_eps)
+
+
+def test_skip_temperature_meets_its_bound():
+    """T_skip of the cold-tile option: with an output layer of constant
+    weights w (|tanh| <= 1 bounds each output by 64 |w| (1 + 2^-7) + |b|),
+    the projected increment exp(-theta_s / T) ||P||_inf max_k(|ybar_k| +
+    s_k max|out_k|) equals skip_eps at T = T_skip.  ||P||_inf is taken here
+    from an orthonormal basis of the element-conserving subspace (an
+    independent route to the same projection)."""
+    import scipy.linalg as sl
+    theta = np.zeros(9286, dtype=np.float32)
+    theta[-6 - 384:-6] = 0.01
+    theta[-6:] = [0.0, 0.1, -0.2, 0.0, 0.05, 0.0]
+    y_mean = [0.0, 1e-3, 0.0, -2e-3, 0.0, 0.0]
+    y_std = [1.0, 0.5, 2.0, 1.0, 1.0, 0.0]
+    rec = _record(y_mean, y_std, 12000.0, 1e-12)
+    T_skip = S.skip_temperature(theta, rec, I.M6)
+    elem, _ = I.element_matrix(I.SPECIES6)
+    B = np.array(elem) / np.asarray(I.M6)[None, :]
+    Nb = sl.null_space(B)
+    P = Nb @ Nb.T
+    out = 64 * float(np.float32(0.01)) * 1.0078125 + np.abs(theta[-6:].astype(np.float64))
+    bound = np.max(np.abs(y_mean) + np.asarray(y_std) * out) * np.abs(P).sum(axis=1).max()
+    assert T_skip > 0
+    assert abs(np.exp(-12000.0 / T_skip) * bound / 1e-12 - 1.0) < 1e-9
+    # colder cells are below the bound, hotter ones above it
+    assert np.exp(-12000.0 / (0.99 * T_skip)) * bound < 1e-12 < np.exp(-12000.0 / (1.01 * T_skip)) * bound
+
+
+def test_skip_temperature_edge_cases():
+    """No skipping without skip_eps; every temperature skips when the
+    network's bound is already below skip_eps."""
+    theta = np.zeros(9286, dtype=np.float32)
+    assert S.skip_temperature(theta, _record([0.0] * 6, [1.0] * 6, 12000.0, 0.0), I.M6) == 0.0
+    assert S.skip_temperature(theta, _record([0.0] * 6, [0.0] * 6, 12000.0, 1e-12),
+                              I.M6) == float("inf")
