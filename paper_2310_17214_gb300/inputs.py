@@ -609,7 +609,8 @@ def wall_phi(d, eta):
                     np.where(d >= eta / 2, 0.0, 0.5 * (1.0 - np.sin(np.pi * d / eta))))
 
 
-def di_channel(L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, A_u=145.0, sharp=False):
+def di_channel(L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, A_u=145.0, sharp=False,
+               T_w=None, A_T=0.0):
     """Isothermal channel of Sec. 4.1 (Fig. A_u-vs-MSE): width L cells between
     two planar walls, inlet-outlet distance H = 5 L, uniform inlet speed,
     characteristic (non-reflecting) outlet, Re = u_in L / nu = 100, air at
@@ -617,7 +618,11 @@ def di_channel(L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, A_u=145.0, sha
     sides with eq. def-phi interfaces of width eta centred on the walls, the
     inlet speed weighted by the fluid fraction, drag A_u.  Sharp form
     (sharp=True): the same channel with the walls as half-way bounce-back
-    lattice walls and no phase field (the coupling of Sec. 4 switched off)."""
+    lattice walls and no phase field (the coupling of Sec. 4 switched off).
+    With T_w (Sec. 4.2, Fig. A_T-vs-MSE) the walls are hot: the gas enters at
+    300 K, the sharp walls hold T_w, the diffuse walls are solid layers at
+    T_w (uniform solid temperature) that exchange heat with the gas through
+    the interface coupling A_T."""
     H = 5 * L if H is None else H
     ny = L if sharp else L + 2 * solid
     p = _base(2, H, ny)
@@ -627,6 +632,11 @@ def di_channel(L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, A_u=145.0, sha
               "A_u": 0.0 if sharp else A_u, "A_T": 0.0, "eta": float(eta), "T_in": 300.0,
               "Ts_uniform": 300.0, "p0_mode": "fixed", "L": L, "solid": 0 if sharp else solid,
               "name": f"channel_{'si' if sharp else 'di'}_L{L}_eta{eta}_Re{Re:g}"})
+    if T_w is not None:
+        p["wall_T"] = [0.0, 0.0, float(T_w), float(T_w), 0.0, 0.0]
+        p["Ts_uniform"] = float(T_w)
+        p["A_T"] = 0.0 if sharp else float(A_T)
+        p["name"] += f"_Tw{T_w:g}"
     return p
 
 

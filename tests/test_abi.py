@@ -118,7 +118,8 @@ def test_every_workload_passes_the_stability_checks():
     probs = [I.config1(), I.config2(), I.config2(precision="fp32"), I.config3(),
              I.config3_crop(64), I.config4(), I.config4(chem="surrogate"),
              I.mixture_transport(I.config2()), I.mixture_transport(I.config3()), I.config6(),
-             I.di_channel(), I.di_channel(sharp=True)] + I.config5()
+             I.di_channel(), I.di_channel(sharp=True),
+             I.di_channel(T_w=400.0, A_T=1000.0), I.di_channel(sharp=True, T_w=400.0)] + I.config5()
     for p in probs:
         rc, msg = nat.validate(p, p.get("precision", "fp64"))
         assert rc == 0, (p.get("name"), rc, msg)

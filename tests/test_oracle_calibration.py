@@ -1,0 +1,63 @@
+"""The A_T calibration of Sec. 4.2 (Fig. A_T-vs-MSE) on the oracle at a
+reduced size: the hot-wall channel (gas entering at 300 K between walls at
+400 K) in its diffuse form against its sharp form.  What the paper's
+procedure needs and what the physics fixes:
+
+* the sharp channel's temperature across the sampled section is symmetric
+  about the centreline and lies between the inlet and wall temperatures,
+  hotter at the walls than at the centre;
+* the mean standard error of eq. mean-standard-error-f (f = T) has an
+  interior minimum in A_T: too weak a coupling leaves the gas near the
+  diffuse walls cold, too strong a one heats it ahead of the sharp wall.
+
+The sweep driver (calibration.sweep_A_T) takes the oracle as its runner here;
+on the GPU it runs the library with one stream per value.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2310_17214_gb300 import calibration as C
+from paper_2310_17214_gb300 import inputs as I
+
+SIZE = {"L": 20, "eta": 4, "solid": 4, "H": 60}
+STEPS = 3000  # about 2.5 transits of the channel: the section at 0.9 H is steady
+
+
+@pytest.fixture(autouse=True)
+def _threads():
+    O.set_threads(0)
+    yield
+
+
+def _oracle_run(probs):
+    out = []
+    for p in probs:
+        f = I.di_channel_fields(p)
+        s = O.OracleState(p, f["phi"], f["T"])
+        s.step(STEPS)
+        out.append(s.T.copy())
+    return out
+
+
+def test_sharp_hot_wall_channel_profile():
+    p = I.di_channel(sharp=True, T_w=400.0, **SIZE)
+    T = _oracle_run([p])[0].reshape(p["ny"], p["nx"])
+    col = T[:, int(round(0.9 * p["nx"])) - 1]
+    assert np.max(np.abs(col - col[::-1])) <= 1e-9 * 400.0
+    assert np.all(col > 300.0) and np.all(col < 400.0)
+    assert col[0] > col[p["ny"] // 2] + 1.0
+
+
+def test_A_T_sweep_has_an_interior_minimum():
+    r = C.sweep_A_T([8, 30, 100, 300, 1000], T_w=400.0, A_u=145.0, steps=STEPS,
+                    run=_oracle_run, **SIZE)
+    mse = np.asarray(r["mse"])
+    k = int(np.argmin(mse))
+    assert 0 < k < len(mse) - 1, mse
+    assert mse[k] < 1e-2 * mse[0] and mse[k] < 0.1 * mse[-1], mse
+    lo, hi = r["A_T"][k - 1], r["A_T"][k + 1]
+    assert lo < r["A_T_star"] < hi
+    assert r["paper_fit_A_T_star"] == pytest.approx(24.24 + 33.81 * 400.0 / 300.0)
