@@ -61,3 +61,18 @@ def test_A_T_sweep_has_an_interior_minimum():
     lo, hi = r["A_T"][k - 1], r["A_T"][k + 1]
     assert lo < r["A_T_star"] < hi
     assert r["paper_fit_A_T_star"] == pytest.approx(24.24 + 33.81 * 400.0 / 300.0)
+
+
+def test_refined_minimiser_is_the_vertex_of_the_log_parabola():
+    """The refinement fits a parabola through the three samples around the
+    sampled minimum in (log value, log MSE): for samples of an exact such
+    parabola it returns the vertex; at the end of the range it keeps the
+    sampled value."""
+    a_star = 137.0
+    values = [10.0, 40.0, 100.0, 250.0, 900.0]
+    mse = [float(np.exp(0.7 * (np.log(v) - np.log(a_star)) ** 2 - 9.0)) for v in values]
+    sampled, refined = C._minimum(values, mse)
+    assert sampled == 100.0
+    assert refined == pytest.approx(a_star, rel=1e-9)
+    sampled, refined = C._minimum(values, sorted(mse))
+    assert sampled == refined == 10.0
