@@ -66,15 +66,21 @@ def _minimum(values, mse):
 
 
 def sweep_A_u(values, L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, steps=15000,
-              precision="fp64", device=0, chunk=1000):
+              precision="fp64", device=0, chunk=1000, run=None):
     """MSE(A_u) of the diffuse channel against the sharp one.  Returns the
     values, the MSE of each, the sampled minimiser and the minimiser of a
-    parabola through the three samples around it in (log A_u, log MSE)."""
+    parabola through the three samples around it in (log A_u, log MSE).
+    `run` (a function from the list of problems to their streamwise
+    velocities) replaces the library runs, e.g. by another implementation of
+    the same steps."""
     values = [float(a) for a in values]
     p_si = I.di_channel(L=L, eta=eta, solid=solid, Re=Re, u_in=u_in, H=H, sharp=True)
     p_di = [I.di_channel(L=L, eta=eta, solid=solid, Re=Re, u_in=u_in, H=H, A_u=a)
             for a in values]
-    us = _run_all([p_si] + p_di, steps, precision, device, chunk)
+    if run is None:
+        def run(probs):
+            return _run_all(probs, steps, precision, device, chunk)
+    us = run([p_si] + p_di)
     mse = [I.channel_mse(us[0], u, p_si, p) for u, p in zip(us[1:], p_di)]
     sampled, refined = _minimum(values, mse)
     return {"A_u": values, "mse": mse, "A_u_star_sampled": sampled,

@@ -1,17 +1,20 @@
-"""The A_T calibration of Sec. 4.2 (Fig. A_T-vs-MSE) on the oracle at a
-reduced size: the hot-wall channel (gas entering at 300 K between walls at
-400 K) in its diffuse form against its sharp form.  What the paper's
-procedure needs and what the physics fixes:
+"""The A_u and A_T calibrations of Secs. 4.1 and 4.2 (Figs. A_u-vs-MSE and
+A_T-vs-MSE) on the oracle at a reduced size: the channel (for A_T with gas
+entering at 300 K between walls at 400 K) in its diffuse form against its
+sharp form.  What the paper's procedure needs and what the physics fixes:
 
 * the sharp channel's temperature across the sampled section is symmetric
   about the centreline and lies between the inlet and wall temperatures,
   hotter at the walls than at the centre;
 * the mean standard error of eq. mean-standard-error-f (f = T) has an
   interior minimum in A_T: too weak a coupling leaves the gas near the
-  diffuse walls cold, too strong a one heats it ahead of the sharp wall.
+  diffuse walls cold, too strong a one heats it ahead of the sharp wall;
+* likewise f = u in A_u: too weak a drag lets the gas slip through the
+  diffuse walls, too strong a one stops it ahead of the sharp wall.
 
-The sweep driver (calibration.sweep_A_T) takes the oracle as its runner here;
-on the GPU it runs the library with one stream per value.
+The sweep drivers (calibration.sweep_A_u, sweep_A_T) take the oracle as
+their runner here; on the GPU they run the library with one stream per
+value.
 """
 from __future__ import annotations
 
@@ -32,13 +35,13 @@ def _threads():
     yield
 
 
-def _oracle_run(probs):
+def _oracle_run(probs, field="T"):
     out = []
     for p in probs:
         f = I.di_channel_fields(p)
         s = O.OracleState(p, f["phi"], f["T"])
         s.step(STEPS)
-        out.append(s.T.copy())
+        out.append(s.T.copy() if field == "T" else s.moments()[0][0].copy())
     return out
 
 
@@ -61,6 +64,16 @@ def test_A_T_sweep_has_an_interior_minimum():
     lo, hi = r["A_T"][k - 1], r["A_T"][k + 1]
     assert lo < r["A_T_star"] < hi
     assert r["paper_fit_A_T_star"] == pytest.approx(24.24 + 33.81 * 400.0 / 300.0)
+
+
+def test_A_u_sweep_has_an_interior_minimum():
+    r = C.sweep_A_u([10, 30, 100, 300, 1000, 3000], steps=STEPS,
+                    run=lambda probs: _oracle_run(probs, "u"), **SIZE)
+    mse = np.asarray(r["mse"])
+    k = int(np.argmin(mse))
+    assert 0 < k < len(mse) - 1, mse
+    assert mse[k] < 0.05 * mse[0] and mse[k] < 0.05 * mse[-1], mse
+    assert r["A_u"][k - 1] < r["A_u_star"] < r["A_u"][k + 1]
 
 
 def test_refined_minimiser_is_the_vertex_of_the_log_parabola():
