@@ -641,13 +641,17 @@ def di_channel(L=50, eta=8, solid=8, Re=100.0, u_in=0.05, H=None, A_u=145.0, sha
 
 
 def di_channel_fields(p):
-    """Phase field of the channel walls (zero in the sharp form)."""
+    """Phase field of the channel walls (zero in the sharp form); gas at
+    T_in, and the solid layers (phi_f below phi_min) at the solid
+    temperature, which they take from the first step on anyway."""
     nx, ny, s, L = p["nx"], p["ny"], p["solid"], p["L"]
     yc = np.arange(ny) + 0.5
     d = np.minimum(yc - s, (s + L) - yc)
     col = wall_phi(d, p["eta"]) if s > 0 else np.zeros(ny)
     phi = np.repeat(col[:, None], nx, axis=1).reshape(-1)
-    return {"phi": phi, "T": np.full(nx * ny, 300.0), "Y": None, "Ts": None, "u": None}
+    T = np.full(nx * ny, float(p["T_in"]))
+    T[1.0 - phi < p.get("phi_min", 1e-6)] = p["Ts_uniform"]
+    return {"phi": phi, "T": T, "Y": None, "Ts": None, "u": None}
 
 
 def channel_mse(u_si, u_di, p_si, p_di, at=0.9):
